@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the CheFSI hot path (H*X point-orbital updates per second).
+
+One step = one complete CheFSI solve of a synthetic cluster on a fixed Hamiltonian, the
+first-SCF-step regime of the paper (Sec. 3.4): k Lanczos steps for the spectral bounds,
+then `iters` CheFSI iterations (Chebyshev filter of degree m, projection, Rayleigh-Ritz,
+rotation), starting from the same resident random block each step. The work unit is the
+point-orbital update: one grid node of one column under one application of H, so a step
+holds k*Nd + iters*(m+1)*Nd*Ns of them.
+
+Default workload: 96^3 grid, h = 0.3 bohr, 40 atoms, Ns = 128, m = 20, 20 iterations,
+FP64 (the medium cluster). Inputs are larger than L2 (the 128-column FP64 block is
+0.91 GB), so no L2 flush is needed between steps.
+
+Under torchrun (N > 1) each rank solves its own replica on its own GPU (replicas only:
+the path has no data exchange), times are max-reduced over ranks and `value` sums the
+ranks' work.
+
+--impl reference times the FP64 CPU oracle instead (on the host cores, rank 0 only),
+each step a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1603_04334_gb300 import synth  # noqa: E402
+
+METRIC = "H*X point-orbitals/s"
+UNIT = "point-orbitals/s"
+ORACLE_COLS = 16      # column slice of the block the oracle timing runs on
+SM_COUNT = 152
+
+
+def reduce_max(value_ms: float, world: int, device=None) -> float:
+    """Max over ranks of a per-rank time (the slowest replica sets the job time)."""
+    if world <= 1:
+        return value_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(work_per_rank_step: int, steps: int, world: int, ms: float) -> float:
+    """Whole-job throughput: every rank's units over the max-over-ranks time."""
+    return work_per_rank_step * steps * world / (ms / 1e3)
+
+
+def work_per_step(w) -> int:
+    return w.lanczos_k * w.nd + w.iters * (w.degree + 1) * w.nd * w.ns
+
+
+def workload_config(w, dtype: str) -> dict:
+    return {"workload": f"{w.name}: {w.n}^3 grid h={w.h} bohr, {w.natoms} atoms, Ns={w.ns}, "
+                        f"Chebyshev degree {w.degree}, {w.iters} CheFSI iterations, {dtype}",
+            "n": w.n, "h": w.h, "natoms": w.natoms, "ns": w.ns, "degree": w.degree,
+            "iters": w.iters, "lanczos_k": w.lanczos_k, "dtype": dtype,
+            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
+
+
+# ----------------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------------
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------
+# roofline helpers
+# ----------------------------------------------------------------------------------
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def fp64_alu_peak_tflops(sm_max_mhz: float = 2070.0) -> float:
+    # 152 SMs x 2 FP64 FMA lanes per SM per clock (1.25 TFLOP/s nominal at 2.07 GHz;
+    # measured 0.595e12 DFMA/s at 1.99 GHz) x 2 flop per FMA.
+    return SM_COUNT * 2 * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+def stencil_traffic(dtype: str):
+    """DRAM bytes per stencil launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "stencil_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    h = hashlib.sha256()
+    for fn in ("stencil.cu", "internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1603_04334_gb300", "csrc", fn), "rb") as g:
+            h.update(g.read())
+    ent = d.get(dtype)
+    if not ent or ent.get("source_sha256") != h.hexdigest():
+        return None
+    return ent.get("bytes_per_launch_full")
+
+
+def stencil_algorithmic(w, dtype: str, prof: dict, steps: int) -> dict:
+    """Algorithmic bytes and flops of the stencil phase over the timed steps.
+
+    Per point-orbital: a filter step reads Y_j and Y_{j-1} and writes Y_{j+1}
+    (3 elements), H X reads X and writes HX (2 elements); V_eff adds one value per node
+    per launch. Flops per point-orbital: 6 radii x (5 adds + 1 FMA) + centre
+    (1 FMA + 1 multiply) + recurrence (1 FMA) = 47 (45 for H X)."""
+    es = 8 if dtype == "f64" else 4
+    nd, ns, m, it = w.nd, w.ns, w.degree, w.iters
+    # per iteration: first filter step without Y_{j-1}, m-1 with it, one H X in RR
+    three = (m - 1) * ns
+    two = 2 * ns
+    per_it_bytes = nd * (three * 3 * es + two * 2 * es) + (m + 1) * nd * es
+    per_it_flops = nd * (three * 47 + two * 45)
+    lz_bytes = w.lanczos_k * nd * (2 * 8 + 8)
+    lz_flops = w.lanczos_k * nd * 45
+    tot_bytes = steps * (it * per_it_bytes + lz_bytes)
+    tot_flops = steps * (it * per_it_flops + lz_flops)
+    n_launch, ms = prof["stencil"]
+    return {"bytes": tot_bytes, "flops": tot_flops, "launches": n_launch, "ms": ms}
+
+
+# ----------------------------------------------------------------------------------
+# our implementation
+# ----------------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1603_04334_gb300 import sparc
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.preset(args.workload)
+    dtype = args.dtype or w.filter_dtype
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    cl = synth.make_cluster(w, args.seed)
+    stream = torch.cuda.current_stream(dev)
+    ctx = sparc.Context(cl.n, cl.h, cl.R, cl.Z, cl.gamma, veff=None, sigma=cl.sigma,
+                        rcut=cl.rcut, rc_erf=cl.rc_erf, stream=stream)
+    X0h = synth.initial_block(args.seed + 1, w.nd, w.ns)
+    X0 = torch.from_numpy(X0h).to(dev, dtype=tdt)
+    X = torch.empty_like(X0)
+    W = torch.empty_like(X0)
+
+    def solve(Xsrc):
+        X.copy_(Xsrc, non_blocking=True)
+        lo, hi = ctx.lanczos_bounds(w.lanczos_k, args.seed)
+        b = sparc.first_bounds(lo, hi)
+        ritz = resid = None
+        for it in range(w.iters):
+            ritz, resid, b = ctx.chefsi_step(X, W, w.degree, b, want_resid=(it == w.iters - 1))
+        return ritz, resid
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        solve(X0)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident in HBM -------------------------------
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    smi_index = int(vis[local_rank]) if local_rank < len(vis) and vis[local_rank].isdigit() \
+        else local_rank
+    clocks = ClockSampler(smi_index)
+    ctx.profile_reset()
+    ctx.profile_enable(True)
+    n0 = sparc.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ritz, resid = solve(X0)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    launches = sparc.launch_count() - n0
+    ms = ev0.elapsed_time(ev1)
+    ctx.profile_enable(False)
+    prof = ctx.profile_read()
+    ms = reduce_max(ms, world, dev)
+    work = work_per_step(w) * args.steps * world
+    value = job_value(work_per_step(w), args.steps, world, ms)
+
+    # ---- end-to-end: host block in pinned memory -> device each step ------------------
+    e2e = None
+    if not args.no_e2e:
+        Xpin = torch.from_numpy(X0h).to(dtype=tdt).pin_memory()
+        solve(Xpin)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r_host, _ = solve(Xpin)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e_ms = reduce_max((t1 - t0) * 1e3, world, dev)
+        es = 8 if dtype == "f64" else 4
+        e2e = {"value": work / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(w.nd * w.ns * es),
+               "d2h_bytes_per_step": int(w.iters * (2 * w.ns * 8 + 4) + 2 * 8 + 4),
+               "ms_per_step": e_ms / args.steps}
+
+    alg = stencil_algorithmic(w, dtype, prof, args.steps)
+    peaks = measured_peaks()
+    sm_max = ck.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    if dtype == "f64":
+        achieved = alg["flops"] / (alg["ms"] / 1e3) / 1e12 if alg["ms"] > 0 else None
+        peak = fp64_alu_peak_tflops(sm_max)
+        roof = {"bound": "alu", "kernel": "k_stencil<double> (fused stencil + V_eff + recurrence)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None,
+                "peak_source": "FP64 FMA issue: 152 SMs x 2 lanes x 2 flop x max SM clock "
+                               "(recipe: 1.25 TFLOP/s nominal)",
+                "hbm_gbs_achieved": alg["bytes"] / (alg["ms"] / 1e3) / 1e9 if alg["ms"] else None,
+                "hbm_frac_of_measured": (alg["bytes"] / (alg["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"])
+                if alg["ms"] and peaks.get("hbm_gbs") else None,
+                "traffic": stencil_traffic(dtype),
+                "avg_launch_ms": alg["ms"] / max(alg["launches"], 1)}
+    else:
+        gbs = alg["bytes"] / (alg["ms"] / 1e3) / 1e9 if alg["ms"] else None
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "kernel": "k_stencil<float>", "achieved": gbs, "peak": peak,
+                "unit": "GB/s", "frac": gbs / peak if gbs else None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback",
+                "traffic": stencil_traffic(dtype),
+                "avg_launch_ms": alg["ms"] / max(alg["launches"], 1)}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+           "config": workload_config(w, dtype), "roofline": roof, "clocks": ck,
+           "e2e": e2e, "gpu_launches": int(launches),
+           "phases_ms": {k: round(v[1], 3) for k, v in prof.items()},
+           "ritz_lowest": [float(x) for x in ritz[:4]],
+           "max_resid": float(np.max(resid)) if resid is not None else None}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_sample(w, args.seed, budget_s=args.cpu_budget)
+    ctx.close()
+    return out
+
+
+# ----------------------------------------------------------------------------------
+# the oracle (CPU baseline and the reference arm)
+# ----------------------------------------------------------------------------------
+def oracle_sample(w, seed: int, budget_s: float = 12.0, max_iters: int = 64) -> dict:
+    """Times the FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    CheFSI iterations (filter of degree m + Rayleigh-Ritz) on a 16-column slice of the
+    start block, repeated until `budget_s` seconds have passed."""
+    import oracle
+
+    cl = synth.make_cluster(w, seed)
+    H = oracle.Hamiltonian.from_cluster(cl)
+    X = synth.initial_block(seed + 1, w.nd, w.ns)[:ORACLE_COLS].copy()
+    lo, hi, _ = H.lanczos_bounds(w.lanczos_k, seed)
+    b = oracle.chefsi_first_bounds(lo, hi)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        X, ritz, res, b = oracle.chefsi_step(H, X, w.degree, b)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s or n >= max_iters:
+            break
+    t = time.perf_counter() - t0
+    work = n * (w.degree + 1) * w.nd * X.shape[0]
+    cores = min(os.cpu_count() or 1, X.shape[0], int(os.environ.get("OMP_NUM_THREADS", "9999")))
+    return {"value": work / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} CheFSI iteration(s) (degree {w.degree} filter + RR) on a "
+                      f"{X.shape[0]}-column slice of {w.name}, {t:.1f} s, OpenMP over columns"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    w = synth.preset(args.workload)
+    dtype = "f64"
+    for _ in range(args.warmup):
+        oracle_sample(w, args.seed, budget_s=0.0, max_iters=1)
+    t0 = time.perf_counter()
+    samples = [oracle_sample(w, args.seed, budget_s=0.0, max_iters=1) for _ in range(args.steps)]
+    t = time.perf_counter() - t0
+    work = args.steps * (w.degree + 1) * w.nd * ORACLE_COLS
+    value = work / t
+    cb = dict(samples[-1])
+    cb["value"] = value
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic", "config": workload_config(w, dtype), "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="cluster96", choices=sorted(synth.PRESETS))
+    ap.add_argument("--dtype", choices=["f64", "f32"], default=None)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and not os.environ.get("SPARC_BENCH_ALLOW_SHORT"):
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * sparc.h -- C ABI of the GB300 (sm_103a) Chebyshev-filtered subspace iteration
+ * library for SPARC's real-space Kohn-Sham Hamiltonian of isolated clusters
+ * (Ghosh & Suryanarayana, arXiv:1603.04334).
+ *
+ * The Hamiltonian (Sec. 3.1, text after Eq. non-localPS:FD) is
+ *     H = -1/2 L_h + diag(V_eff) + V_nl,
+ * with L_h the order-2n_o central finite-difference Laplacian of Eq. (FD:Laplacian),
+ * weights of Eq. (weightsLap), n_o = 6, zero-Dirichlet boundaries, and the
+ * Kleinman-Bylander nonlocal operator of Eq. (non-localPS:FD),
+ *     V_nl f = h^3 sum_J sum_lm gamma_Jlm chi_Jlm (chi_Jlm^T f).
+ *
+ * Conventions shared by every call:
+ *   - Grid nodes (i, j, k), 0 <= i < n[0], ..., at coordinates (i h, j h, k h); the
+ *     linear node index is p = i + n[0] (j + n[1] k) (x fastest). Nd = n0 n1 n2.
+ *   - A block of orbitals (Psi in Sec. 3.1) is a column-major Nd x ncols array on the
+ *     device: column c starts at element c*ld, ld >= Nd. Blocks are owned by the
+ *     caller (for instance PyTorch tensors of shape (ncols, ld)); the library never
+ *     frees them. Element type is given by a sparc_dtype argument.
+ *   - Every call is enqueued on the stream bound at sparc_create. Calls that return
+ *     host values (Ritz values, residuals, bounds) synchronise that stream before
+ *     returning; the others are asynchronous.
+ *   - Every call returns a status; none aborts, traps or prints. On failure the
+ *     message is kept per context (sparc_last_error). Arguments are checked on the
+ *     host before any work is enqueued.
+ *   - One context per stream; a context must not be used by two threads at once.
+ */
+#ifndef SPARC_GB300_H
+#define SPARC_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sparc_ctx sparc_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    SPARC_OK = 0,
+    SPARC_ERR_ARG = -1,        /* invalid argument (sizes, pointers, bounds order) */
+    SPARC_ERR_OOM = -2,        /* device or pinned-host allocation failed */
+    SPARC_ERR_CUDA = -3,       /* a CUDA runtime call or kernel launch failed */
+    SPARC_ERR_NOT_SPD = -4,    /* overlap matrix M_s not positive definite (Cholesky) */
+    SPARC_ERR_NONFINITE = -5,  /* NaN or Inf met in a projected matrix */
+    SPARC_ERR_TIMEOUT = -6,    /* a bounded device-side iteration ran out */
+    SPARC_ERR_BUDGET = -7      /* a request exceeds a configured memory budget */
+} sparc_status;
+
+typedef enum { SPARC_F64 = 0, SPARC_F32 = 1 } sparc_dtype;
+
+/* Uniform grid of Sec. 3.1: n[d] nodes per axis, spacing h (bohr), stencil radius
+ * n_o (`radius`, 1..6; the paper uses 6, Sec. 4). */
+typedef struct {
+    int n[3];
+    double h;
+    int radius;
+} sparc_grid;
+
+/* Atoms of the cluster. R: 3*natoms positions (bohr), host memory. Z: natoms valence
+ * charges (only read when sparc_create builds V_eff itself). gamma: 4*natoms KB
+ * coefficients for the projectors (s, px, py, pz) of each atom (Sec. 2). Projector
+ * radial form: chi_s = Y00 exp(-r^2/(2 sigma^2)), chi_pd = sqrt(3/4pi) (x_d - R_d)
+ * exp(-r^2/(2 sigma^2)), truncated to nodes with r^2 <= rcut^2. rc_erf is the width
+ * of the synthetic local potential -Z erf(r/rc_erf)/r. natoms may be 0. */
+typedef struct {
+    int natoms;
+    const double *R;
+    const double *Z;
+    const double *gamma;
+    double sigma;
+    double rcut;
+    double rc_erf;
+} sparc_atoms;
+
+/* Creates a context: copies V_eff (or builds it on the device when veff_host is
+ * NULL, from V_eff(x) = sum_J -Z_J erf(|x-R_J|/rc_erf)/|x-R_J|), builds the projector
+ * support tables on the device (Sec. 3.2's per-atom influence boxes, restricted to
+ * the sphere r <= rcut), and binds `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream). veff_host: Nd doubles, x fastest, host memory. */
+sparc_status sparc_create(const sparc_grid *grid, const double *veff_host,
+                          const sparc_atoms *atoms, void *cuda_stream, sparc_ctx **out);
+
+/* Frees everything the context owns. NULL is accepted. */
+sparc_status sparc_destroy(sparc_ctx *ctx);
+
+/* Last error message of the context ("" if none); valid until the next call. */
+const char *sparc_last_error(const sparc_ctx *ctx);
+
+/* Copies the context's V_eff (Nd doubles) to host memory; synchronises. */
+sparc_status sparc_get_veff(sparc_ctx *ctx, double *veff_host);
+
+/* Number of nodes and of projector support entries (sum over atoms). */
+sparc_status sparc_info(const sparc_ctx *ctx, long *nd, long *nsupport, int *natoms);
+
+/* Scales the kinetic term: H = -1/2 kscale L_h + V_eff + V_nl (default 1). kscale = 0
+ * gives a diagonal-plus-nonlocal operator, used to check the filter against scalar
+ * Chebyshev values. */
+sparc_status sparc_set_kinetic_scale(sparc_ctx *ctx, double kscale);
+
+/* HX = H X, Sec. 3.1. X, HX: distinct device blocks of `dtype` (F64 or F32, the
+ * arithmetic follows the storage type), ncols columns, leading dimension ld. */
+sparc_status sparc_apply_H(sparc_ctx *ctx, sparc_dtype dtype, const void *X, void *HX,
+                           int ncols, long ld);
+
+/* Spectral bounds by k Lanczos steps (Sec. 4: extremal eigenvalues of H from "a few
+ * iterations of the Lanczos method"), all on the device in FP64. Start vector
+ * v0[p] = u(splitmix64(seed ^ p)) - 0.5, u(z) = (z >> 11) 2^-53, normalised; no
+ * reorthogonalisation. Returns lo = theta_min(T_k) and
+ * hi = max(1.01 theta_max, theta_max + |beta_k s_k|) (s_k: last component of the
+ * unit eigenvector of theta_max). 1 <= k <= 64. Synchronises. */
+sparc_status sparc_lanczos_bounds(sparc_ctx *ctx, int ksteps, unsigned long long seed,
+                                  double *lo, double *hi);
+
+/* Chebyshev filter, Algorithm ChebychevFilter with Eq. (ChebFilter), Sec. 3.4:
+ * X <- p_m(H) X with p_m(t) = C_m((t - c)/e) / C_m((a0 - c)/e), e = (b - a)/2,
+ * c = (b + a)/2, m = degree (number of applications of H), using the scaled
+ * three-term recurrence of the CheFSI method the paper cites:
+ *   sigma_1 = e/(a0 - c); Y_1 = (sigma_1/e)(H - c)X;
+ *   sigma_j = 1/(2/sigma_1 - sigma_{j-1}),
+ *   Y_j = (2 sigma_j/e)(H - c) Y_{j-1} - sigma_{j-1} sigma_j Y_{j-2}.
+ * a = cutoff lambda_c, b = upper bound of the spectrum, a0 = lower end (lambda_1
+ * estimate); requires a0 < a < b, degree >= 1. work: a second device block with the
+ * same dtype, ncols and ld, overwritten. FP64 or FP32 arithmetic per dtype. */
+sparc_status sparc_cheb_filter(sparc_ctx *ctx, sparc_dtype dtype, void *X, void *work,
+                               int ncols, long ld, int degree, double a, double b,
+                               double a0);
+
+/* Projection, generalized eigenproblem and rotation, Sec. 3.4 (Eq.
+ * SubspaceGeneralizedEigenproblem and Eq. OrbitalTransformation), in FP64 on the
+ * device: M_s = Xf^T Xf, H_s = Xf^T (H Xf), M_s = L L^T (Cholesky),
+ * Q^T (L^-1 H_s L^-T) Q = diag(ritz) (cyclic Jacobi), Xf <- Xf (L^-T Q).
+ * Each column of Q is signed so that its largest-magnitude entry is positive.
+ * On return Xf holds Euclidean-orthonormal Ritz vectors (ascending Ritz values),
+ * ritz_host[ncols] the Ritz values, and resid_host[ncols] (if not NULL) the residual
+ * norms ||H x_n - ritz_n x_n||_2. For dtype F32 the block stays FP32 while H Xf, the
+ * projected matrices and the eigensolve are FP64. HXf_or_null: optional FP64 device
+ * block (ncols x ld) used as the H Xf workspace; when NULL the context allocates one.
+ * Fails with SPARC_ERR_NOT_SPD if M_s is not numerically positive definite and with
+ * SPARC_ERR_NONFINITE on NaN/Inf, leaving Xf unrotated. ncols <= 1024. Synchronises. */
+sparc_status sparc_orth_rr(sparc_ctx *ctx, sparc_dtype dtype, void *Xf, void *HXf_or_null,
+                           int ncols, long ld, double *ritz_host, double *resid_host);
+
+/* One CheFSI iteration, Sec. 3.4: sparc_cheb_filter with bounds_inout = [a, b, a0],
+ * then sparc_orth_rr. Afterwards bounds_inout is updated for the next iteration:
+ * a = largest Ritz value, a0 = smallest Ritz value, b unchanged. work as in
+ * sparc_cheb_filter. Synchronises. */
+sparc_status sparc_chefsi_step(sparc_ctx *ctx, sparc_dtype dtype, void *X, void *work,
+                               int ncols, long ld, int degree, double *bounds_inout,
+                               double *ritz_host, double *resid_host);
+
+/* ---- instrumentation ------------------------------------------------------------ */
+
+/* Phases timed by the context's profiler. */
+typedef enum {
+    SPARC_PHASE_STENCIL = 0, /* fused stencil + V_eff + recurrence (H X, filter steps) */
+    SPARC_PHASE_PROJECT = 1, /* nonlocal projections chi^T Y */
+    SPARC_PHASE_SCATTER = 2, /* nonlocal scatter-add */
+    SPARC_PHASE_GRAM = 3,    /* M_s and H_s contractions */
+    SPARC_PHASE_DENSE = 4,   /* Cholesky, Jacobi eigensolve, back-transform */
+    SPARC_PHASE_ROTATE = 5,  /* subspace rotation (and rotated H X for residuals) */
+    SPARC_PHASE_OTHER = 6,   /* Lanczos vector kernels, residual norms, copies */
+    SPARC_NPHASES = 7
+} sparc_phase;
+
+/* Enables (1) or disables (0) per-phase timing: each phase's launches are bracketed by
+ * CUDA events recorded on the context stream. Disabling discards pending events. */
+sparc_status sparc_profile_enable(sparc_ctx *ctx, int enable);
+
+/* Accumulated launches and device milliseconds of `phase` since the last reset;
+ * synchronises the context stream. */
+sparc_status sparc_profile_read(sparc_ctx *ctx, int phase, long long *launches, double *ms);
+
+/* Clears the accumulated profile. */
+sparc_status sparc_profile_reset(sparc_ctx *ctx);
+
+/* Number of kernels this library has launched in the calling process (all contexts). */
+sparc_status sparc_launch_count(long long *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPARC_GB300_H */

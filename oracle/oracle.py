@@ -131,12 +131,18 @@ def laplacian(f: np.ndarray, n, h: float, no: int = 6) -> np.ndarray:
 # ----------------------------------------------------------------------------------
 # Potential and projectors
 # ----------------------------------------------------------------------------------
-def veff(n: int, h: float, R: np.ndarray, Z: np.ndarray, rc: float = 1.0) -> np.ndarray:
-    """Synthetic local potential sum_J -Z_J erf(r/rc)/r on the grid (flat, x fastest)."""
+def _n3(n):
+    return (int(n), int(n), int(n)) if np.isscalar(n) else tuple(int(v) for v in n)
+
+
+def veff(n, h: float, R: np.ndarray, Z: np.ndarray, rc: float = 1.0) -> np.ndarray:
+    """Synthetic local potential sum_J -Z_J erf(r/rc)/r on the grid (flat, x fastest).
+    n: nodes per axis (int for a cubic grid, or (n0, n1, n2))."""
+    n0, n1, n2 = _n3(n)
     R = np.ascontiguousarray(R, dtype=np.float64).reshape(-1, 3)
     Z = np.ascontiguousarray(Z, dtype=np.float64)
-    V = np.zeros(n ** 3)
-    lib().orc_veff(n, n, n, h, R.shape[0], _dp(R), _dp(Z), rc, _dp(V))
+    V = np.zeros(n0 * n1 * n2)
+    lib().orc_veff(n0, n1, n2, h, R.shape[0], _dp(R), _dp(Z), rc, _dp(V))
     return V
 
 
@@ -149,15 +155,16 @@ class Projectors:
     chi: np.ndarray        # (nsup, 4) float64: s, px, py, pz
 
 
-def projectors(n: int, h: float, R: np.ndarray, sigma: float = 0.8,
+def projectors(n, h: float, R: np.ndarray, sigma: float = 0.8,
                rcut: float = 3.0) -> Projectors:
+    n0, n1, n2 = _n3(n)
     R = np.ascontiguousarray(R, dtype=np.float64).reshape(-1, 3)
     na = R.shape[0]
     counts = np.zeros(max(na, 1), dtype=np.int64)
-    total = lib().orc_projector_count(n, n, n, h, na, _dp(R), rcut, _lp(counts))
+    total = lib().orc_projector_count(n0, n1, n2, h, na, _dp(R), rcut, _lp(counts))
     idx = np.zeros(max(total, 1), dtype=np.int64)
     chi = np.zeros((max(total, 1), 4))
-    lib().orc_projector_fill(n, n, n, h, na, _dp(R), sigma, rcut, _lp(idx), _dp(chi))
+    lib().orc_projector_fill(n0, n1, n2, h, na, _dp(R), sigma, rcut, _lp(idx), _dp(chi))
     ptr = np.zeros(na + 1, dtype=np.int64)
     ptr[1:] = np.cumsum(counts[:na])
     return Projectors(ptr, idx[:total].copy(), chi[:total].copy())
@@ -167,15 +174,17 @@ def projectors(n: int, h: float, R: np.ndarray, sigma: float = 0.8,
 # Hamiltonian
 # ----------------------------------------------------------------------------------
 class Hamiltonian:
-    """H = -1/2 kscale L_h + diag(V) + V_nl on an n^3 grid (Sec. 3.1).
+    """H = -1/2 kscale L_h + diag(V) + V_nl on an n0 x n1 x n2 grid (Sec. 3.1).
 
-    kscale = 0 keeps only the diagonal part (plus V_nl if atoms are given)."""
+    n: int (cubic grid) or (n0, n1, n2). kscale = 0 keeps only the diagonal part (plus
+    V_nl if atoms are given)."""
 
-    def __init__(self, n: int, h: float, V: np.ndarray, R: Optional[np.ndarray] = None,
+    def __init__(self, n, h: float, V: np.ndarray, R: Optional[np.ndarray] = None,
                  gamma: Optional[np.ndarray] = None, sigma: float = 0.8,
                  rcut: float = 3.0, no: int = 6, kscale: float = 1.0):
+        self.n3 = _n3(n)
         self.n, self.h, self.no, self.kscale = n, h, no, kscale
-        self.nd = n ** 3
+        self.nd = self.n3[0] * self.n3[1] * self.n3[2]
         self.V = np.ascontiguousarray(V, dtype=np.float64).reshape(-1)
         assert self.V.shape[0] == self.nd
         if R is None or len(R) == 0:
@@ -187,7 +196,7 @@ class Hamiltonian:
             self.proj = projectors(n, h, R, sigma, rcut)
             self.natoms = int(np.asarray(R).reshape(-1, 3).shape[0])
             self.gamma = np.ascontiguousarray(gamma, dtype=np.float64).reshape(-1, 4)
-        self._s = _Ham(n, n, n, h, no, kscale, _dp(self.V), self.natoms,
+        self._s = _Ham(*self.n3, h, no, kscale, _dp(self.V), self.natoms,
                        _lp(self.proj.atom_ptr), _lp(self.proj.idx), _dp(self.proj.chi),
                        _dp(self.gamma))
 
@@ -308,6 +317,11 @@ def orth_rr(Yf: np.ndarray, HYf: np.ndarray):
         L = sla.cholesky(M, lower=True)
     except np.linalg.LinAlgError as e:
         raise NotSPD(str(e)) from e
+    # numerically positive definite: every pivot L_jj^2 above 4 n eps M_jj (the squared
+    # sine of the angle between column j and the span of the columns before it)
+    n = M.shape[0]
+    if np.any(np.diag(L) ** 2 <= 4.0 * n * np.finfo(float).eps * np.diag(M)):
+        raise NotSPD("Cholesky pivot below 4 n eps of its diagonal entry")
     W = sla.solve_triangular(L, Hs, lower=True)          # L^-1 H_s
     A = sla.solve_triangular(L, W.T, lower=True).T       # L^-1 H_s L^-T
     A = 0.5 * (A + A.T)

@@ -1,0 +1,165 @@
+// internal.cuh -- declarations shared by the CUDA translation units of libsparc_gb300.
+// Not part of the public ABI (include/sparc.h is).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace sparc {
+
+constexpr int kRadius = 6;  // stencil radius the kernels are written for (n_o <= 6)
+
+// Counts kernel launches made by this library (process-wide, read by sparc_launch_count).
+void note_launch(int n = 1);
+
+// Device copy of the discrete Hamiltonian (Sec. 3.1) and of its projector tables.
+struct DevHam {
+    int n0 = 0, n1 = 0, n2 = 0;
+    long nd = 0;
+    double h = 0;
+    int radius = 6;
+    double kscale = 1.0;
+    double w[kRadius + 1] = {0};  // Laplacian weights w_p (1/h^2 included), zero beyond radius
+
+    const double *V = nullptr;   // V_eff, Nd
+    const float *Vf = nullptr;   // V_eff rounded to float (FP32 filter)
+
+    int natoms = 0;
+    long nsup = 0;                   // support entries over all atoms
+    const int *atom_ptr = nullptr;   // natoms+1 offsets into the entry arrays
+    const int *idx = nullptr;        // node index of each entry
+    const double *chi = nullptr;     // 4 per entry: chi_s, chi_px, chi_py, chi_pz
+    const float *chi_f = nullptr;
+    const double *gchi = nullptr;    // 4 per entry: h^3 gamma_Jlm chi_Jlm
+    const float *gchi_f = nullptr;
+    const int *ent_atom = nullptr;   // atom of each entry
+
+    long nuniq = 0;                  // nodes covered by at least one support
+    const int *uniq_node = nullptr;  // ascending node indices
+    const int *uniq_ptr = nullptr;   // nuniq+1 offsets into ent_list
+    const int *ent_list = nullptr;   // entries of each node, ascending entry id
+};
+
+// Coefficients of one fused step  out = alpha*((-1/2 ks L_h + V - c) Y + V_nl Y) - beta*Yprev.
+// w[r] = alpha * (-1/2) * ks * w_r (r >= 1); c0 = alpha * (-1/2) * ks * 6 w_0 - alpha * c.
+template <typename TC>
+struct StepCoef {
+    TC w[kRadius + 1];
+    TC c0;
+    TC alpha;
+    TC beta;
+};
+
+StepCoef<double> make_coef(const DevHam &H, double alpha, double shift, double beta);
+
+// ---- stencil.cu -------------------------------------------------------------------
+// out = alpha*((-1/2 ks L_h + V - shift) Y) - beta*Yprev   (local part of H, fused step).
+// Yprev may be null (beta ignored) and may alias out (in-place recurrence).
+cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, double *out,
+                        int ncols, long ld, double alpha, double shift, double beta,
+                        cudaStream_t st);
+cudaError_t stencil_f32(const DevHam &H, const float *Y, const float *Yprev, float *out,
+                        int ncols, long ld, double alpha, double shift, double beta,
+                        cudaStream_t st);
+// FP64 arithmetic on an FP32 block (H applied to FP32 Ritz blocks in FP64).
+cudaError_t stencil_f32in_f64(const DevHam &H, const float *Y, double *out, int ncols,
+                              long ld, cudaStream_t st);
+
+// ---- nonlocal.cu ------------------------------------------------------------------
+// C[(J*4+lm)*ncols + c] = sum_{s in supp(J)} chi_Jlm(s) Y[idx(s) + c*ld]
+cudaError_t project_f64(const DevHam &H, const double *Y, int ncols, long ld, double *C,
+                        cudaStream_t st);
+cudaError_t project_f32(const DevHam &H, const float *Y, int ncols, long ld, float *C,
+                        cudaStream_t st);
+cudaError_t project_f32in_f64(const DevHam &H, const float *Y, int ncols, long ld, double *C,
+                              cudaStream_t st);
+// out[node + c*ld] += alpha * sum_{entries e at node} sum_lm gchi(e,lm) C[(atom(e)*4+lm)*ncols + c]
+cudaError_t scatter_f64(const DevHam &H, const double *C, double *out, int ncols, long ld,
+                        double alpha, cudaStream_t st);
+cudaError_t scatter_f32(const DevHam &H, const float *C, float *out, int ncols, long ld,
+                        double alpha, cudaStream_t st);
+
+// ---- setup.cu -------------------------------------------------------------------
+// V_eff(x) = sum_J -Z_J erf(r/rc)/r on the device.
+cudaError_t build_veff(int n0, int n1, int n2, double h, int natoms, const double *R_dev,
+                       const double *Z_dev, double rc, double *V, cudaStream_t st);
+// Support counts per atom (r^2 <= rcut^2 within the grid).
+cudaError_t support_count(int n0, int n1, int n2, double h, int natoms, const double *R_dev,
+                          double rcut, int *counts, cudaStream_t st);
+// Fills idx/chi (entries atom by atom, ascending node index), ent_atom, gchi (+ float copies).
+cudaError_t support_fill(int n0, int n1, int n2, double h, int natoms, const double *R_dev,
+                         const double *gamma_dev, double sigma, double rcut,
+                         const int *atom_ptr, int *idx, double *chi, float *chi_f,
+                         double *gchi, float *gchi_f, int *ent_atom, cudaStream_t st);
+// Inverse map node -> entries. Scratch buffers sized by the caller (see sparc.cu).
+cudaError_t build_inverse_map(long nd, long nsup, const int *idx, int *node_cnt,
+                              int *node_start, int *cursor, int *ent_list, int *flags,
+                              int *uniq_rank, int *scan_tmp, int *uniq_node, int *uniq_ptr,
+                              cudaStream_t st);
+cudaError_t exclusive_scan_int(const int *in, int *out, long n, int *tmp, cudaStream_t st);
+cudaError_t to_float(const double *in, float *out, long n, cudaStream_t st);
+
+// ---- gram.cu --------------------------------------------------------------------
+// G (ns x ns, column-major, FP64) = A^T B over nd rows; A, B column-major with lda/ldb.
+// part: workspace of gram_part_elems(ns, nd) doubles.
+long gram_part_elems(int ns, long nd);
+cudaError_t gram_f64(const double *A, long lda, const double *B, long ldb, long nd, int ns,
+                     double *G, double *part, cudaStream_t st);
+cudaError_t gram_f32_f32(const float *A, long lda, const float *B, long ldb, long nd, int ns,
+                         double *G, double *part, cudaStream_t st);
+cudaError_t gram_f32_f64(const float *A, long lda, const double *B, long ldb, long nd, int ns,
+                         double *G, double *part, cudaStream_t st);
+// out (nd x ns, ldo) = A (nd x ns, lda) Q (ns x ns, column-major FP64)
+cudaError_t rotate_f64(const double *A, long lda, long nd, int ns, const double *Q,
+                       double *out, long ldo, cudaStream_t st);
+cudaError_t rotate_f32(const float *A, long lda, long nd, int ns, const double *Q, float *out,
+                       long ldo, cudaStream_t st);
+
+// ---- dense.cu -------------------------------------------------------------------
+// Small dense Rayleigh-Ritz on the device (single CTA kernels), ns <= kMaxDense.
+constexpr int kMaxDense = 1024;
+// Given M and Hs (ns x ns column-major, overwritten), computes ritz (ascending) and
+// Cf = L^-T Q (column-major, ns x ns). status: 0 ok, 1 not SPD, 2 non-finite, 3 no
+// convergence. work: dense_work_elems(ns) doubles.
+long dense_work_elems(int ns);
+cudaError_t dense_rr(double *M, double *Hs, int ns, double *ritz, double *Cf, double *work,
+                     int *status, cudaStream_t st);
+// Symmetric eigensolve (cyclic Jacobi) of A (n x n, column-major, overwritten):
+// eigenvalues ascending in ev, eigenvectors (sign-fixed) in Q. n = *ns_dev when ns_dev is
+// not null (then n <= ns), else ns. work: dense_work_elems(ns).
+cudaError_t dense_syev(double *A, int ns, const int *ns_dev, double *ev, double *Q,
+                       double *work, int *status, cudaStream_t st);
+
+// ---- lanczos.cu -------------------------------------------------------------------
+constexpr int kDotBlocks = 608;
+// r = <x, y> (FP64, deterministic two-level reduction); part: kDotBlocks doubles.
+cudaError_t dot_f64(const double *x, const double *y, long n, double *part, double *r,
+                    cudaStream_t st);
+cudaError_t lanczos_start(double *v, long n, unsigned long long seed, cudaStream_t st);
+// v *= 1/sqrt(*nrm2)
+cudaError_t scale_rsqrt(double *v, long n, const double *nrm2, cudaStream_t st);
+// w = w - alpha[j] v - beta[j-1] vp   (beta term skipped when j == 0); skipped if *stop
+cudaError_t lanczos_orth(double *w, const double *v, const double *vp, long n,
+                         const double *alpha, const double *beta, int j, const int *stop,
+                         cudaStream_t st);
+// beta[j] = sqrt(*nrm2); if beta[j] == 0 or non-finite: *stop = j+1 (once)
+cudaError_t lanczos_beta(double *beta, int j, const double *nrm2, int *stop, cudaStream_t st);
+// vp = v; v = w / beta[j] (skipped if *stop)
+cudaError_t lanczos_next(double *v, double *vp, const double *w, long n, const double *beta,
+                         int j, const int *stop, cudaStream_t st);
+// T (k x k) from alpha, beta, using keff = (*stop ? *stop : k)
+cudaError_t lanczos_tridiag(const double *alpha, const double *beta, int k, const int *stop,
+                            double *T, int *keff, cudaStream_t st);
+// out[0] = theta_min, out[1] = max(1.01 theta_max, theta_max + |beta_keff s|)
+cudaError_t lanczos_bounds_final(const double *ev, const double *Q, const double *beta, int k,
+                                 const int *keff, double *out, cudaStream_t st);
+
+// ---- resid (gram.cu) --------------------------------------------------------------
+// resid[c] = || HX[:,c] - ritz[c] X[:,c] ||_2 (deterministic per-column reduction)
+cudaError_t resid_f64(const double *X, const double *HX, long ld, long nd, int ncols,
+                      const double *ritz, double *resid, cudaStream_t st);
+cudaError_t resid_f32(const float *X, const double *HX, long ld, long nd, int ncols,
+                      const double *ritz, double *resid, cudaStream_t st);
+// flag |= 1 if any of n values is NaN or Inf
+cudaError_t check_finite(const double *a, long n, int *flag, cudaStream_t st);
+
+}  // namespace sparc

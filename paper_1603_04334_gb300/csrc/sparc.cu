@@ -1,0 +1,785 @@
+// sparc.cu -- context, workspaces and the C ABI declared in include/sparc.h.
+//
+// The context owns the device copy of the Hamiltonian of Sec. 3.1 (V_eff, projector
+// tables) and grow-only workspaces; caller blocks (X, HX, work) are never freed here.
+// Host code only validates arguments, sizes workspaces and enqueues kernels; every
+// arithmetic step of the path runs in the kernels of stencil.cu, nonlocal.cu, gram.cu,
+// dense.cu, lanczos.cu and setup.cu.
+#include "sparc.h"
+#include "internal.cuh"
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace sparc;
+
+namespace sparc {
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace sparc
+
+// Per-phase CUDA-event timing on the context stream.
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;          // recycled events
+    std::vector<cudaEvent_t> used;          // events handed out since the last read
+    std::vector<int> phase;                 // phase of each (start, stop) pair in `used`
+    long long count[SPARC_NPHASES] = {0};
+    double ms[SPARC_NPHASES] = {0};
+};
+
+struct sparc_ctx {
+    DevHam H;
+    cudaStream_t st = nullptr;
+    std::string err;
+
+    // owned tables
+    double *V = nullptr;
+    float *Vf = nullptr;
+    int *atom_ptr = nullptr, *idx = nullptr, *ent_atom = nullptr;
+    double *chi = nullptr, *gchi = nullptr;
+    float *chi_f = nullptr, *gchi_f = nullptr;
+    int *uniq_node = nullptr, *uniq_ptr = nullptr, *ent_list = nullptr;
+
+    // grow-only workspaces
+    void *C = nullptr;       size_t C_bytes = 0;     // projection coefficients
+    void *hx = nullptr;      size_t hx_bytes = 0;    // FP64 H Xf
+    void *rotx = nullptr;    size_t rotx_bytes = 0;  // rotated block
+    void *roth = nullptr;    size_t roth_bytes = 0;  // rotated H block (residuals)
+    void *part = nullptr;    size_t part_bytes = 0;  // Gram split-K partials
+    void *dm = nullptr;      size_t dm_bytes = 0;    // M, Hs, Cf, ritz, resid, dense work
+    void *lz = nullptr;      size_t lz_bytes = 0;    // Lanczos vectors and scalars
+    int *flags = nullptr;                            // device status words
+    double *pin = nullptr;                           // pinned host staging (2*1024+16)
+    int *pin_i = nullptr;
+    Profiler prof;
+};
+
+namespace {
+
+constexpr int kMaxLanczos = 64;
+constexpr int kPinDoubles = 2 * kMaxDense + 16;
+
+sparc_status fail(sparc_ctx *c, sparc_status s, const char *fmt, ...)
+    __attribute__((format(printf, 3, 4)));
+
+sparc_status fail(sparc_ctx *c, sparc_status s, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? SPARC_ERR_OOM : SPARC_ERR_CUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define TRY(call)                                                                      \
+    do {                                                                               \
+        sparc_status s_ = (call);                                                      \
+        if (s_ != SPARC_OK) return s_;                                                 \
+    } while (0)
+
+cudaEvent_t prof_event(sparc_ctx *ctx)
+{
+    Profiler &P = ctx->prof;
+    cudaEvent_t e = nullptr;
+    if (!P.pool.empty()) {
+        e = P.pool.back();
+        P.pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return nullptr;
+    }
+    P.used.push_back(e);
+    return e;
+}
+
+// Brackets the launches of one phase with events when profiling is on.
+struct PhaseScope {
+    sparc_ctx *ctx;
+    int ph;
+    bool live = false;
+    PhaseScope(sparc_ctx *c, int p) : ctx(c), ph(p)
+    {
+        if (!ctx->prof.on) return;
+        cudaEvent_t e = prof_event(ctx);
+        if (e && cudaEventRecord(e, ctx->st) == cudaSuccess) live = true;
+    }
+    ~PhaseScope()
+    {
+        if (!live) return;
+        cudaEvent_t e = prof_event(ctx);
+        if (e) {
+            cudaEventRecord(e, ctx->st);
+            ctx->prof.phase.push_back(ph);
+        } else {
+            ctx->prof.used.pop_back();
+        }
+    }
+};
+#define PHASE(p) PhaseScope phase_scope_(ctx, (p))
+
+sparc_status prof_collect(sparc_ctx *ctx)
+{
+    Profiler &P = ctx->prof;
+    if (P.used.empty()) return SPARC_OK;
+    CK(cudaStreamSynchronize(ctx->st));
+    const size_t pairs = P.phase.size();
+    for (size_t q = 0; q < pairs && 2 * q + 1 < P.used.size(); ++q) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, P.used[2 * q], P.used[2 * q + 1]));
+        P.count[P.phase[q]] += 1;
+        P.ms[P.phase[q]] += t;
+    }
+    for (cudaEvent_t e : P.used) P.pool.push_back(e);
+    P.used.clear();
+    P.phase.clear();
+    return SPARC_OK;
+}
+
+sparc_status ensure(sparc_ctx *ctx, void *&p, size_t &cap, size_t bytes)
+{
+    if (bytes <= cap) return SPARC_OK;
+    if (p) CK(cudaFree(p));
+    p = nullptr;
+    cap = 0;
+    CK(cudaMalloc(&p, bytes));
+    cap = bytes;
+    return SPARC_OK;
+}
+
+template <typename T>
+sparc_status dmalloc(sparc_ctx *ctx, T *&p, size_t n)
+{
+    CK(cudaMalloc((void **)&p, sizeof(T) * (n ? n : 1)));
+    return SPARC_OK;
+}
+
+void dfree(void *p)
+{
+    if (p) cudaFree(p);
+}
+
+sparc_status check_block(sparc_ctx *ctx, const void *X, int ncols, long ld, const char *name)
+{
+    if (!X) return fail(ctx, SPARC_ERR_ARG, "%s is NULL", name);
+    if (ncols <= 0) return fail(ctx, SPARC_ERR_ARG, "ncols must be positive (got %d)", ncols);
+    if (ncols > 65535) return fail(ctx, SPARC_ERR_ARG, "ncols %d exceeds 65535", ncols);
+    if (ld < ctx->H.nd)
+        return fail(ctx, SPARC_ERR_ARG, "ld (%ld) must be >= Nd (%ld)", ld, ctx->H.nd);
+    return SPARC_OK;
+}
+
+size_t esize(sparc_dtype t) { return t == SPARC_F32 ? 4 : 8; }
+
+// --- H applications --------------------------------------------------------------------
+sparc_status ensure_C(sparc_ctx *ctx, int ncols)
+{
+    const size_t b = sizeof(double) * 4 * (size_t)(ctx->H.natoms > 0 ? ctx->H.natoms : 1) * ncols;
+    return ensure(ctx, ctx->C, ctx->C_bytes, b);
+}
+
+// out = alpha ((H - shift) Y) - beta Yprev  (Yprev may alias out, may be null)
+sparc_status step_f64(sparc_ctx *ctx, const double *Y, const double *Yprev, double *out, int ncols,
+                      long ld, double alpha, double shift, double beta)
+{
+    const DevHam &H = ctx->H;
+    if (H.natoms > 0) {
+        TRY(ensure_C(ctx, ncols));
+        { PHASE(SPARC_PHASE_PROJECT); CK(project_f64(H, Y, ncols, ld, (double *)ctx->C, ctx->st)); }
+    }
+    { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f64(H, Y, Yprev, out, ncols, ld, alpha, shift, beta, ctx->st)); }
+    if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f64(H, (const double *)ctx->C, out, ncols, ld, alpha, ctx->st)); }
+    return SPARC_OK;
+}
+
+sparc_status step_f32(sparc_ctx *ctx, const float *Y, const float *Yprev, float *out, int ncols,
+                      long ld, double alpha, double shift, double beta)
+{
+    const DevHam &H = ctx->H;
+    if (H.natoms > 0) {
+        TRY(ensure_C(ctx, ncols));
+        { PHASE(SPARC_PHASE_PROJECT); CK(project_f32(H, Y, ncols, ld, (float *)ctx->C, ctx->st)); }
+    }
+    { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f32(H, Y, Yprev, out, ncols, ld, alpha, shift, beta, ctx->st)); }
+    if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f32(H, (const float *)ctx->C, out, ncols, ld, alpha, ctx->st)); }
+    return SPARC_OK;
+}
+
+// FP64 H applied to an FP32 block (result FP64)
+sparc_status apply_f32in_f64(sparc_ctx *ctx, const float *Y, double *out, int ncols, long ld)
+{
+    const DevHam &H = ctx->H;
+    if (H.natoms > 0) {
+        TRY(ensure_C(ctx, ncols));
+        { PHASE(SPARC_PHASE_PROJECT); CK(project_f32in_f64(H, Y, ncols, ld, (double *)ctx->C, ctx->st)); }
+    }
+    { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f32in_f64(H, Y, out, ncols, ld, ctx->st)); }
+    if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f64(H, (const double *)ctx->C, out, ncols, ld, 1.0, ctx->st)); }
+    return SPARC_OK;
+}
+
+template <typename T>
+sparc_status step_t(sparc_ctx *ctx, const T *Y, const T *Yp, T *out, int ncols, long ld,
+                    double alpha, double shift, double beta);
+template <>
+sparc_status step_t<double>(sparc_ctx *ctx, const double *Y, const double *Yp, double *out,
+                            int ncols, long ld, double alpha, double shift, double beta)
+{
+    return step_f64(ctx, Y, Yp, out, ncols, ld, alpha, shift, beta);
+}
+template <>
+sparc_status step_t<float>(sparc_ctx *ctx, const float *Y, const float *Yp, float *out,
+                           int ncols, long ld, double alpha, double shift, double beta)
+{
+    return step_f32(ctx, Y, Yp, out, ncols, ld, alpha, shift, beta);
+}
+
+// --- Chebyshev filter (Algorithm ChebychevFilter, scaled recurrence) -------------------
+sparc_status check_bounds(sparc_ctx *ctx, int degree, double a, double b, double a0)
+{
+    if (degree < 1) return fail(ctx, SPARC_ERR_ARG, "degree must be >= 1 (got %d)", degree);
+    if (!(std::isfinite(a) && std::isfinite(b) && std::isfinite(a0)))
+        return fail(ctx, SPARC_ERR_ARG, "filter bounds must be finite");
+    if (!(a0 < a && a < b))
+        return fail(ctx, SPARC_ERR_ARG, "filter bounds need a0 < a < b (a0=%g a=%g b=%g)", a0, a, b);
+    return SPARC_OK;
+}
+
+// Runs the filter with X as Y_0 and W as the second buffer; *result is the buffer that
+// holds Y_m (X when degree is even, W when odd).
+template <typename T>
+sparc_status filter_impl(sparc_ctx *ctx, T *X, T *W, int ncols, long ld, int m, double a,
+                         double b, double a0, T **result)
+{
+    const double e = (b - a) / 2.0, c = (b + a) / 2.0;
+    const double sigma1 = e / (a0 - c);
+    TRY(step_t<T>(ctx, X, nullptr, W, ncols, ld, sigma1 / e, c, 0.0));
+    T *cur = W, *prev = X;
+    double sigma = sigma1;
+    for (int j = 2; j <= m; ++j) {
+        const double sn = 1.0 / (2.0 / sigma1 - sigma);
+        TRY(step_t<T>(ctx, cur, prev, prev, ncols, ld, 2.0 * sn / e, c, sigma * sn));
+        T *t = cur;
+        cur = prev;
+        prev = t;
+        sigma = sn;
+    }
+    *result = cur;
+    return SPARC_OK;
+}
+
+template <typename T>
+sparc_status copy_block(sparc_ctx *ctx, T *dst, const T *src, int ncols, long ld)
+{
+    if (dst == src) return SPARC_OK;
+    CK(cudaMemcpy2DAsync(dst, ld * sizeof(T), src, ld * sizeof(T), ctx->H.nd * sizeof(T), ncols,
+                         cudaMemcpyDeviceToDevice, ctx->st));
+    return SPARC_OK;
+}
+
+// --- Rayleigh-Ritz --------------------------------------------------------------------
+struct DenseBufs {
+    double *M, *Hs, *Cf, *ritz, *resid, *work;
+};
+
+sparc_status dense_bufs(sparc_ctx *ctx, int ns, DenseBufs &d)
+{
+    const size_t nn = (size_t)ns * ns;
+    const size_t tot = 3 * nn + 2 * (size_t)ns + (size_t)dense_work_elems(ns);
+    TRY(ensure(ctx, ctx->dm, ctx->dm_bytes, tot * sizeof(double)));
+    double *b = (double *)ctx->dm;
+    d.M = b;
+    d.Hs = b + nn;
+    d.Cf = b + 2 * nn;
+    d.ritz = b + 3 * nn;
+    d.resid = d.ritz + ns;
+    d.work = d.resid + ns;
+    return SPARC_OK;
+}
+
+// Projection + eigensolve + rotation of the filtered block Yf. The rotated block is
+// written to `dst` (which may be Yf itself). HX: FP64 workspace (ncols x ld) or null.
+template <typename T>
+sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
+                     double *ritz_host, double *resid_host)
+{
+    const long nd = ctx->H.nd;
+    if (ns > kMaxDense)
+        return fail(ctx, SPARC_ERR_ARG, "ncols %d exceeds the dense eigensolver limit %d", ns,
+                    kMaxDense);
+    if (!ritz_host) return fail(ctx, SPARC_ERR_ARG, "ritz_host is NULL");
+    if (!HX) {
+        TRY(ensure(ctx, ctx->hx, ctx->hx_bytes, sizeof(double) * (size_t)ns * ld));
+        HX = (double *)ctx->hx;
+    }
+    // H Yf in FP64
+    if (sizeof(T) == 8)
+        TRY(step_f64(ctx, (const double *)Yf, nullptr, HX, ns, ld, 1.0, 0.0, 0.0));
+    else
+        TRY(apply_f32in_f64(ctx, (const float *)Yf, HX, ns, ld));
+    // M_s = Yf^T Yf, H_s = Yf^T (H Yf)
+    DenseBufs d;
+    TRY(dense_bufs(ctx, ns, d));
+    TRY(ensure(ctx, ctx->part, ctx->part_bytes, sizeof(double) * (size_t)gram_part_elems(ns, nd)));
+    double *part = (double *)ctx->part;
+    if (sizeof(T) == 8) {
+        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64((const double *)Yf, ld, (const double *)Yf, ld, nd, ns, d.M, part, ctx->st)); }
+        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64((const double *)Yf, ld, HX, ld, nd, ns, d.Hs, part, ctx->st)); }
+    } else {
+        { PHASE(SPARC_PHASE_GRAM); CK(gram_f32_f32((const float *)Yf, ld, (const float *)Yf, ld, nd, ns, d.M, part, ctx->st)); }
+        { PHASE(SPARC_PHASE_GRAM); CK(gram_f32_f64((const float *)Yf, ld, HX, ld, nd, ns, d.Hs, part, ctx->st)); }
+    }
+    { PHASE(SPARC_PHASE_DENSE); CK(dense_rr(d.M, d.Hs, ns, d.ritz, d.Cf, d.work, ctx->flags, ctx->st)); }
+    CK(cudaMemcpyAsync(ctx->pin_i, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    const int status = ctx->pin_i[0];
+    if (status == 1)
+        return fail(ctx, SPARC_ERR_NOT_SPD, "overlap matrix M_s is not positive definite");
+    if (status == 2) return fail(ctx, SPARC_ERR_NONFINITE, "non-finite entries in M_s or H_s");
+    if (status == 3) return fail(ctx, SPARC_ERR_TIMEOUT, "Jacobi eigensolver did not converge");
+    if (status != 0) return fail(ctx, SPARC_ERR_CUDA, "dense eigensolver status %d", status);
+    // rotation X = Yf (L^-T Q)
+    T *xout = dst;
+    if (dst == Yf) {
+        TRY(ensure(ctx, ctx->rotx, ctx->rotx_bytes, sizeof(T) * (size_t)ns * ld));
+        xout = (T *)ctx->rotx;
+    }
+    if (sizeof(T) == 8)
+        { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64((const double *)Yf, ld, nd, ns, d.Cf, (double *)xout, ld, ctx->st)); }
+    else
+        { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f32((const float *)Yf, ld, nd, ns, d.Cf, (float *)xout, ld, ctx->st)); }
+    if (resid_host) {
+        TRY(ensure(ctx, ctx->roth, ctx->roth_bytes, sizeof(double) * (size_t)ns * ld));
+        double *hxr = (double *)ctx->roth;
+        { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64(HX, ld, nd, ns, d.Cf, hxr, ld, ctx->st)); }
+        if (sizeof(T) == 8)
+            { PHASE(SPARC_PHASE_OTHER); CK(resid_f64((const double *)xout, hxr, ld, nd, ns, d.ritz, d.resid, ctx->st)); }
+        else
+            { PHASE(SPARC_PHASE_OTHER); CK(resid_f32((const float *)xout, hxr, ld, nd, ns, d.ritz, d.resid, ctx->st)); }
+    }
+    if (xout != dst) TRY(copy_block<T>(ctx, dst, xout, ns, ld));
+    CK(cudaMemcpyAsync(ctx->pin, d.ritz, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    std::memcpy(ritz_host, ctx->pin, sizeof(double) * ns);
+    if (resid_host) std::memcpy(resid_host, ctx->pin + ns, sizeof(double) * ns);
+    return SPARC_OK;
+}
+
+void lap_weights(int no, double h, double *w)
+{
+    // Eq. (weightsLap), Sec. 3.1.
+    double s = 0.0;
+    for (int q = 1; q <= no; ++q) s += 1.0 / ((double)q * q);
+    w[0] = -s / (h * h);
+    for (int p = 1; p <= kRadius; ++p) {
+        if (p > no) {
+            w[p] = 0.0;
+            continue;
+        }
+        double ratio = 1.0;
+        for (int q = 1; q <= p; ++q) ratio *= (double)(no - q + 1) / (double)(no + q);
+        w[p] = 2.0 * ((p % 2) ? 1.0 : -1.0) / (h * h * (double)p * p) * ratio;
+    }
+}
+
+void free_ctx(sparc_ctx *c)
+{
+    if (!c) return;
+    void *ps[] = {c->V, c->Vf, c->atom_ptr, c->idx, c->ent_atom, c->chi, c->gchi, c->chi_f,
+                  c->gchi_f, c->uniq_node, c->uniq_ptr, c->ent_list, c->C, c->hx, c->rotx,
+                  c->roth, c->part, c->dm, c->lz, c->flags};
+    for (void *p : ps) dfree(p);
+    for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->prof.used) cudaEventDestroy(e);
+    if (c->pin) cudaFreeHost(c->pin);
+    if (c->pin_i) cudaFreeHost(c->pin_i);
+    delete c;
+}
+
+sparc_status build_tables(sparc_ctx *ctx, const sparc_atoms *at)
+{
+    DevHam &H = ctx->H;
+    const int na = at->natoms;
+    H.natoms = na;
+    if (na == 0) return SPARC_OK;
+    double *R = nullptr, *G = nullptr;
+    int *counts = nullptr;
+    TRY(dmalloc(ctx, R, 3 * (size_t)na));
+    TRY(dmalloc(ctx, G, 4 * (size_t)na));
+    TRY(dmalloc(ctx, counts, (size_t)na));
+    CK(cudaMemcpyAsync(R, at->R, sizeof(double) * 3 * na, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(G, at->gamma, sizeof(double) * 4 * na, cudaMemcpyHostToDevice, ctx->st));
+    CK(support_count(H.n0, H.n1, H.n2, H.h, na, R, at->rcut, counts, ctx->st));
+    std::vector<int> hc(na);
+    CK(cudaMemcpyAsync(hc.data(), counts, sizeof(int) * na, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    std::vector<int> ptr(na + 1, 0);
+    long tot = 0;
+    for (int J = 0; J < na; ++J) {
+        tot += hc[J];
+        if (tot > 2000000000L) return fail(ctx, SPARC_ERR_ARG, "too many projector support entries");
+        ptr[J + 1] = (int)tot;
+    }
+    H.nsup = tot;
+    TRY(dmalloc(ctx, ctx->atom_ptr, na + 1));
+    CK(cudaMemcpyAsync(ctx->atom_ptr, ptr.data(), sizeof(int) * (na + 1), cudaMemcpyHostToDevice,
+                       ctx->st));
+    TRY(dmalloc(ctx, ctx->idx, tot));
+    TRY(dmalloc(ctx, ctx->ent_atom, tot));
+    TRY(dmalloc(ctx, ctx->chi, 4 * tot));
+    TRY(dmalloc(ctx, ctx->gchi, 4 * tot));
+    TRY(dmalloc(ctx, ctx->chi_f, 4 * tot));
+    TRY(dmalloc(ctx, ctx->gchi_f, 4 * tot));
+    CK(support_fill(H.n0, H.n1, H.n2, H.h, na, R, G, at->sigma, at->rcut, ctx->atom_ptr, ctx->idx,
+                    ctx->chi, ctx->chi_f, ctx->gchi, ctx->gchi_f, ctx->ent_atom, ctx->st));
+    // inverse map node -> entries
+    const long nd = H.nd;
+    const long nu_max = tot < nd ? tot : nd;
+    int *node_cnt = nullptr, *node_start = nullptr, *cursor = nullptr, *flags = nullptr,
+        *rank = nullptr, *scan_tmp = nullptr;
+    TRY(dmalloc(ctx, node_cnt, nd));
+    TRY(dmalloc(ctx, node_start, nd + 1));
+    TRY(dmalloc(ctx, cursor, nd));
+    TRY(dmalloc(ctx, flags, nd));
+    TRY(dmalloc(ctx, rank, nd + 1));
+    TRY(dmalloc(ctx, scan_tmp, nd / 4096 + 2));
+    TRY(dmalloc(ctx, ctx->ent_list, tot));
+    TRY(dmalloc(ctx, ctx->uniq_node, nu_max));
+    TRY(dmalloc(ctx, ctx->uniq_ptr, nu_max + 1));
+    CK(build_inverse_map(nd, tot, ctx->idx, node_cnt, node_start, cursor, ctx->ent_list, flags,
+                         rank, scan_tmp, ctx->uniq_node, ctx->uniq_ptr, ctx->st));
+    int nuniq = 0;
+    CK(cudaMemcpyAsync(&nuniq, rank + nd, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    H.nuniq = nuniq;
+    for (void *p : {(void *)R, (void *)G, (void *)counts, (void *)node_cnt, (void *)node_start,
+                    (void *)cursor, (void *)flags, (void *)rank, (void *)scan_tmp})
+        CK(cudaFree(p));
+    H.atom_ptr = ctx->atom_ptr;
+    H.idx = ctx->idx;
+    H.chi = ctx->chi;
+    H.chi_f = ctx->chi_f;
+    H.gchi = ctx->gchi;
+    H.gchi_f = ctx->gchi_f;
+    H.ent_atom = ctx->ent_atom;
+    H.uniq_node = ctx->uniq_node;
+    H.uniq_ptr = ctx->uniq_ptr;
+    H.ent_list = ctx->ent_list;
+    return SPARC_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+sparc_status sparc_create(const sparc_grid *grid, const double *veff_host,
+                          const sparc_atoms *atoms, void *cuda_stream, sparc_ctx **out)
+{
+    if (!out) return SPARC_ERR_ARG;
+    *out = nullptr;
+    if (!grid || !atoms) return SPARC_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (grid->n[d] < 1) return SPARC_ERR_ARG;
+    const long nd = (long)grid->n[0] * grid->n[1] * grid->n[2];
+    if (nd > 2000000000L || !(grid->h > 0.0) || grid->radius < 1 || grid->radius > kRadius)
+        return SPARC_ERR_ARG;
+    if (atoms->natoms < 0) return SPARC_ERR_ARG;
+    if (atoms->natoms > 0 && (!atoms->R || !atoms->gamma || !(atoms->sigma > 0.0) ||
+                              !(atoms->rcut >= 0.0)))
+        return SPARC_ERR_ARG;
+    if (!veff_host && atoms->natoms > 0 && (!atoms->Z || !(atoms->rc_erf > 0.0)))
+        return SPARC_ERR_ARG;
+
+    sparc_ctx *ctx = new (std::nothrow) sparc_ctx();
+    if (!ctx) return SPARC_ERR_OOM;
+    ctx->st = (cudaStream_t)cuda_stream;
+    DevHam &H = ctx->H;
+    H.n0 = grid->n[0];
+    H.n1 = grid->n[1];
+    H.n2 = grid->n[2];
+    H.nd = nd;
+    H.h = grid->h;
+    H.radius = grid->radius;
+    H.kscale = 1.0;
+    lap_weights(grid->radius, grid->h, H.w);
+
+    sparc_status s = SPARC_OK;
+    auto run = [&]() -> sparc_status {
+        CK(cudaMallocHost((void **)&ctx->pin, sizeof(double) * kPinDoubles));
+        CK(cudaMallocHost((void **)&ctx->pin_i, sizeof(int) * 16));
+        TRY(dmalloc(ctx, ctx->flags, 16));
+        CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int) * 16, ctx->st));
+        TRY(dmalloc(ctx, ctx->V, nd));
+        TRY(dmalloc(ctx, ctx->Vf, nd));
+        if (veff_host) {
+            CK(cudaMemcpyAsync(ctx->V, veff_host, sizeof(double) * nd, cudaMemcpyHostToDevice,
+                               ctx->st));
+        } else if (atoms->natoms == 0) {
+            CK(cudaMemsetAsync(ctx->V, 0, sizeof(double) * nd, ctx->st));
+        } else {
+            double *R = nullptr, *Z = nullptr;
+            TRY(dmalloc(ctx, R, 3 * (size_t)atoms->natoms));
+            TRY(dmalloc(ctx, Z, (size_t)atoms->natoms));
+            CK(cudaMemcpyAsync(R, atoms->R, sizeof(double) * 3 * atoms->natoms,
+                               cudaMemcpyHostToDevice, ctx->st));
+            CK(cudaMemcpyAsync(Z, atoms->Z, sizeof(double) * atoms->natoms,
+                               cudaMemcpyHostToDevice, ctx->st));
+            CK(build_veff(H.n0, H.n1, H.n2, H.h, atoms->natoms, R, Z, atoms->rc_erf, ctx->V,
+                          ctx->st));
+            CK(cudaStreamSynchronize(ctx->st));
+            CK(cudaFree(R));
+            CK(cudaFree(Z));
+        }
+        CK(to_float(ctx->V, ctx->Vf, nd, ctx->st));
+        H.V = ctx->V;
+        H.Vf = ctx->Vf;
+        TRY(build_tables(ctx, atoms));
+        CK(cudaStreamSynchronize(ctx->st));
+        CK(cudaGetLastError());
+        return SPARC_OK;
+    };
+    s = run();
+    if (s != SPARC_OK) {
+        fprintf(stderr, "sparc_create: %s\n", ctx->err.c_str());
+        free_ctx(ctx);
+        return s;
+    }
+    *out = ctx;
+    return SPARC_OK;
+}
+
+sparc_status sparc_destroy(sparc_ctx *ctx)
+{
+    if (!ctx) return SPARC_OK;
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    free_ctx(ctx);
+    return SPARC_OK;
+}
+
+const char *sparc_last_error(const sparc_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+sparc_status sparc_get_veff(sparc_ctx *ctx, double *veff_host)
+{
+    if (!ctx || !veff_host) return fail(ctx, SPARC_ERR_ARG, "null argument");
+    CK(cudaMemcpyAsync(veff_host, ctx->V, sizeof(double) * ctx->H.nd, cudaMemcpyDeviceToHost,
+                       ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return SPARC_OK;
+}
+
+sparc_status sparc_info(const sparc_ctx *ctx, long *nd, long *nsupport, int *natoms)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    if (nd) *nd = ctx->H.nd;
+    if (nsupport) *nsupport = ctx->H.nsup;
+    if (natoms) *natoms = ctx->H.natoms;
+    return SPARC_OK;
+}
+
+sparc_status sparc_set_kinetic_scale(sparc_ctx *ctx, double kscale)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    if (!std::isfinite(kscale)) return fail(ctx, SPARC_ERR_ARG, "kscale must be finite");
+    ctx->H.kscale = kscale;
+    return SPARC_OK;
+}
+
+sparc_status sparc_apply_H(sparc_ctx *ctx, sparc_dtype dtype, const void *X, void *HX, int ncols,
+                           long ld)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    ctx->err.clear();
+    TRY(check_block(ctx, X, ncols, ld, "X"));
+    TRY(check_block(ctx, HX, ncols, ld, "HX"));
+    if (X == HX) return fail(ctx, SPARC_ERR_ARG, "X and HX must be distinct");
+    if (dtype == SPARC_F64)
+        return step_f64(ctx, (const double *)X, nullptr, (double *)HX, ncols, ld, 1.0, 0.0, 0.0);
+    if (dtype == SPARC_F32)
+        return step_f32(ctx, (const float *)X, nullptr, (float *)HX, ncols, ld, 1.0, 0.0, 0.0);
+    return fail(ctx, SPARC_ERR_ARG, "unknown dtype %d", (int)dtype);
+}
+
+sparc_status sparc_cheb_filter(sparc_ctx *ctx, sparc_dtype dtype, void *X, void *work, int ncols,
+                               long ld, int degree, double a, double b, double a0)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    ctx->err.clear();
+    TRY(check_block(ctx, X, ncols, ld, "X"));
+    TRY(check_block(ctx, work, ncols, ld, "work"));
+    if (X == work) return fail(ctx, SPARC_ERR_ARG, "X and work must be distinct");
+    TRY(check_bounds(ctx, degree, a, b, a0));
+    if (dtype == SPARC_F64) {
+        double *res = nullptr;
+        TRY(filter_impl<double>(ctx, (double *)X, (double *)work, ncols, ld, degree, a, b, a0, &res));
+        return copy_block<double>(ctx, (double *)X, res, ncols, ld);
+    }
+    if (dtype == SPARC_F32) {
+        float *res = nullptr;
+        TRY(filter_impl<float>(ctx, (float *)X, (float *)work, ncols, ld, degree, a, b, a0, &res));
+        return copy_block<float>(ctx, (float *)X, res, ncols, ld);
+    }
+    return fail(ctx, SPARC_ERR_ARG, "unknown dtype %d", (int)dtype);
+}
+
+sparc_status sparc_orth_rr(sparc_ctx *ctx, sparc_dtype dtype, void *Xf, void *HXf_or_null,
+                           int ncols, long ld, double *ritz_host, double *resid_host)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    ctx->err.clear();
+    TRY(check_block(ctx, Xf, ncols, ld, "Xf"));
+    if (dtype == SPARC_F64)
+        return rr_core<double>(ctx, (double *)Xf, (double *)Xf, (double *)HXf_or_null, ncols, ld,
+                               ritz_host, resid_host);
+    if (dtype == SPARC_F32)
+        return rr_core<float>(ctx, (float *)Xf, (float *)Xf, (double *)HXf_or_null, ncols, ld,
+                              ritz_host, resid_host);
+    return fail(ctx, SPARC_ERR_ARG, "unknown dtype %d", (int)dtype);
+}
+
+sparc_status sparc_chefsi_step(sparc_ctx *ctx, sparc_dtype dtype, void *X, void *work, int ncols,
+                               long ld, int degree, double *bounds_inout, double *ritz_host,
+                               double *resid_host)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    ctx->err.clear();
+    if (!bounds_inout) return fail(ctx, SPARC_ERR_ARG, "bounds_inout is NULL");
+    TRY(check_block(ctx, X, ncols, ld, "X"));
+    TRY(check_block(ctx, work, ncols, ld, "work"));
+    if (X == work) return fail(ctx, SPARC_ERR_ARG, "X and work must be distinct");
+    if (!ritz_host) return fail(ctx, SPARC_ERR_ARG, "ritz_host is NULL");
+    const double a = bounds_inout[0], b = bounds_inout[1], a0 = bounds_inout[2];
+    TRY(check_bounds(ctx, degree, a, b, a0));
+    if (ncols > kMaxDense)
+        return fail(ctx, SPARC_ERR_ARG, "ncols %d exceeds the dense eigensolver limit %d", ncols,
+                    kMaxDense);
+    if (dtype == SPARC_F64) {
+        double *res = nullptr;
+        TRY(filter_impl<double>(ctx, (double *)X, (double *)work, ncols, ld, degree, a, b, a0, &res));
+        double *dst = (res == (double *)work) ? (double *)X : (double *)work;
+        TRY(rr_core<double>(ctx, res, dst, nullptr, ncols, ld, ritz_host, resid_host));
+        TRY(copy_block<double>(ctx, (double *)X, dst, ncols, ld));
+    } else if (dtype == SPARC_F32) {
+        float *res = nullptr;
+        TRY(filter_impl<float>(ctx, (float *)X, (float *)work, ncols, ld, degree, a, b, a0, &res));
+        float *dst = (res == (float *)work) ? (float *)X : (float *)work;
+        TRY(rr_core<float>(ctx, res, dst, nullptr, ncols, ld, ritz_host, resid_host));
+        TRY(copy_block<float>(ctx, (float *)X, dst, ncols, ld));
+    } else {
+        return fail(ctx, SPARC_ERR_ARG, "unknown dtype %d", (int)dtype);
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    double lo = ritz_host[0], hi = ritz_host[0];
+    for (int i = 1; i < ncols; ++i) {
+        lo = ritz_host[i] < lo ? ritz_host[i] : lo;
+        hi = ritz_host[i] > hi ? ritz_host[i] : hi;
+    }
+    bounds_inout[0] = hi;
+    bounds_inout[2] = lo;
+    return SPARC_OK;
+}
+
+sparc_status sparc_lanczos_bounds(sparc_ctx *ctx, int ksteps, unsigned long long seed, double *lo,
+                                  double *hi)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    ctx->err.clear();
+    if (!lo || !hi) return fail(ctx, SPARC_ERR_ARG, "lo/hi is NULL");
+    if (ksteps < 1 || ksteps > kMaxLanczos)
+        return fail(ctx, SPARC_ERR_ARG, "ksteps must be in 1..%d (got %d)", kMaxLanczos, ksteps);
+    const long nd = ctx->H.nd;
+    const int K = kMaxLanczos;
+    const size_t nsc = 4 * (size_t)K + 8 + 2 * (size_t)K * K + (size_t)dense_work_elems(K);
+    const size_t tot = 3 * (size_t)nd + (size_t)kDotBlocks + nsc;
+    TRY(ensure(ctx, ctx->lz, ctx->lz_bytes, tot * sizeof(double)));
+    double *v = (double *)ctx->lz, *vp = v + nd, *w = vp + nd, *part = w + nd;
+    double *alpha = part + kDotBlocks, *beta = alpha + K, *nrm2 = beta + K, *outb = nrm2 + 2,
+           *ev = outb + 4, *T = ev + K + 2, *Q = T + (size_t)K * K, *work = Q + (size_t)K * K;
+    int *stop = ctx->flags + 4, *keff = ctx->flags + 5, *status = ctx->flags + 6;
+    CK(cudaMemsetAsync(ctx->flags + 4, 0, sizeof(int) * 3, ctx->st));
+    CK(cudaMemsetAsync(vp, 0, sizeof(double) * nd, ctx->st));
+    CK(cudaMemsetAsync(beta, 0, sizeof(double) * K, ctx->st));
+    { PHASE(SPARC_PHASE_OTHER); CK(lanczos_start(v, nd, seed, ctx->st)); }
+    { PHASE(SPARC_PHASE_OTHER); CK(dot_f64(v, v, nd, part, nrm2, ctx->st)); }
+    { PHASE(SPARC_PHASE_OTHER); CK(scale_rsqrt(v, nd, nrm2, ctx->st)); }
+    for (int j = 0; j < ksteps; ++j) {
+        TRY(step_f64(ctx, v, nullptr, w, 1, nd, 1.0, 0.0, 0.0));
+        { PHASE(SPARC_PHASE_OTHER); CK(dot_f64(w, v, nd, part, alpha + j, ctx->st)); }
+        { PHASE(SPARC_PHASE_OTHER); CK(lanczos_orth(w, v, vp, nd, alpha, beta, j, stop, ctx->st)); }
+        { PHASE(SPARC_PHASE_OTHER); CK(dot_f64(w, w, nd, part, nrm2, ctx->st)); }
+        { PHASE(SPARC_PHASE_OTHER); CK(lanczos_beta(beta, j, nrm2, stop, ctx->st)); }
+        { PHASE(SPARC_PHASE_OTHER); CK(lanczos_next(v, vp, w, nd, beta, j, stop, ctx->st)); }
+    }
+    { PHASE(SPARC_PHASE_OTHER); CK(lanczos_tridiag(alpha, beta, ksteps, stop, T, keff, ctx->st)); }
+    { PHASE(SPARC_PHASE_DENSE); CK(dense_syev(T, ksteps, keff, ev, Q, work, status, ctx->st)); }
+    { PHASE(SPARC_PHASE_OTHER); CK(lanczos_bounds_final(ev, Q, beta, ksteps, keff, outb, ctx->st)); }
+    CK(cudaMemcpyAsync(ctx->pin, outb, sizeof(double) * 2, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(ctx->pin_i, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (ctx->pin_i[0] != 0)
+        return fail(ctx, SPARC_ERR_TIMEOUT, "tridiagonal eigensolve failed (status %d)", ctx->pin_i[0]);
+    *lo = ctx->pin[0];
+    *hi = ctx->pin[1];
+    return SPARC_OK;
+}
+
+sparc_status sparc_profile_enable(sparc_ctx *ctx, int enable)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    if (!enable && ctx->prof.on) {
+        TRY(prof_collect(ctx));
+    }
+    ctx->prof.on = enable != 0;
+    return SPARC_OK;
+}
+
+sparc_status sparc_profile_read(sparc_ctx *ctx, int phase, long long *launches, double *ms)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    if (phase < 0 || phase >= SPARC_NPHASES)
+        return fail(ctx, SPARC_ERR_ARG, "phase %d out of range", phase);
+    TRY(prof_collect(ctx));
+    if (launches) *launches = ctx->prof.count[phase];
+    if (ms) *ms = ctx->prof.ms[phase];
+    return SPARC_OK;
+}
+
+sparc_status sparc_profile_reset(sparc_ctx *ctx)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    TRY(prof_collect(ctx));
+    for (int p = 0; p < SPARC_NPHASES; ++p) {
+        ctx->prof.count[p] = 0;
+        ctx->prof.ms[p] = 0.0;
+    }
+    return SPARC_OK;
+}
+
+sparc_status sparc_launch_count(long long *count)
+{
+    if (!count) return SPARC_ERR_ARG;
+    *count = g_launches.load(std::memory_order_relaxed);
+    return SPARC_OK;
+}
+
+}  // extern "C"
+

@@ -1,0 +1,158 @@
+// stencil.cu -- fused local Hamiltonian + Chebyshev three-term step.
+//
+// One launch computes, for every node p and column c,
+//   out = alpha * ( (-1/2 ks L_h + V_eff - shift) Y )(p) - beta * Yprev(p),
+// with L_h the radius-6 central stencil of Eq. (FD:Laplacian) (weights Eq. weightsLap,
+// Sec. 3.1) and zero-Dirichlet boundaries (values outside the grid are 0, Sec. 3.1).
+// alpha = 1, shift = 0, beta = 0 is the local part of H X; the filter of Algorithm
+// ChebychevFilter (Sec. 3.4) uses alpha = 2 sigma_j / e, shift = c, beta =
+// sigma_{j-1} sigma_j and writes Y_{j+1} in place over Y_{j-1}.
+//
+// Layout: column-major block, column c at c*ld, node p = i + n0 (j + n1 k).
+// Blocking: a CTA owns a BX x BY tile of (i, j) for one column and streams along k
+// (2.5-D blocking). The thread's own z-line lives in a 13-deep register queue
+// (k-6 .. k+6); the current plane with its radius-6 x/y halos is staged in shared
+// memory, so each value is read from global memory once per tile plus halo.
+#include "internal.cuh"
+
+namespace sparc {
+
+StepCoef<double> make_coef(const DevHam &H, double alpha, double shift, double beta)
+{
+    StepCoef<double> c{};
+    const double ks = -0.5 * H.kscale;
+    for (int r = 1; r <= kRadius; ++r) c.w[r] = alpha * ks * H.w[r];
+    c.w[0] = 0.0;
+    c.c0 = alpha * ks * 6.0 * H.w[0] - alpha * shift;
+    c.alpha = alpha;
+    c.beta = beta;
+    return c;
+}
+
+template <typename TC>
+static StepCoef<TC> cast_coef(const StepCoef<double> &d)
+{
+    StepCoef<TC> c;
+    for (int r = 0; r <= kRadius; ++r) c.w[r] = (TC)d.w[r];
+    c.c0 = (TC)d.c0;
+    c.alpha = (TC)d.alpha;
+    c.beta = (TC)d.beta;
+    return c;
+}
+
+template <typename T, typename TO, typename TC, int BX, int BY>
+__global__ void __launch_bounds__(BX *BY)
+k_stencil(const T *__restrict__ Y, const TO *Yprev, TO *out, const TC *__restrict__ V,
+          int n0, int n1, int n2, long ld, int nzc, int zchunk, StepCoef<TC> cf)
+{
+    constexpr int R = kRadius;
+    __shared__ TC s[BY + 2 * R][BX + 2 * R];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+    const int i = i0 + tx, j = j0 + ty;
+    const int col = blockIdx.z / nzc;
+    const int k0 = (blockIdx.z % nzc) * zchunk;
+    const int k1 = min(n2, k0 + zchunk);
+    const long plane = (long)n0 * n1;
+    const T *Yc = Y + (long)col * ld;
+    const TO *Pc = Yprev ? Yprev + (long)col * ld : nullptr;
+    TO *Oc = out + (long)col * ld;
+    const bool act = (i < n0) && (j < n1);
+    const long pij = (long)i + (long)n0 * j;
+
+    TC q[2 * R + 1];
+#pragma unroll
+    for (int t = 0; t < 2 * R + 1; ++t) {
+        const int kk = k0 - R + t;
+        q[t] = (act && kk >= 0 && kk < n2) ? (TC)Yc[pij + (long)kk * plane] : (TC)0;
+    }
+    for (int k = k0; k < k1; ++k) {
+        const long pk = (long)k * plane;
+        __syncthreads();
+        s[ty + R][tx + R] = q[R];
+        if (tx < R) {
+            const int il = i0 - R + tx, ir = i0 + BX + tx;
+            const bool okj = j < n1;
+            s[ty + R][tx] = (okj && il >= 0) ? (TC)Yc[pk + il + (long)n0 * j] : (TC)0;
+            s[ty + R][tx + BX + R] = (okj && ir < n0) ? (TC)Yc[pk + ir + (long)n0 * j] : (TC)0;
+        }
+        if (ty < R) {
+            const int jt = j0 - R + ty, jb = j0 + BY + ty;
+            const bool oki = i < n0;
+            s[ty][tx + R] = (oki && jt >= 0) ? (TC)Yc[pk + i + (long)n0 * jt] : (TC)0;
+            s[ty + BY + R][tx + R] = (oki && jb < n1) ? (TC)Yc[pk + i + (long)n0 * jb] : (TC)0;
+        }
+        __syncthreads();
+        if (act) {
+            const long p = pij + pk;
+            TC acc = (cf.c0 + cf.alpha * V[p]) * q[R];
+#pragma unroll
+            for (int r = 1; r <= R; ++r) {
+                const TC t = (s[ty + R][tx + R + r] + s[ty + R][tx + R - r])
+                           + (s[ty + R + r][tx + R] + s[ty + R - r][tx + R])
+                           + (q[R + r] + q[R - r]);
+                acc += cf.w[r] * t;
+            }
+            if (Pc) acc -= cf.beta * (TC)Pc[p];
+            Oc[p] = (TO)acc;
+        }
+#pragma unroll
+        for (int t = 0; t < 2 * R; ++t) q[t] = q[t + 1];
+        const int kn = k + R + 1;
+        q[2 * R] = (act && kn < n2) ? (TC)Yc[pij + (long)kn * plane] : (TC)0;
+    }
+}
+
+// Picks the number of z-chunks so that small problems still fill the 152 SMs.
+static void z_split(int n2, long tiles, int ncols, int &nzc, int &zchunk)
+{
+    const long want = 152L * 8;
+    long per = tiles * ncols;
+    nzc = 1;
+    while (per * nzc < want && n2 / (nzc * 2) >= 16) nzc *= 2;
+    while ((long)nzc * ncols > 65535) nzc /= 2;
+    if (nzc < 1) nzc = 1;
+    zchunk = (n2 + nzc - 1) / nzc;
+}
+
+template <typename T, typename TO, typename TC>
+static cudaError_t launch(const DevHam &H, const T *Y, const TO *Yprev, TO *out, const TC *V,
+                          int ncols, long ld, const StepCoef<double> &cd, cudaStream_t st)
+{
+    constexpr int BX = 32, BY = 8;
+    if (ncols <= 0) return cudaSuccess;
+    if (ncols > 65535) return cudaErrorInvalidValue;
+    const int gx = (H.n0 + BX - 1) / BX, gy = (H.n1 + BY - 1) / BY;
+    int nzc, zchunk;
+    z_split(H.n2, (long)gx * gy, ncols, nzc, zchunk);
+    dim3 grid(gx, gy, ncols * nzc), block(BX, BY);
+    k_stencil<T, TO, TC, BX, BY><<<grid, block, 0, st>>>(Y, Yprev, out, V, H.n0, H.n1, H.n2,
+                                                         ld, nzc, zchunk, cast_coef<TC>(cd));
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, double *out,
+                        int ncols, long ld, double alpha, double shift, double beta,
+                        cudaStream_t st)
+{
+    return launch<double, double, double>(H, Y, Yprev, out, H.V, ncols, ld,
+                                          make_coef(H, alpha, shift, beta), st);
+}
+
+cudaError_t stencil_f32(const DevHam &H, const float *Y, const float *Yprev, float *out,
+                        int ncols, long ld, double alpha, double shift, double beta,
+                        cudaStream_t st)
+{
+    return launch<float, float, float>(H, Y, Yprev, out, H.Vf, ncols, ld,
+                                       make_coef(H, alpha, shift, beta), st);
+}
+
+cudaError_t stencil_f32in_f64(const DevHam &H, const float *Y, double *out, int ncols,
+                              long ld, cudaStream_t st)
+{
+    return launch<float, double, double>(H, Y, (const double *)nullptr, out, H.V, ncols, ld,
+                                         make_coef(H, 1.0, 0.0, 0.0), st);
+}
+
+}  // namespace sparc

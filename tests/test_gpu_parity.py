@@ -1,0 +1,342 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (stated by the hot path's contract, or derived from it):
+* H X (FP64): max|dHX| / max|HX_oracle| <= 1e-12 (normwise).
+* Chebyshev filter (FP64): degree * 1e-12 normwise (m applications of H, each within the
+  H X bound; the scaled recurrence keeps |Y_j| <= |Y_0| on the filtered components).
+* Ritz values (FP64): <= 1e-10 Ha absolute; Lanczos bounds: <= 1e-10 absolute.
+* FP32 arithmetic: 2e-6 normwise for H X, 1e-5 for the filter output.
+Integer results (support sizes) are compared exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1603_04334_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU-only hosts with -m gpu: skip loudly
+    pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="no CUDA device")]
+
+from paper_1603_04334_gb300 import sparc  # noqa: E402
+
+
+DEV = "cuda:0"
+
+
+def to_dev(X, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(X)).to(DEV, dtype=dtype)
+
+
+def nrm_err(got, ref):
+    return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+def make_ctx(cl, V=None, n=None):
+    return sparc.Context(n if n is not None else cl.n, cl.h, cl.R, cl.Z, cl.gamma, veff=V,
+                         sigma=cl.sigma, rcut=cl.rcut, rc_erf=cl.rc_erf)
+
+
+@pytest.fixture(scope="module")
+def c24():
+    w = synth.preset("cluster24")
+    cl = synth.make_cluster(w, 0)
+    H = oracle.Hamiltonian.from_cluster(cl)
+    ctx = make_ctx(cl, V=H.V)
+    yield w, cl, H, ctx
+    ctx.close()
+
+
+# --------------------------------------------------------------------------------------
+# setup: V_eff and projector tables
+# --------------------------------------------------------------------------------------
+def test_veff_built_on_device_matches_oracle():
+    w = synth.preset("cluster24")
+    cl = synth.make_cluster(w, 1)
+    ctx = make_ctx(cl, V=None)
+    Vg = ctx.get_veff()
+    Vo = oracle.veff(cl.n, cl.h, cl.R, cl.Z, cl.rc_erf)
+    assert nrm_err(Vg, Vo) <= 1e-14
+    ctx.close()
+
+
+@pytest.mark.parametrize("name,seed", [("cluster24", 0), ("cluster24", 3), ("cluster96", 0)])
+def test_projector_support_size_exact(name, seed):
+    w = synth.preset(name)
+    cl = synth.make_cluster(w, seed)
+    P = oracle.projectors(cl.n, cl.h, cl.R, cl.sigma, cl.rcut)
+    ctx = make_ctx(cl, V=np.zeros(w.nd))
+    info = ctx.info()
+    assert info["natoms"] == cl.natoms
+    assert info["nsupport"] == int(P.atom_ptr[-1])
+    ctx.close()
+
+
+# --------------------------------------------------------------------------------------
+# H X
+# --------------------------------------------------------------------------------------
+def test_apply_H_f64_cluster24(c24):
+    w, cl, H, ctx = c24
+    X = synth.initial_block(2, w.nd, w.ns)
+    ref = H.apply(X)
+    Xd = to_dev(X)
+    HXd = torch.empty_like(Xd)
+    ctx.apply_H(Xd, HXd)
+    torch.cuda.synchronize()
+    assert nrm_err(HXd.cpu().numpy(), ref) <= 1e-12
+    # deterministic: a second call is bitwise identical
+    HX2 = torch.empty_like(Xd)
+    ctx.apply_H(Xd, HX2)
+    assert torch.equal(HXd, HX2)
+
+
+@pytest.mark.parametrize("n3,natoms", [((37, 29, 23), 3), ((5, 7, 9), 0), ((13, 13, 13), 1),
+                                       ((70, 9, 33), 2)])
+def test_apply_H_f64_ragged_grids(n3, natoms):
+    # several 32 x 8 tiles with ragged tails in x and y, grids smaller than the radius-6
+    # halo, and the no-atom case
+    h = 0.45
+    rng = np.random.default_rng(sum(n3))
+    R = np.array([[rng.uniform(0, (n3[0] - 1) * h), rng.uniform(0, (n3[1] - 1) * h),
+                   rng.uniform(0, (n3[2] - 1) * h)] for _ in range(natoms)]).reshape(-1, 3)
+    gamma = rng.uniform(-2, 2, (natoms, 4))
+    nd = n3[0] * n3[1] * n3[2]
+    V = rng.uniform(-3, 1, nd)
+    H = oracle.Hamiltonian(n3, h, V, R if natoms else None, gamma if natoms else None)
+    ctx = sparc.Context(n3, h, R if natoms else None, None, gamma if natoms else None, veff=V)
+    ld = nd + 5                                       # padded leading dimension
+    X = rng.uniform(-0.5, 0.5, (3, ld))
+    X[:, nd:] = 0.0
+    ref = H.apply(X[:, :nd].copy())
+    Xd = to_dev(X)
+    HXd = torch.full_like(Xd, 7.0)
+    ctx.apply_H(Xd, HXd)
+    got = HXd.cpu().numpy()
+    assert nrm_err(got[:, :nd], ref) <= 1e-12
+    assert np.all(got[:, nd:] == 7.0)                 # padding rows untouched
+    ctx.close()
+
+
+def test_apply_H_f32(c24):
+    w, cl, H, ctx = c24
+    X = synth.initial_block(5, w.nd, 4)
+    ref = H.apply(X)
+    Xd = to_dev(X, torch.float32)
+    HXd = torch.empty_like(Xd)
+    ctx.apply_H(Xd, HXd)
+    got = HXd.double().cpu().numpy()
+    ref32 = H.apply(Xd.double().cpu().numpy())       # same rounded input, FP64 oracle
+    assert nrm_err(got, ref32) <= 2e-6
+    assert nrm_err(got, ref) <= 1e-5
+
+
+def test_apply_H_single_column(c24):
+    w, cl, H, ctx = c24
+    X = synth.initial_block(8, w.nd, 1)
+    Xd = to_dev(X)
+    HXd = torch.empty_like(Xd)
+    ctx.apply_H(Xd, HXd)
+    assert nrm_err(HXd.cpu().numpy(), H.apply(X)) <= 1e-12
+
+
+# --------------------------------------------------------------------------------------
+# Chebyshev filter
+# --------------------------------------------------------------------------------------
+@pytest.mark.parametrize("degree", [1, 2, 10])
+def test_cheb_filter_f64(c24, degree):
+    w, cl, H, ctx = c24
+    X = synth.initial_block(3, w.nd, w.ns)
+    a0, a, b = -3.3, 7.6, 40.1
+    ref = H.cheb_filter(X, degree, a, b, a0)
+    Xd = to_dev(X)
+    Wd = torch.empty_like(Xd)
+    ctx.cheb_filter(Xd, Wd, degree, a, b, a0)
+    assert nrm_err(Xd.cpu().numpy(), ref) <= degree * 1e-12
+
+
+def test_cheb_filter_f32(c24):
+    w, cl, H, ctx = c24
+    X = synth.initial_block(3, w.nd, 6)
+    a0, a, b = -3.3, 7.6, 40.1
+    Xd = to_dev(X, torch.float32)
+    ref = H.cheb_filter(Xd.double().cpu().numpy(), 10, a, b, a0)
+    Wd = torch.empty_like(Xd)
+    ctx.cheb_filter(Xd, Wd, 10, a, b, a0)
+    assert nrm_err(Xd.double().cpu().numpy(), ref) <= 1e-5
+
+
+def _cheb(m, x):
+    x = np.asarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    ins = np.abs(x) <= 1
+    out[ins] = np.cos(m * np.arccos(x[ins]))
+    out[~ins] = np.cosh(m * np.arccosh(np.abs(x[~ins]))) * np.sign(x[~ins]) ** m
+    return out
+
+
+def test_cheb_filter_diagonal_closed_form():
+    # kscale = 0 and no atoms: H = diag(V); the filter must equal the scalar Chebyshev value.
+    n, m = 20, 12
+    rng = np.random.default_rng(4)
+    a0, a, b = -4.0, 1.5, 30.0
+    V = rng.uniform(a0 - 0.3, b + 0.1, n ** 3)
+    ctx = sparc.Context(n, 0.5, veff=V)
+    ctx.set_kinetic_scale(0.0)
+    X = rng.uniform(-0.5, 0.5, (2, n ** 3))
+    Xd = to_dev(X)
+    ctx.cheb_filter(Xd, torch.empty_like(Xd), m, a, b, a0)
+    e, c = (b - a) / 2, (b + a) / 2
+    p = _cheb(m, (V - c) / e) / _cheb(m, np.array([(a0 - c) / e]))[0]
+    ref = X * p[None, :]
+    got = Xd.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 1e-13 * np.maximum(np.abs(ref), 1e-3 * np.max(np.abs(ref))))
+    ctx.close()
+
+
+def test_cheb_filter_rejects_bad_bounds(c24):
+    w, cl, H, ctx = c24
+    Xd = to_dev(synth.initial_block(0, w.nd, 2))
+    before = Xd.clone()
+    with pytest.raises(sparc.SparcError) as ei:
+        ctx.cheb_filter(Xd, torch.empty_like(Xd), 5, 1.0, 0.5, -1.0)
+    assert ei.value.status == sparc.SPARC_ERR_ARG
+    with pytest.raises(sparc.SparcError):
+        ctx.cheb_filter(Xd, torch.empty_like(Xd), 0, 1.0, 5.0, -1.0)
+    assert torch.equal(Xd, before)
+
+
+# --------------------------------------------------------------------------------------
+# Lanczos bounds
+# --------------------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [0, 7])
+def test_lanczos_bounds(c24, seed):
+    w, cl, H, ctx = c24
+    lo, hi = ctx.lanczos_bounds(10, seed)
+    olo, ohi, _ = H.lanczos_bounds(10, seed)
+    assert abs(lo - olo) <= 1e-10 and abs(hi - ohi) <= 1e-10
+
+
+def test_lanczos_early_stop_tiny_grid():
+    # Nd = 8 < k: the Krylov space is exhausted and beta reaches (numerically) zero.
+    n = 2
+    V = np.array([-1.0, 0.5, 2.0, 3.0, -0.25, 1.0, 4.0, 0.0])
+    H = oracle.Hamiltonian(n, 0.5, V)
+    ctx = sparc.Context(n, 0.5, veff=V)
+    lo, hi = ctx.lanczos_bounds(12, 3)
+    olo, ohi, _ = H.lanczos_bounds(12, 3)
+    ev = np.linalg.eigvalsh(H.dense())
+    assert abs(lo - olo) <= 1e-9 and abs(hi - ohi) <= 1e-9
+    assert lo == pytest.approx(ev[0], abs=1e-8) and hi >= ev[-1] - 1e-12
+    ctx.close()
+
+
+# --------------------------------------------------------------------------------------
+# Rayleigh-Ritz and CheFSI
+# --------------------------------------------------------------------------------------
+def _align(X, Xref):
+    s = np.sign(np.sum(X * Xref, axis=1))
+    s[s == 0] = 1
+    return X * s[:, None]
+
+
+def test_orth_rr_f64(c24):
+    w, cl, H, ctx = c24
+    X0 = synth.initial_block(6, w.nd, w.ns)
+    Yf = H.cheb_filter(X0, 10, 7.6, 40.1, -3.3)
+    Xo, HXo, lam, res, _ = oracle.orth_rr(Yf, H.apply(Yf))
+    Yd = to_dev(Yf)
+    ritz, resid = ctx.orth_rr(Yd)
+    assert np.max(np.abs(ritz - lam)) <= 1e-10
+    assert np.max(np.abs(resid - res)) <= 1e-9
+    Xg = Yd.cpu().numpy()
+    assert np.max(np.abs(_align(Xg, Xo) - Xo)) <= 1e-9
+    assert np.max(np.abs(Xg @ Xg.T - np.eye(w.ns))) <= 1e-12
+
+
+def test_orth_rr_not_spd_leaves_block(c24):
+    w, cl, H, ctx = c24
+    X = synth.initial_block(6, w.nd, 3)
+    X[1] = X[0]                                   # rank-deficient block
+    Xd = to_dev(X)
+    before = Xd.clone()
+    with pytest.raises(sparc.SparcError) as ei:
+        ctx.orth_rr(Xd)
+    assert ei.value.status == sparc.SPARC_ERR_NOT_SPD
+    assert torch.equal(Xd, before)
+
+
+def test_orth_rr_nonfinite(c24):
+    w, cl, H, ctx = c24
+    X = synth.initial_block(6, w.nd, 3)
+    X[2, 100] = np.nan
+    Xd = to_dev(X)
+    with pytest.raises(sparc.SparcError) as ei:
+        ctx.orth_rr(Xd)
+    assert ei.value.status == sparc.SPARC_ERR_NONFINITE
+
+
+def test_chefsi_loop_matches_oracle_cluster24(c24):
+    w, cl, H, ctx = c24
+    X0 = synth.initial_block(1, w.nd, w.ns)
+    lo, hi = ctx.lanczos_bounds(w.lanczos_k, 0)
+    olo, ohi, _ = H.lanczos_bounds(w.lanczos_k, 0)
+    b_g = sparc.first_bounds(lo, hi)
+    b_o = oracle.chefsi_first_bounds(olo, ohi)
+    Xd = to_dev(X0)
+    Wd = torch.empty_like(Xd)
+    Xo = X0.copy()
+    for it in range(w.iters):
+        ritz, resid, b_g = ctx.chefsi_step(Xd, Wd, w.degree, b_g)
+        Xo, ritz_o, res_o, b_o = oracle.chefsi_step(H, Xo, w.degree, b_o)
+        assert np.max(np.abs(ritz - ritz_o)) <= 1e-10, (it, ritz - ritz_o)
+        assert np.max(np.abs(np.array(b_g) - np.array(b_o))) <= 1e-10
+    Xg = Xd.cpu().numpy()
+    assert np.max(np.abs(Xg @ Xg.T - np.eye(w.ns))) <= 1e-12
+    # converged lower states agree with the oracle's vectors
+    k = w.ns - 2
+    assert np.max(np.abs(_align(Xg[:k], Xo[:k]) - Xo[:k])) <= 1e-8
+
+
+def test_chefsi_dense_12cubed_eigenvalues():
+    w = synth.preset("cluster12")
+    cl = synth.make_cluster(w, 7)
+    H = oracle.Hamiltonian.from_cluster(cl)
+    ev = np.linalg.eigvalsh(H.dense())
+    ctx = make_ctx(cl, V=H.V)
+    Xd = to_dev(synth.initial_block(4, w.nd, w.ns))
+    Wd = torch.empty_like(Xd)
+    lo, hi = ctx.lanczos_bounds(10, 0)
+    b = sparc.first_bounds(lo, hi)
+    for it in range(40):
+        ritz, resid, b = ctx.chefsi_step(Xd, Wd, 12, b)
+        if np.max(resid) <= 1e-9:
+            break
+    k = w.ns - 2
+    assert np.max(np.abs(ritz[:k] - ev[:k])) <= 1e-10
+    ctx.close()
+
+
+def test_mixed_precision_ritz_within_1e5(c24):
+    # FP32 filter + FP64 Rayleigh-Ritz, then one FP64 refinement sweep: Ritz values of the
+    # converged states within 1e-5 Ha of the FP64 run.
+    w, cl, H, ctx = c24
+    X0 = synth.initial_block(1, w.nd, w.ns)
+    lo, hi = ctx.lanczos_bounds(10, 0)
+    b64 = sparc.first_bounds(lo, hi)
+    X64 = to_dev(X0)
+    W64 = torch.empty_like(X64)
+    for it in range(w.iters):
+        r64, _, b64 = ctx.chefsi_step(X64, W64, w.degree, b64)
+    b32 = sparc.first_bounds(lo, hi)
+    X32 = to_dev(X0, torch.float32)
+    W32 = torch.empty_like(X32)
+    for it in range(w.iters):
+        r32, _, b32 = ctx.chefsi_step(X32, W32, w.degree, b32)
+    Xr = X32.double()
+    rr, res, _ = ctx.chefsi_step(Xr, torch.empty_like(Xr), w.degree, b32)
+    k = w.ns - 2
+    assert np.max(np.abs(rr[:k] - r64[:k])) <= 1e-5
