@@ -139,6 +139,17 @@ sparc_status sparc_cheb_filter(sparc_ctx *ctx, sparc_dtype dtype, void *X, void 
 sparc_status sparc_orth_rr(sparc_ctx *ctx, sparc_dtype dtype, void *Xf, void *HXf_or_null,
                            int ncols, long ld, double *ritz_host, double *resid_host);
 
+/* Projection contraction of Sec. 3.4 (the relations after Eq.
+ * SubspaceGeneralizedEigenproblem): G = A^T B over the context's Nd rows, e.g.
+ * M_s = Psi_f^T Psi_f or H_s = Psi_f^T (H Psi_f). A, B: device blocks (ncols columns,
+ * leading dimension ld) of types (dtype_a, dtype_b) = (F64, F64), (F32, F32) or
+ * (F32, F64); products and sums are FP64. G: device, ncols x ncols, column-major FP64,
+ * overwritten. The row slices are summed in a fixed order, so repeated calls are
+ * bitwise identical. Uses context workspace (allocated on first use or growth).
+ * Asynchronous on the context stream. */
+sparc_status sparc_gram(sparc_ctx *ctx, sparc_dtype dtype_a, const void *A, sparc_dtype dtype_b,
+                        const void *B, int ncols, long ld, double *G);
+
 /* One CheFSI iteration, Sec. 3.4: sparc_cheb_filter with bounds_inout = [a, b, a0],
  * then sparc_orth_rr. Afterwards bounds_inout is updated for the next iteration:
  * a = largest Ritz value, a0 = smallest Ritz value, b unchanged. work as in

@@ -18,6 +18,7 @@ struct DevHam {
     double h = 0;
     int radius = 6;
     double kscale = 1.0;
+    int f64_df = 1;  // FP64 stencil in FP32-pair arithmetic (stencil_df.cu) instead of FP64 FMA
     double w[kRadius + 1] = {0};  // Laplacian weights w_p (1/h^2 included), zero beyond radius
 
     const double *V = nullptr;   // V_eff, Nd
@@ -60,6 +61,10 @@ cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, d
 cudaError_t stencil_f32(const DevHam &H, const float *Y, const float *Yprev, float *out,
                         int ncols, long ld, double alpha, double shift, double beta,
                         cudaStream_t st);
+cudaError_t stencil_f64_df(const DevHam &H, const double *Y, const double *Yprev, double *out,
+                           int ncols, long ld, double alpha, double shift, double beta,
+                           cudaStream_t st);
+void stencil_z_split(int n2, long tiles, int ncols, int &nzc, int &zchunk);
 // FP64 arithmetic on an FP32 block (H applied to FP32 Ritz blocks in FP64).
 cudaError_t stencil_f32in_f64(const DevHam &H, const float *Y, double *out, int ncols,
                               long ld, cudaStream_t st);
@@ -101,13 +106,20 @@ cudaError_t to_float(const double *in, float *out, long n, cudaStream_t st);
 // ---- gram.cu --------------------------------------------------------------------
 // G (ns x ns, column-major, FP64) = A^T B over nd rows; A, B column-major with lda/ldb.
 // part: workspace of gram_part_elems(ns, nd) doubles.
+// sym: A^T B is known to be symmetric (M_s, H_s); only tiles i0 <= j0 are computed.
 long gram_part_elems(int ns, long nd);
 cudaError_t gram_f64(const double *A, long lda, const double *B, long ldb, long nd, int ns,
-                     double *G, double *part, cudaStream_t st);
+                     double *G, double *part, cudaStream_t st, bool sym = false);
 cudaError_t gram_f32_f32(const float *A, long lda, const float *B, long ldb, long nd, int ns,
-                         double *G, double *part, cudaStream_t st);
+                         double *G, double *part, cudaStream_t st, bool sym = false);
 cudaError_t gram_f32_f64(const float *A, long lda, const double *B, long ldb, long nd, int ns,
-                         double *G, double *part, cudaStream_t st);
+                         double *G, double *part, cudaStream_t st, bool sym = false);
+// gram_df.cu: FP32-pair kernels behind the entry points above and below.
+template <typename TA, typename TB>
+cudaError_t gram_df_launch(const TA *A, long lda, const TB *B, long ldb, long nd, int ns,
+                           double *G, double *part, int nsplit, bool sym, cudaStream_t st);
+cudaError_t rotate_f64_df(const double *A, long lda, long nd, int ns, const double *Q, double *out,
+                          long ldo, cudaStream_t st);
 // out (nd x ns, ldo) = A (nd x ns, lda) Q (ns x ns, column-major FP64)
 cudaError_t rotate_f64(const double *A, long lda, long nd, int ns, const double *Q,
                        double *out, long ldo, cudaStream_t st);

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -340,11 +341,11 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
     TRY(ensure(ctx, ctx->part, ctx->part_bytes, sizeof(double) * (size_t)gram_part_elems(ns, nd)));
     double *part = (double *)ctx->part;
     if (sizeof(T) == 8) {
-        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64((const double *)Yf, ld, (const double *)Yf, ld, nd, ns, d.M, part, ctx->st)); }
-        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64((const double *)Yf, ld, HX, ld, nd, ns, d.Hs, part, ctx->st)); }
+        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64((const double *)Yf, ld, (const double *)Yf, ld, nd, ns, d.M, part, ctx->st, true)); }
+        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64((const double *)Yf, ld, HX, ld, nd, ns, d.Hs, part, ctx->st, true)); }
     } else {
-        { PHASE(SPARC_PHASE_GRAM); CK(gram_f32_f32((const float *)Yf, ld, (const float *)Yf, ld, nd, ns, d.M, part, ctx->st)); }
-        { PHASE(SPARC_PHASE_GRAM); CK(gram_f32_f64((const float *)Yf, ld, HX, ld, nd, ns, d.Hs, part, ctx->st)); }
+        { PHASE(SPARC_PHASE_GRAM); CK(gram_f32_f32((const float *)Yf, ld, (const float *)Yf, ld, nd, ns, d.M, part, ctx->st, true)); }
+        { PHASE(SPARC_PHASE_GRAM); CK(gram_f32_f64((const float *)Yf, ld, HX, ld, nd, ns, d.Hs, part, ctx->st, true)); }
     }
     { PHASE(SPARC_PHASE_DENSE); CK(dense_rr(d.M, d.Hs, ns, d.ritz, d.Cf, d.work, ctx->flags, ctx->st)); }
     CK(cudaMemcpyAsync(ctx->pin_i, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
@@ -521,6 +522,10 @@ sparc_status sparc_create(const sparc_grid *grid, const double *veff_host,
     H.h = grid->h;
     H.radius = grid->radius;
     H.kscale = 1.0;
+    {
+        const char *m = getenv("SPARC_F64_STENCIL");
+        H.f64_df = (m && strcmp(m, "native") == 0) ? 0 : 1;
+    }
     lap_weights(grid->radius, grid->h, H.w);
 
     sparc_status s = SPARC_OK;
@@ -654,6 +659,31 @@ sparc_status sparc_orth_rr(sparc_ctx *ctx, sparc_dtype dtype, void *Xf, void *HX
         return rr_core<float>(ctx, (float *)Xf, (float *)Xf, (double *)HXf_or_null, ncols, ld,
                               ritz_host, resid_host);
     return fail(ctx, SPARC_ERR_ARG, "unknown dtype %d", (int)dtype);
+}
+
+sparc_status sparc_gram(sparc_ctx *ctx, sparc_dtype dtype_a, const void *A, sparc_dtype dtype_b,
+                        const void *B, int ncols, long ld, double *G)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    ctx->err.clear();
+    TRY(check_block(ctx, A, ncols, ld, "A"));
+    TRY(check_block(ctx, B, ncols, ld, "B"));
+    if (!G) return fail(ctx, SPARC_ERR_ARG, "G is NULL");
+    const long nd = ctx->H.nd;
+    TRY(ensure(ctx, ctx->part, ctx->part_bytes,
+               sizeof(double) * (size_t)gram_part_elems(ncols, nd)));
+    double *part = (double *)ctx->part;
+    PHASE(SPARC_PHASE_GRAM);
+    if (dtype_a == SPARC_F64 && dtype_b == SPARC_F64)
+        CK(gram_f64((const double *)A, ld, (const double *)B, ld, nd, ncols, G, part, ctx->st));
+    else if (dtype_a == SPARC_F32 && dtype_b == SPARC_F32)
+        CK(gram_f32_f32((const float *)A, ld, (const float *)B, ld, nd, ncols, G, part, ctx->st));
+    else if (dtype_a == SPARC_F32 && dtype_b == SPARC_F64)
+        CK(gram_f32_f64((const float *)A, ld, (const double *)B, ld, nd, ncols, G, part, ctx->st));
+    else
+        return fail(ctx, SPARC_ERR_ARG, "unsupported dtype pair (%d, %d)", (int)dtype_a,
+                    (int)dtype_b);
+    return SPARC_OK;
 }
 
 sparc_status sparc_chefsi_step(sparc_ctx *ctx, sparc_dtype dtype, void *X, void *work, int ncols,

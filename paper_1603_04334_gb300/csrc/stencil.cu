@@ -104,7 +104,7 @@ k_stencil(const T *__restrict__ Y, const TO *Yprev, TO *out, const TC *__restric
 }
 
 // Picks the number of z-chunks so that small problems still fill the 152 SMs.
-static void z_split(int n2, long tiles, int ncols, int &nzc, int &zchunk)
+void stencil_z_split(int n2, long tiles, int ncols, int &nzc, int &zchunk)
 {
     const long want = 152L * 8;
     long per = tiles * ncols;
@@ -124,7 +124,7 @@ static cudaError_t launch(const DevHam &H, const T *Y, const TO *Yprev, TO *out,
     if (ncols > 65535) return cudaErrorInvalidValue;
     const int gx = (H.n0 + BX - 1) / BX, gy = (H.n1 + BY - 1) / BY;
     int nzc, zchunk;
-    z_split(H.n2, (long)gx * gy, ncols, nzc, zchunk);
+    stencil_z_split(H.n2, (long)gx * gy, ncols, nzc, zchunk);
     dim3 grid(gx, gy, ncols * nzc), block(BX, BY);
     k_stencil<T, TO, TC, BX, BY><<<grid, block, 0, st>>>(Y, Yprev, out, V, H.n0, H.n1, H.n2,
                                                          ld, nzc, zchunk, cast_coef<TC>(cd));
@@ -136,6 +136,8 @@ cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, d
                         int ncols, long ld, double alpha, double shift, double beta,
                         cudaStream_t st)
 {
+    if (H.f64_df)
+        return stencil_f64_df(H, Y, Yprev, out, ncols, ld, alpha, shift, beta, st);
     return launch<double, double, double>(H, Y, Yprev, out, H.V, ncols, ld,
                                           make_coef(H, alpha, shift, beta), st);
 }

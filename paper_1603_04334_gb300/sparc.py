@@ -34,7 +34,8 @@ _STATUS = {SPARC_ERR_ARG: "SPARC_ERR_ARG", SPARC_ERR_OOM: "SPARC_ERR_OOM",
 # Entry points of include/sparc.h (checked by the test suite against the header).
 EXPORTS = ("sparc_create", "sparc_destroy", "sparc_last_error", "sparc_get_veff", "sparc_info",
            "sparc_set_kinetic_scale", "sparc_apply_H", "sparc_lanczos_bounds",
-           "sparc_cheb_filter", "sparc_orth_rr", "sparc_chefsi_step", "sparc_profile_enable",
+           "sparc_cheb_filter", "sparc_orth_rr", "sparc_gram", "sparc_chefsi_step",
+           "sparc_profile_enable",
            "sparc_profile_read", "sparc_profile_reset", "sparc_launch_count")
 
 PHASES = ("stencil", "project", "scatter", "gram", "dense", "rotate", "other")
@@ -88,6 +89,7 @@ def load(build_if_missing: bool = True):
                                     C.c_double]
     L.sparc_orth_rr.argtypes = [vp, ip, vp, vp, ip, C.c_long, dp, dp]
     L.sparc_chefsi_step.argtypes = [vp, ip, vp, vp, ip, C.c_long, ip, dp, dp, dp]
+    L.sparc_gram.argtypes = [vp, ip, vp, ip, vp, ip, C.c_long, vp]
     L.sparc_profile_enable.argtypes = [vp, ip]
     L.sparc_profile_read.argtypes = [vp, ip, C.POINTER(C.c_longlong), dp]
     L.sparc_profile_reset.argtypes = [vp]
@@ -245,6 +247,20 @@ class Context:
             ritz.ctypes.data_as(C.POINTER(C.c_double)),
             resid.ctypes.data_as(C.POINTER(C.c_double)) if resid is not None else None))
         return ritz, resid
+
+    def gram(self, A, B, G=None):
+        """G = A^T B (FP64, ncols x ncols, column-major: G[j, i] in torch indexing is
+        entry (i, j)); returns the device tensor G."""
+        import torch
+        ncols, ld = _block(A, "A")
+        if B.shape != A.shape:
+            raise ValueError("A and B must have the same shape")
+        if G is None:
+            G = torch.empty((ncols, ncols), dtype=torch.float64, device=A.device)
+        self._check(self._L.sparc_gram(self._h, _dtype_code(A), C.c_void_p(A.data_ptr()),
+                                       _dtype_code(B), C.c_void_p(B.data_ptr()), ncols, ld,
+                                       C.c_void_p(G.data_ptr())))
+        return G
 
     def chefsi_step(self, X, work, degree: int, bounds: Sequence[float],
                     want_resid: bool = True):
