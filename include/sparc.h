@@ -186,6 +186,26 @@ sparc_status sparc_profile_reset(sparc_ctx *ctx);
 /* Number of kernels this library has launched in the calling process (all contexts). */
 sparc_status sparc_launch_count(long long *count);
 
+/* ---- allocation-free variant ---------------------------------------------------- */
+
+/* G = A^T B in FP64 without allocating any memory (the paper has no counterpart; it is
+ * a service for callers that cannot call cudaMalloc where they call this: code inside a
+ * CUDA stream capture, loops that forbid allocation after start-up, or hosts that hand
+ * in buffers from their own pool). Same result as sparc_gram for FP64 inputs, up to the
+ * order of the row-slice sums. A, B: device, nd rows x ncols columns, column-major,
+ * leading dimension ld >= nd. G: device, ncols x ncols, column-major, overwritten.
+ * Enqueued on `cuda_stream` (a cudaStream_t; NULL = legacy default stream); needs no
+ * context. The row-slice partial sums live in a fixed 16 MiB __device__ array that every
+ * GPU loading the library keeps until exit: ncols^2 must not exceed 2^21 (any
+ * ncols <= 1024 fits), else SPARC_ERR_ARG. The first call on a device looks up that
+ * array's address (cudaGetSymbolAddress) with the device current; make it before any
+ * stream capture. All calls share the array: calls that overlap on the GPU race on it
+ * and must be serialised. Each call overwrites every partial it reads, so no clearing is
+ * needed. Returns SPARC_ERR_ARG for NULL pointers or bad sizes, SPARC_ERR_CUDA if the
+ * lookup or the launch fails. */
+sparc_status sparc_gram_noalloc(const double *A, const double *B, long nd, int ncols, long ld,
+                                double *G, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,6 +46,14 @@ cudaError_t gram_f64(const double *A, long lda, const double *B, long ldb, long 
 {
     return gram<double, double>(A, lda, B, ldb, nd, ns, G, part, st, sym);
 }
+int gram_default_splits(int ns, long nd) { return gram_splits(ns, nd); }
+
+cudaError_t gram_f64_nsplit(const double *A, long lda, const double *B, long ldb, long nd, int ns,
+                            double *G, double *part, int nsplit, cudaStream_t st)
+{
+    return gram_df_launch<double, double>(A, lda, B, ldb, nd, ns, G, part, nsplit, false, st);
+}
+
 cudaError_t gram_f32_f32(const float *A, long lda, const float *B, long ldb, long nd, int ns,
                          double *G, double *part, cudaStream_t st, bool sym)
 {

@@ -120,6 +120,10 @@ cudaError_t gram_df_launch(const TA *A, long lda, const TB *B, long ldb, long nd
                            double *G, double *part, int nsplit, bool sym, cudaStream_t st);
 cudaError_t rotate_f64_df(const double *A, long lda, long nd, int ns, const double *Q, double *out,
                           long ldo, cudaStream_t st);
+// FP64 Gram with a caller-chosen number of row slices (part: nsplit * ns * ns doubles).
+int gram_default_splits(int ns, long nd);
+cudaError_t gram_f64_nsplit(const double *A, long lda, const double *B, long ldb, long nd, int ns,
+                            double *G, double *part, int nsplit, cudaStream_t st);
 // out (nd x ns, ldo) = A (nd x ns, lda) Q (ns x ns, column-major FP64)
 cudaError_t rotate_f64(const double *A, long lda, long nd, int ns, const double *Q,
                        double *out, long ldo, cudaStream_t st);

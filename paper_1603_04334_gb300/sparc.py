@@ -36,7 +36,8 @@ EXPORTS = ("sparc_create", "sparc_destroy", "sparc_last_error", "sparc_get_veff"
            "sparc_set_kinetic_scale", "sparc_apply_H", "sparc_lanczos_bounds",
            "sparc_cheb_filter", "sparc_orth_rr", "sparc_gram", "sparc_chefsi_step",
            "sparc_profile_enable",
-           "sparc_profile_read", "sparc_profile_reset", "sparc_launch_count")
+           "sparc_profile_read", "sparc_profile_reset", "sparc_launch_count",
+           "sparc_gram_noalloc")
 
 PHASES = ("stencil", "project", "scatter", "gram", "dense", "rotate", "other")
 
@@ -94,6 +95,8 @@ def load(build_if_missing: bool = True):
     L.sparc_profile_read.argtypes = [vp, ip, C.POINTER(C.c_longlong), dp]
     L.sparc_profile_reset.argtypes = [vp]
     L.sparc_launch_count.argtypes = [C.POINTER(C.c_longlong)]
+    # allocation-free G = A^T B: (A, B, nd, ncols, ld, G, stream)
+    L.sparc_gram_noalloc.argtypes = [vp, vp, C.c_long, ip, C.c_long, vp, vp]
     for name in EXPORTS:
         f = getattr(L, name)
         if name != "sparc_last_error" and f.restype is not C.c_char_p:
