@@ -42,6 +42,9 @@ METRIC = "H*X point-orbitals/s"
 UNIT = "point-orbitals/s"
 ORACLE_COLS = 16      # column slice of the block the oracle timing runs on
 SM_COUNT = 152
+# kernel sources whose DRAM traffic the committed ncu summary was taken on, per dtype
+STENCIL_SOURCES = {"f64": ("stencil_df.cu", "df.cuh", "internal.cuh"),
+                   "f32": ("stencil_tma.cu", "tma.cuh", "internal.cuh")}
 
 
 def reduce_max(value_ms: float, world: int, device=None) -> float:
@@ -159,7 +162,8 @@ def stencil_traffic(dtype: str):
     with open(p) as f:
         d = json.load(f)
     h = hashlib.sha256()
-    for fn in ("stencil.cu", "internal.cuh"):
+    srcs = STENCIL_SOURCES.get(dtype, ())
+    for fn in srcs:
         with open(os.path.join(ROOT, "paper_1603_04334_gb300", "csrc", fn), "rb") as g:
             h.update(g.read())
     ent = d.get(dtype)
@@ -278,27 +282,24 @@ def run_ours(args, rank, world, local_rank):
     alg = stencil_algorithmic(w, dtype, prof, args.steps)
     peaks = measured_peaks()
     sm_max = ck.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    gbs = alg["bytes"] / (alg["ms"] / 1e3) / 1e9 if alg["ms"] else None
+    peak = peaks.get("hbm_gbs", 6800.0)
+    roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+            "frac": gbs / peak if gbs else None,
+            "peak_source": "of measured (hbm_gbs, copy)" if peaks.get("hbm_gbs")
+            else "of fallback (6.8 TB/s)",
+            "traffic": stencil_traffic(dtype),
+            "avg_launch_ms": alg["ms"] / max(alg["launches"], 1),
+            "launches": alg["launches"]}
     if dtype == "f64":
-        achieved = alg["flops"] / (alg["ms"] / 1e3) / 1e12 if alg["ms"] > 0 else None
-        peak = fp64_alu_peak_tflops(sm_max)
-        roof = {"bound": "alu", "kernel": "k_stencil<double> (fused stencil + V_eff + recurrence)",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None,
-                "peak_source": "FP64 FMA issue: 152 SMs x 2 lanes x 2 flop x max SM clock "
-                               "(recipe: 1.25 TFLOP/s nominal)",
-                "hbm_gbs_achieved": alg["bytes"] / (alg["ms"] / 1e3) / 1e9 if alg["ms"] else None,
-                "hbm_frac_of_measured": (alg["bytes"] / (alg["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"])
-                if alg["ms"] and peaks.get("hbm_gbs") else None,
-                "traffic": stencil_traffic(dtype),
-                "avg_launch_ms": alg["ms"] / max(alg["launches"], 1)}
+        # The FP64 step runs in FP32-pair arithmetic on the FP32 pipe; its FP64-equivalent
+        # flop rate is compared with the FP64 pipe's issue limit as context.
+        fl = alg["flops"] / (alg["ms"] / 1e3) / 1e12 if alg["ms"] > 0 else None
+        roof["kernel"] = "k_stencil_df (fused stencil + V_eff + recurrence, FP32-pair)"
+        roof["fp64_equiv_tflops"] = fl
+        roof["fp64_pipe_peak_tflops"] = fp64_alu_peak_tflops(sm_max)
     else:
-        gbs = alg["bytes"] / (alg["ms"] / 1e3) / 1e9 if alg["ms"] else None
-        peak = peaks.get("hbm_gbs", 6800.0)
-        roof = {"bound": "hbm", "kernel": "k_stencil<float>", "achieved": gbs, "peak": peak,
-                "unit": "GB/s", "frac": gbs / peak if gbs else None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback",
-                "traffic": stencil_traffic(dtype),
-                "avg_launch_ms": alg["ms"] / max(alg["launches"], 1)}
+        roof["kernel"] = "k_stencil_f32_tma (fused stencil + V_eff + recurrence, TMA-fed)"
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

@@ -139,16 +139,17 @@ __device__ int jacobi(double *A, double *V, int n, Pairs &P, int *sh_flag)
     return -1;
 }
 
-// ev[i] = A[i,i] sorted ascending; Q[:, rank(i)] = V[:, i], signed (largest |.| > 0).
-__device__ void sort_and_sign(const double *A, const double *V, int n, double *ev, double *Q,
-                              int *rank)
+// ev[rank(i)] = dg[i * ds] sorted ascending (ds = n + 1 reads the diagonal of an n x n
+// matrix); Q[:, rank(i)] = V[:, i], signed so its largest |.| entry is positive.
+__device__ void sort_and_sign(const double *dg, long ds, const double *V, int n, double *ev,
+                              double *Q, int *rank)
 {
     const int tid = threadIdx.x;
     for (int i = tid; i < n; i += NT) {
-        const double di = A[i + (long)i * n];
+        const double di = dg[i * ds];
         int r = 0;
         for (int j = 0; j < n; ++j) {
-            const double dj = A[j + (long)j * n];
+            const double dj = dg[j * ds];
             if (dj < di || (dj == di && j < i)) ++r;
         }
         rank[i] = r;
@@ -175,12 +176,11 @@ __device__ void sort_and_sign(const double *A, const double *V, int n, double *e
 
 long dense_work_elems(int ns) { return 3L * ns * ns + 8L * ns + 64; }
 
+// Symmetrise, Cholesky M = L L^T (L overwrites M), A = L^-1 H_s L^-T into work + n^2.
 __global__ void __launch_bounds__(NT)
-k_dense_rr(double *M, double *Hs, int n, double *ritz, double *Cf, double *work, int *status)
+k_dense_pre(double *M, double *Hs, int n, double *work, int *status)
 {
-    __shared__ Pairs P;
     __shared__ int flag;
-    __shared__ int rank[kMaxDense];
     const int tid = threadIdx.x;
     const long nn = (long)n * n;
     double *W = work;            // L^-1 H_s
@@ -261,16 +261,24 @@ k_dense_rr(double *M, double *Hs, int n, double *ritz, double *Cf, double *work,
             A[j + (long)i * n] = a;
         }
     }
-    __syncthreads();
-    // 5. Jacobi eigensolve
-    const int sweeps = jacobi(A, V, n, P, &flag);
-    if (sweeps < 0) {
-        if (tid == 0) *status = 3;
+    if (tid == 0) *status = 0;
+}
+
+// After the multi-SM Jacobi (jacobi.cu): sort and sign the eigenpairs (Q into W) and form
+// Cf = L^-T Q by backward substitution, one thread per column.
+__global__ void __launch_bounds__(NT)
+k_dense_post(const double *L, int n, const double *diag, const double *V, double *ritz,
+             double *Cf, double *W, int *status, const GridBarrier *bar)
+{
+    __shared__ int rank[kMaxDense];
+    const int tid = threadIdx.x;
+    if (*status != 0) return;
+    if (bar->err) {
+        if (tid == 0) *status = 4;
         return;
     }
-    // 6. sort, sign; Q goes into W (W is free now)
-    sort_and_sign(A, V, n, ritz, W, rank);
-    // 7. Cf = L^-T Q (backward substitution, one thread per column)
+    sort_and_sign(diag, 1, V, n, ritz, W, rank);
+    const double *M = L;
     for (int c = tid; c < n; c += NT) {
         for (int r = n - 1; r >= 0; --r) {
             double s = W[r + (long)c * n];
@@ -285,7 +293,16 @@ cudaError_t dense_rr(double *M, double *Hs, int ns, double *ritz, double *Cf, do
                      int *status, cudaStream_t st)
 {
     if (ns <= 0 || ns > kMaxDense) return cudaErrorInvalidValue;
-    k_dense_rr<<<1, NT, 0, st>>>(M, Hs, ns, ritz, Cf, work, status);
+    const long nn = (long)ns * ns;
+    double *W = work, *A = work + nn, *V = work + 2 * nn, *diag = work + 3 * nn;
+    GridBarrier *bar = (GridBarrier *)(status + 8);
+    k_dense_pre<<<1, NT, 0, st>>>(M, Hs, ns, work, status);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = jacobi_grid(A, W, V, diag, ns, bar, status, status + 12, st);
+    if (e != cudaSuccess) return e;
+    k_dense_post<<<1, NT, 0, st>>>(M, ns, diag, V, ritz, Cf, W, status, bar);
     note_launch();
     return cudaGetLastError();
 }
@@ -308,7 +325,7 @@ k_dense_syev(double *A, int nmax, const int *n_dev, double *ev, double *Q, doubl
         if (threadIdx.x == 0) *status = 3;
         return;
     }
-    sort_and_sign(A, V, n, ev, Q, rank);
+    sort_and_sign(A, (long)n + 1, V, n, ev, Q, rank);
     if (threadIdx.x == 0) *status = 0;
 }
 

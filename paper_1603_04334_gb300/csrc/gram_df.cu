@@ -32,8 +32,10 @@ k_gram_df(const TA *__restrict__ A, long lda, const TB *__restrict__ B, long ldb
           long rows_per, int sym, double *__restrict__ part)
 {
     if (sym && blockIdx.x > blockIdx.y) return;
-    __shared__ float2 As[GK][GT + 1];
-    __shared__ float2 Bs[GK][GT + 1];
+    // chunk c is read from buffer c & 1 while chunk c+1 is split into the other one; the
+    // global loads of chunk c+1 are issued before the compute of chunk c
+    __shared__ float2 As[2][GK][GT + 1];
+    __shared__ float2 Bs[2][GK][GT + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
     const long r0 = (long)blockIdx.z * rows_per;
@@ -49,31 +51,47 @@ k_gram_df(const TA *__restrict__ A, long lda, const TB *__restrict__ B, long ldb
         }
     const int lr = threadIdx.x & 15, lc = threadIdx.x >> 4;
     const float2 z = make_float2(0.0f, 0.0f);
-    int chunk = 0;
-    for (long r = r0; r < r1; r += GK) {
+    TA ra[4];
+    TB rb[4];
+    auto load = [&](long r) {
         const long row = r + lr;
         const bool okr = row < r1;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int c = lc + 16 * u;
-            As[lr][c] = (okr && i0 + c < ns) ? split_double(A[row + (long)(i0 + c) * lda]) : z;
-            Bs[lr][c] = (okr && j0 + c < ns) ? split_double(B[row + (long)(j0 + c) * ldb]) : z;
+            ra[u] = (okr && i0 + c < ns) ? A[row + (long)(i0 + c) * lda] : (TA)0;
+            rb[u] = (okr && j0 + c < ns) ? B[row + (long)(j0 + c) * ldb] : (TB)0;
         }
-        __syncthreads();
+    };
+    auto stage = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            As[buf][lr][lc + 16 * u] = split_double(ra[u]);
+            Bs[buf][lr][lc + 16 * u] = split_double(rb[u]);
+        }
+    };
+    if (r0 < r1) {
+        load(r0);
+        stage(0);
+    }
+    __syncthreads();
+    int chunk = 0, buf = 0;
+    for (long r = r0; r < r1; r += GK) {
+        const bool more = r + GK < r1;
+        if (more) load(r + GK);
 #pragma unroll 4
         for (int kk = 0; kk < GK; ++kk) {
             float2 a[4], b[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                a[u] = As[kk][ty + 16 * u];
-                b[u] = Bs[kk][tx + 16 * u];
+                a[u] = As[buf][kk][ty + 16 * u];
+                b[u] = Bs[buf][kk][tx + 16 * u];
             }
 #pragma unroll
             for (int x = 0; x < 4; ++x)
 #pragma unroll
                 for (int y = 0; y < 4; ++y) mac(a[x], b[y], sh[x][y], sl[x][y]);
         }
-        __syncthreads();
         // every kFlush rows the FP32 pair is added into FP64 and restarted, so the FP32
         // error accumulator never sums more than kFlush products
         if (++chunk == kFlush / GK) {
@@ -82,10 +100,13 @@ k_gram_df(const TA *__restrict__ A, long lda, const TB *__restrict__ B, long ldb
             for (int x = 0; x < 4; ++x)
 #pragma unroll
                 for (int y = 0; y < 4; ++y) {
-                    acc[x][y] += (double)sh[x][y] + (double)sl[x][y];
+                    acc[x][y] += pair_to_double(sh[x][y], sl[x][y]);
                     sh[x][y] = sl[x][y] = 0.0f;
                 }
         }
+        if (more) stage(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
     }
     double *P = part + (long)blockIdx.z * ns * ns;
 #pragma unroll
@@ -94,7 +115,7 @@ k_gram_df(const TA *__restrict__ A, long lda, const TB *__restrict__ B, long ldb
         for (int y = 0; y < 4; ++y) {
             const int gi = i0 + ty + 16 * x, gj = j0 + tx + 16 * y;
             if (gi < ns && gj < ns)
-                P[gi + (long)gj * ns] = acc[x][y] + ((double)sh[x][y] + (double)sl[x][y]);
+                P[gi + (long)gj * ns] = acc[x][y] + pair_to_double(sh[x][y], sl[x][y]);
         }
 }
 

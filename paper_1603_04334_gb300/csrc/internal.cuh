@@ -18,11 +18,12 @@ struct DevHam {
     double h = 0;
     int radius = 6;
     double kscale = 1.0;
-    int f64_df = 1;  // FP64 stencil in FP32-pair arithmetic (stencil_df.cu) instead of FP64 FMA
     double w[kRadius + 1] = {0};  // Laplacian weights w_p (1/h^2 included), zero beyond radius
+    int *err = nullptr;           // device word set by a kernel whose bounded wait ran out
 
     const double *V = nullptr;   // V_eff, Nd
     const float *Vf = nullptr;   // V_eff rounded to float (FP32 filter)
+    const float2 *Vdf = nullptr; // V_eff as FP32 pairs (hi, lo) for the pair-arithmetic stencil
 
     int natoms = 0;
     long nsup = 0;                   // support entries over all atoms
@@ -30,6 +31,7 @@ struct DevHam {
     const int *idx = nullptr;        // node index of each entry
     const double *chi = nullptr;     // 4 per entry: chi_s, chi_px, chi_py, chi_pz
     const float *chi_f = nullptr;
+    const float2 *chi_df = nullptr;  // chi as FP32 pairs (pair-arithmetic projection)
     const double *gchi = nullptr;    // 4 per entry: h^3 gamma_Jlm chi_Jlm
     const float *gchi_f = nullptr;
     const int *ent_atom = nullptr;   // atom of each entry
@@ -38,6 +40,11 @@ struct DevHam {
     const int *uniq_node = nullptr;  // ascending node indices
     const int *uniq_ptr = nullptr;   // nuniq+1 offsets into ent_list
     const int *ent_list = nullptr;   // entries of each node, ascending entry id
+
+    // node-ordered copies of the entry data read by the scatter kernels
+    const int *nl_atom = nullptr;    // per ent_list position: atom
+    const float *nl_gf = nullptr;    // per ent_list position: 4 x h^3 gamma chi (FP32)
+    const float2 *nl_gdf = nullptr;  // same as FP32 pairs
 };
 
 // Coefficients of one fused step  out = alpha*((-1/2 ks L_h + V - c) Y + V_nl Y) - beta*Yprev.
@@ -52,36 +59,50 @@ struct StepCoef {
 
 StepCoef<double> make_coef(const DevHam &H, double alpha, double shift, double beta);
 
-// ---- stencil.cu -------------------------------------------------------------------
-// out = alpha*((-1/2 ks L_h + V - shift) Y) - beta*Yprev   (local part of H, fused step).
-// Yprev may be null (beta ignored) and may alias out (in-place recurrence).
+// ---- stencil.cu / stencil_df.cu ----------------------------------------------------
+// out = alpha*((-1/2 ks L_h + V - shift) Y + V_nl Y) - beta*Yprev   (one fused step).
+// Yprev may be null (beta ignored) and may alias out (in-place recurrence). Cs: the
+// projection coefficients alpha * chi^T Y (FP32 pairs for FP64 blocks, FP32 for FP32
+// blocks), or null when the Hamiltonian has no atoms.
 cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, double *out,
                         int ncols, long ld, double alpha, double shift, double beta,
+                        cudaStream_t st);
+// out += V_nl part from Cs = alpha chi^T Y (pairs), for FP64 blocks (stencil_df.cu)
+cudaError_t scatter_f64_df(const DevHam &H, const float2 *Cs, double *out, int ncols, long ld,
+                           cudaStream_t st);
+// out += V_nl part from Cs = alpha chi^T Y, FP32 blocks (nonlocal.cu)
+cudaError_t scatter_f32(const DevHam &H, const float *Cs, float *out, int ncols, long ld,
                         cudaStream_t st);
 cudaError_t stencil_f32(const DevHam &H, const float *Y, const float *Yprev, float *out,
                         int ncols, long ld, double alpha, double shift, double beta,
                         cudaStream_t st);
-cudaError_t stencil_f64_df(const DevHam &H, const double *Y, const double *Yprev, double *out,
-                           int ncols, long ld, double alpha, double shift, double beta,
-                           cudaStream_t st);
 void stencil_z_split(int n2, long tiles, int ncols, int &nzc, int &zchunk);
+// stencil_tma.cu: TMA-fed FP32 step for shapes with n0, ld multiples of 4 and 16-byte
+// aligned blocks (stencil_tma_ok); stencil_f32 picks it when it applies.
+bool stencil_tma_ok(const DevHam &H, const void *Y, const void *Yprev, const void *out, long ld);
+cudaError_t stencil_f32_tma(const DevHam &H, const float *Y, const float *Yprev, float *out,
+                            int ncols, long ld, const StepCoef<float> &cf, int *err,
+                            cudaStream_t st);
 // FP64 arithmetic on an FP32 block (H applied to FP32 Ritz blocks in FP64).
 cudaError_t stencil_f32in_f64(const DevHam &H, const float *Y, double *out, int ncols,
                               long ld, cudaStream_t st);
 
 // ---- nonlocal.cu ------------------------------------------------------------------
-// C[(J*4+lm)*ncols + c] = sum_{s in supp(J)} chi_Jlm(s) Y[idx(s) + c*ld]
-cudaError_t project_f64(const DevHam &H, const double *Y, int ncols, long ld, double *C,
-                        cudaStream_t st);
-cudaError_t project_f32(const DevHam &H, const float *Y, int ncols, long ld, float *C,
-                        cudaStream_t st);
+// C[(J*4+lm)*ncols + c] = alpha * sum_{s in supp(J)} chi_Jlm(s) Y[idx(s) + c*ld]
+// (FP64 blocks: FP32-pair arithmetic, output as pairs; FP32 blocks: FP32)
+cudaError_t project_f64_df(const DevHam &H, const double *Y, int ncols, long ld, double alpha,
+                           float2 *C, cudaStream_t st);
+cudaError_t project_f32(const DevHam &H, const float *Y, int ncols, long ld, double alpha,
+                        float *C, cudaStream_t st);
 cudaError_t project_f32in_f64(const DevHam &H, const float *Y, int ncols, long ld, double *C,
                               cudaStream_t st);
 // out[node + c*ld] += alpha * sum_{entries e at node} sum_lm gchi(e,lm) C[(atom(e)*4+lm)*ncols + c]
 cudaError_t scatter_f64(const DevHam &H, const double *C, double *out, int ncols, long ld,
                         double alpha, cudaStream_t st);
-cudaError_t scatter_f32(const DevHam &H, const float *C, float *out, int ncols, long ld,
-                        double alpha, cudaStream_t st);
+// node-ordered entry tables of the scatter kernels
+cudaError_t build_nl_node_tables(long nuniq, const int *uniq_ptr, const int *ent_list,
+                                 const int *ent_atom, const double *gchi, int *nl_atom,
+                                 float *nl_gf, float2 *nl_gdf, cudaStream_t st);
 
 // ---- setup.cu -------------------------------------------------------------------
 // V_eff(x) = sum_J -Z_J erf(r/rc)/r on the device.
@@ -102,6 +123,8 @@ cudaError_t build_inverse_map(long nd, long nsup, const int *idx, int *node_cnt,
                               cudaStream_t st);
 cudaError_t exclusive_scan_int(const int *in, int *out, long n, int *tmp, cudaStream_t st);
 cudaError_t to_float(const double *in, float *out, long n, cudaStream_t st);
+// out[i] = (hi, lo) FP32 pair of in[i] (stencil_df.cu)
+cudaError_t to_float_pair(const double *in, float2 *out, long n, cudaStream_t st);
 
 // ---- gram.cu --------------------------------------------------------------------
 // G (ns x ns, column-major, FP64) = A^T B over nd rows; A, B column-major with lda/ldb.
@@ -144,6 +167,20 @@ cudaError_t dense_rr(double *M, double *Hs, int ns, double *ritz, double *Cf, do
 // not null (then n <= ns), else ns. work: dense_work_elems(ns).
 cudaError_t dense_syev(double *A, int ns, const int *ns_dev, double *ev, double *Q,
                        double *work, int *status, cudaStream_t st);
+
+// ---- jacobi.cu --------------------------------------------------------------------
+// Grid-wide barrier state (zeroed before each cooperative launch).
+struct GridBarrier {
+    unsigned count;
+    unsigned gen;
+    int err;
+    int pad;
+};
+// Multi-SM cyclic Jacobi of A0 (n x n, column-major; A1 is a second n x n buffer):
+// eigenvalues (unsorted) in diag, eigenvectors in V. Skipped if *status != 0 on entry;
+// sets *status = 3 if the sweeps do not converge; bar->err != 0 after a barrier timeout.
+cudaError_t jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrier *bar,
+                        int *status, int *sweeps_out, cudaStream_t st);
 
 // ---- lanczos.cu -------------------------------------------------------------------
 constexpr int kDotBlocks = 608;

@@ -1,0 +1,203 @@
+// jacobi.cu -- the symmetric eigensolve of the Rayleigh-Ritz step (Sec. 3.4, the
+// standard problem L^-1 H_s L^-T q = lambda q) spread over many SMs.
+//
+// Cyclic Jacobi with the round-robin parallel ordering of Brent & Luk (1985): each round
+// rotates n/2 disjoint (p, q) pairs. The two-sided update A <- J^T A J factors into
+// independent 2 x 2 blocks A[{p1,q1},{p2,q2}] <- J_1^T A[...] J_2, so a round is one pass
+// over all blocks with no ordering between them. A is double-buffered (read the current
+// copy, write the next), and every CTA recomputes all of the round's rotation angles from
+// the current copy, so a round needs a single grid-wide barrier and every CTA reaches the
+// same convergence decision without further communication. V <- V J updates columns p, q
+// of V in place (each (row, pair) belongs to one thread).
+//
+// Rotation angles follow Golub & Van Loan's symmetric Schur decomposition (Algorithm
+// 8.4.1); a rotation is skipped when |a_pq| <= 4 eps ||A||_F, and the sweeps stop after a
+// sweep that skipped all of them (as in dense.cu's single-CTA version).
+//
+// The grid barrier is a counter/generation pair in global memory; the kernel is launched
+// cooperatively (all CTAs co-resident), and every wait is bounded: after kBarrierSpins
+// polls the waiting CTA raises an error flag, every CTA leaves at its next barrier and the
+// host reports SPARC_ERR_TIMEOUT.
+#include "internal.cuh"
+
+namespace sparc {
+
+namespace {
+constexpr int NT = 256;
+constexpr int kMaxSweeps = 60;
+constexpr double kEps = 2.220446049250313e-16;
+constexpr unsigned long long kBarrierSpins = 1ull << 25;  // ~2 s of 64 ns sleeps
+
+__device__ __forceinline__ void pair_of(int r, int k, int m, int &p, int &q)
+{
+    if (k == 0) {
+        p = r;
+        q = m - 1;
+    } else {
+        p = (r + k) % (m - 1);
+        q = (r - k + (m - 1)) % (m - 1);
+    }
+    if (p > q) {
+        const int t = p;
+        p = q;
+        q = t;
+    }
+}
+
+// Returns false (to every thread of the CTA) once any CTA has hit the spin limit.
+__device__ bool grid_barrier(GridBarrier *b, unsigned nblocks)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vg = &b->gen;
+        const unsigned g = *vg;
+        __threadfence();
+        if (atomicAdd(&b->count, 1u) == nblocks - 1u) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            unsigned long long it = 0;
+            while (*vg == g) {
+                if (++it > kBarrierSpins) {
+                    atomicExch(&b->err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *((volatile int *)&b->err) == 0;
+}
+}  // namespace
+
+__global__ void __launch_bounds__(NT)
+k_jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrier *bar,
+              int *status, int *sweeps_out)
+{
+    __shared__ int sp[kMaxDense / 2], sq[kMaxDense / 2];
+    __shared__ double sc[kMaxDense / 2], ss[kMaxDense / 2];
+    __shared__ double red[NT / 32];
+    __shared__ int any_rot;
+    if (*((volatile int *)status) != 0) return;  // the reduction step failed
+    const unsigned nb = gridDim.x;
+    const long nn = (long)n * n;
+    const long gtid = (long)blockIdx.x * NT + threadIdx.x, gstride = (long)nb * NT;
+    for (long t = gtid; t < nn; t += gstride) V[t] = ((t % n) == (t / n)) ? 1.0 : 0.0;
+    double f = 0.0;
+    for (long t = threadIdx.x; t < nn; t += NT) f += A0[t] * A0[t];
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f;
+    __syncthreads();
+    double fro = 0.0;
+    for (int w = 0; w < NT / 32; ++w) fro += red[w];
+    const double thr = 4.0 * kEps * sqrt(fro);
+    if (!grid_barrier(bar, nb)) return;
+
+    double *cur = A0, *nxt = A1;
+    const int m = n + (n & 1), half = m / 2;
+    int sweeps = -1;
+    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+        if (threadIdx.x == 0) any_rot = 0;
+        __syncthreads();
+        for (int r = 0; r < m - 1; ++r) {
+            for (int k = threadIdx.x; k < half; k += NT) {
+                int p, q;
+                pair_of(r, k, m, p, q);
+                double c = 1.0, s = 0.0;
+                if (q < n) {
+                    const double apq = cur[p + (long)q * n];
+                    if (fabs(apq) > thr) {
+                        const double app = cur[p + (long)p * n], aqq = cur[q + (long)q * n];
+                        const double tau = (aqq - app) / (2.0 * apq);
+                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                        any_rot = 1;
+                    }
+                }
+                sp[k] = p;
+                sq[k] = q;
+                sc[k] = c;
+                ss[k] = s;
+            }
+            __syncthreads();
+            // 2 x 2 blocks: next = J_1^T cur J_2 (every entry of next is written)
+            for (long b = gtid; b < (long)half * half; b += gstride) {
+                const int k1 = (int)(b % half), k2 = (int)(b / half);
+                const int p1 = sp[k1], q1 = sq[k1], p2 = sp[k2], q2 = sq[k2];
+                const bool v1 = q1 < n, v2 = q2 < n;
+                const double c1 = sc[k1], s1 = ss[k1], c2 = sc[k2], s2 = ss[k2];
+                const double app = cur[p1 + (long)p2 * n];
+                const double apq = v2 ? cur[p1 + (long)q2 * n] : 0.0;
+                const double aqp = v1 ? cur[q1 + (long)p2 * n] : 0.0;
+                const double aqq = (v1 && v2) ? cur[q1 + (long)q2 * n] : 0.0;
+                const double bpp = c1 * app - s1 * aqp, bpq = c1 * apq - s1 * aqq;
+                const double bqp = s1 * app + c1 * aqp, bqq = s1 * apq + c1 * aqq;
+                nxt[p1 + (long)p2 * n] = c2 * bpp - s2 * bpq;
+                if (v2) nxt[p1 + (long)q2 * n] = s2 * bpp + c2 * bpq;
+                if (v1) nxt[q1 + (long)p2 * n] = c2 * bqp - s2 * bqq;
+                if (v1 && v2) nxt[q1 + (long)q2 * n] = s2 * bqp + c2 * bqq;
+            }
+            // V <- V J, columns p, q of each rotated pair
+            for (long t = gtid; t < (long)half * n; t += gstride) {
+                const int k = (int)(t / n), row = (int)(t % n);
+                const double s = ss[k];
+                if (s == 0.0) continue;
+                const double c = sc[k];
+                const int p = sp[k], q = sq[k];
+                const double vp = V[row + (long)p * n], vq = V[row + (long)q * n];
+                V[row + (long)p * n] = c * vp - s * vq;
+                V[row + (long)q * n] = s * vp + c * vq;
+            }
+            if (!grid_barrier(bar, nb)) return;
+            double *t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+        const int any = any_rot;
+        __syncthreads();
+        if (!any) {
+            sweeps = sweep + 1;
+            break;
+        }
+    }
+    for (long i = gtid; i < n; i += gstride) diag[i] = cur[i + i * n];
+    if (gtid == 0) {
+        *sweeps_out = sweeps;
+        if (sweeps < 0) *status = 3;
+    }
+}
+
+static int g_coop_blocks = 0;  // co-resident CTAs of k_jacobi_grid (queried once)
+
+cudaError_t jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrier *bar,
+                        int *status, int *sweeps_out, cudaStream_t st)
+{
+    if (n <= 0 || n > kMaxDense) return cudaErrorInvalidValue;
+    if (g_coop_blocks == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_jacobi_grid, NT, 0);
+        if (e != cudaSuccess) return e;
+        g_coop_blocks = sms * (per > 0 ? per : 1);
+    }
+    const long half = (n + 1) / 2;
+    long want = (half * half + NT - 1) / NT;  // one 2 x 2 block of A per thread
+    if (want < 1) want = 1;
+    int G = (int)(want < g_coop_blocks ? want : g_coop_blocks);
+    if (G > 152) G = 152;
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&A0, &A1, &V, &diag, &n, &bar, &status, &sweeps_out};
+    e = cudaLaunchCooperativeKernel((const void *)k_jacobi_grid, dim3(G), dim3(NT), args, 0, st);
+    note_launch();
+    return e;
+}
+
+}  // namespace sparc

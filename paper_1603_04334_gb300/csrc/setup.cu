@@ -362,6 +362,39 @@ cudaError_t build_inverse_map(long nd, long nsup, const int *idx, int *node_cnt,
     return cudaGetLastError();
 }
 
+// Node-ordered copies of the entry data for the scatter kernels: for every position q of
+// ent_list, the atom and h^3 gamma chi of entry ent_list[q] (FP32 and FP32 pair), so a
+// covered node reads its entries contiguously.
+__global__ void k_nl_node_tables(long nuniq, const int *uniq_ptr, const int *ent_list,
+                                 const int *ent_atom, const double *gchi, int *nl_atom,
+                                 float *nl_gf, float2 *nl_gdf)
+{
+    for (long u = (long)blockIdx.x * blockDim.x + threadIdx.x; u < nuniq;
+         u += (long)gridDim.x * blockDim.x) {
+        for (int q = uniq_ptr[u]; q < uniq_ptr[u + 1]; ++q) {
+            const int e = ent_list[q];
+            nl_atom[q] = ent_atom[e];
+            for (int l = 0; l < 4; ++l) {
+                const double g = gchi[4L * e + l];
+                const float gh = (float)g;
+                nl_gf[4L * q + l] = gh;
+                nl_gdf[4L * q + l] = make_float2(gh, (float)(g - (double)gh));
+            }
+        }
+    }
+}
+
+cudaError_t build_nl_node_tables(long nuniq, const int *uniq_ptr, const int *ent_list,
+                                 const int *ent_atom, const double *gchi, int *nl_atom,
+                                 float *nl_gf, float2 *nl_gdf, cudaStream_t st)
+{
+    if (nuniq == 0) return cudaSuccess;
+    k_nl_node_tables<<<152 * 4, 256, 0, st>>>(nuniq, uniq_ptr, ent_list, ent_atom, gchi, nl_atom,
+                                              nl_gf, nl_gdf);
+    note_launch();
+    return cudaGetLastError();
+}
+
 __global__ void k_to_float(const double *in, float *out, long n)
 {
     for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n;

@@ -43,10 +43,14 @@ struct sparc_ctx {
     // owned tables
     double *V = nullptr;
     float *Vf = nullptr;
+    float2 *Vdf = nullptr;
     int *atom_ptr = nullptr, *idx = nullptr, *ent_atom = nullptr;
     double *chi = nullptr, *gchi = nullptr;
     float *chi_f = nullptr, *gchi_f = nullptr;
     int *uniq_node = nullptr, *uniq_ptr = nullptr, *ent_list = nullptr;
+    float2 *chi_df = nullptr, *nl_gdf = nullptr;
+    int *nl_atom = nullptr;
+    float *nl_gf = nullptr;
 
     // grow-only workspaces
     void *C = nullptr;       size_t C_bytes = 0;     // projection coefficients
@@ -196,17 +200,18 @@ sparc_status ensure_C(sparc_ctx *ctx, int ncols)
     return ensure(ctx, ctx->C, ctx->C_bytes, b);
 }
 
-// out = alpha ((H - shift) Y) - beta Yprev  (Yprev may alias out, may be null)
+// out = alpha ((H - shift) Y) - beta Yprev  (Yprev may alias out, may be null):
+// projection alpha chi^T Y, stencil step, nonlocal scatter-add.
 sparc_status step_f64(sparc_ctx *ctx, const double *Y, const double *Yprev, double *out, int ncols,
                       long ld, double alpha, double shift, double beta)
 {
     const DevHam &H = ctx->H;
     if (H.natoms > 0) {
         TRY(ensure_C(ctx, ncols));
-        { PHASE(SPARC_PHASE_PROJECT); CK(project_f64(H, Y, ncols, ld, (double *)ctx->C, ctx->st)); }
+        { PHASE(SPARC_PHASE_PROJECT); CK(project_f64_df(H, Y, ncols, ld, alpha, (float2 *)ctx->C, ctx->st)); }
     }
     { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f64(H, Y, Yprev, out, ncols, ld, alpha, shift, beta, ctx->st)); }
-    if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f64(H, (const double *)ctx->C, out, ncols, ld, alpha, ctx->st)); }
+    if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f64_df(H, (const float2 *)ctx->C, out, ncols, ld, ctx->st)); }
     return SPARC_OK;
 }
 
@@ -216,10 +221,10 @@ sparc_status step_f32(sparc_ctx *ctx, const float *Y, const float *Yprev, float 
     const DevHam &H = ctx->H;
     if (H.natoms > 0) {
         TRY(ensure_C(ctx, ncols));
-        { PHASE(SPARC_PHASE_PROJECT); CK(project_f32(H, Y, ncols, ld, (float *)ctx->C, ctx->st)); }
+        { PHASE(SPARC_PHASE_PROJECT); CK(project_f32(H, Y, ncols, ld, alpha, (float *)ctx->C, ctx->st)); }
     }
     { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f32(H, Y, Yprev, out, ncols, ld, alpha, shift, beta, ctx->st)); }
-    if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f32(H, (const float *)ctx->C, out, ncols, ld, alpha, ctx->st)); }
+    if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f32(H, (const float *)ctx->C, out, ncols, ld, ctx->st)); }
     return SPARC_OK;
 }
 
@@ -348,9 +353,14 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
         { PHASE(SPARC_PHASE_GRAM); CK(gram_f32_f64((const float *)Yf, ld, HX, ld, nd, ns, d.Hs, part, ctx->st, true)); }
     }
     { PHASE(SPARC_PHASE_DENSE); CK(dense_rr(d.M, d.Hs, ns, d.ritz, d.Cf, d.work, ctx->flags, ctx->st)); }
-    CK(cudaMemcpyAsync(ctx->pin_i, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(ctx->pin_i, ctx->flags, sizeof(int) * 16, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     const int status = ctx->pin_i[0];
+    if (ctx->pin_i[14] != 0) {
+        CK(cudaMemsetAsync(ctx->flags + 14, 0, sizeof(int), ctx->st));
+        return fail(ctx, SPARC_ERR_TIMEOUT, "a stencil launch timed out waiting for a TMA load");
+    }
+    if (status == 4) return fail(ctx, SPARC_ERR_TIMEOUT, "grid barrier of the Jacobi solver timed out");
     if (status == 1)
         return fail(ctx, SPARC_ERR_NOT_SPD, "overlap matrix M_s is not positive definite");
     if (status == 2) return fail(ctx, SPARC_ERR_NONFINITE, "non-finite entries in M_s or H_s");
@@ -403,9 +413,9 @@ void lap_weights(int no, double h, double *w)
 void free_ctx(sparc_ctx *c)
 {
     if (!c) return;
-    void *ps[] = {c->V, c->Vf, c->atom_ptr, c->idx, c->ent_atom, c->chi, c->gchi, c->chi_f,
-                  c->gchi_f, c->uniq_node, c->uniq_ptr, c->ent_list, c->C, c->hx, c->rotx,
-                  c->roth, c->part, c->dm, c->lz, c->flags};
+    void *ps[] = {c->V, c->Vf, c->Vdf, c->atom_ptr, c->idx, c->ent_atom, c->chi, c->gchi, c->chi_f,
+                  c->gchi_f, c->chi_df, c->uniq_node, c->uniq_ptr, c->ent_list, c->nl_atom, c->nl_gf, c->nl_gdf, c->C, c->hx, c->rotx, c->roth, c->part,
+                  c->dm, c->lz, c->flags};
     for (void *p : ps) dfree(p);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->prof.used) cudaEventDestroy(e);
@@ -473,6 +483,19 @@ sparc_status build_tables(sparc_ctx *ctx, const sparc_atoms *at)
     for (void *p : {(void *)R, (void *)G, (void *)counts, (void *)node_cnt, (void *)node_start,
                     (void *)cursor, (void *)flags, (void *)rank, (void *)scan_tmp})
         CK(cudaFree(p));
+    // pair copy of chi (pair-arithmetic projection) and the node-ordered entry tables of
+    // the scatter kernels
+    TRY(dmalloc(ctx, ctx->chi_df, 4 * tot));
+    CK(to_float_pair(ctx->chi, ctx->chi_df, 4 * tot, ctx->st));
+    TRY(dmalloc(ctx, ctx->nl_atom, tot));
+    TRY(dmalloc(ctx, ctx->nl_gf, 4 * tot));
+    TRY(dmalloc(ctx, ctx->nl_gdf, 4 * tot));
+    CK(build_nl_node_tables(nuniq, ctx->uniq_ptr, ctx->ent_list, ctx->ent_atom, ctx->gchi,
+                            ctx->nl_atom, ctx->nl_gf, ctx->nl_gdf, ctx->st));
+    H.chi_df = ctx->chi_df;
+    H.nl_atom = ctx->nl_atom;
+    H.nl_gf = ctx->nl_gf;
+    H.nl_gdf = ctx->nl_gdf;
     H.atom_ptr = ctx->atom_ptr;
     H.idx = ctx->idx;
     H.chi = ctx->chi;
@@ -522,10 +545,6 @@ sparc_status sparc_create(const sparc_grid *grid, const double *veff_host,
     H.h = grid->h;
     H.radius = grid->radius;
     H.kscale = 1.0;
-    {
-        const char *m = getenv("SPARC_F64_STENCIL");
-        H.f64_df = (m && strcmp(m, "native") == 0) ? 0 : 1;
-    }
     lap_weights(grid->radius, grid->h, H.w);
 
     sparc_status s = SPARC_OK;
@@ -534,8 +553,10 @@ sparc_status sparc_create(const sparc_grid *grid, const double *veff_host,
         CK(cudaMallocHost((void **)&ctx->pin_i, sizeof(int) * 16));
         TRY(dmalloc(ctx, ctx->flags, 16));
         CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int) * 16, ctx->st));
+        H.err = ctx->flags + 14;
         TRY(dmalloc(ctx, ctx->V, nd));
         TRY(dmalloc(ctx, ctx->Vf, nd));
+        TRY(dmalloc(ctx, ctx->Vdf, nd));
         if (veff_host) {
             CK(cudaMemcpyAsync(ctx->V, veff_host, sizeof(double) * nd, cudaMemcpyHostToDevice,
                                ctx->st));
@@ -556,6 +577,8 @@ sparc_status sparc_create(const sparc_grid *grid, const double *veff_host,
             CK(cudaFree(Z));
         }
         CK(to_float(ctx->V, ctx->Vf, nd, ctx->st));
+        CK(to_float_pair(ctx->V, ctx->Vdf, nd, ctx->st));
+        H.Vdf = ctx->Vdf;
         H.V = ctx->V;
         H.Vf = ctx->Vf;
         TRY(build_tables(ctx, atoms));

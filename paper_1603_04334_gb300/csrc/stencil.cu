@@ -46,7 +46,9 @@ k_stencil(const T *__restrict__ Y, const TO *Yprev, TO *out, const TC *__restric
           int n0, int n1, int n2, long ld, int nzc, int zchunk, StepCoef<TC> cf)
 {
     constexpr int R = kRadius;
-    __shared__ TC s[BY + 2 * R][BX + 2 * R];
+    // plane k is read from s[b] while plane k+1 is staged into s[b ^ 1] (one barrier per
+    // plane; the global loads of plane k+1 are in flight during the compute of plane k)
+    __shared__ TC s[2][BY + 2 * R][BX + 2 * R];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
     const int i = i0 + tx, j = j0 + ty;
@@ -59,6 +61,12 @@ k_stencil(const T *__restrict__ Y, const TO *Yprev, TO *out, const TC *__restric
     TO *Oc = out + (long)col * ld;
     const bool act = (i < n0) && (j < n1);
     const long pij = (long)i + (long)n0 * j;
+    const bool hx = tx < R, hy = ty < R;
+    const int il = i0 - R + tx, ir = i0 + BX + tx, jt = j0 - R + ty, jb = j0 + BY + ty;
+    const bool okl = hx && j < n1 && il >= 0, okr = hx && j < n1 && ir < n0;
+    const bool okt = hy && i < n0 && jt >= 0, okb = hy && i < n0 && jb < n1;
+    const long offl = il + (long)n0 * j, offr = ir + (long)n0 * j;
+    const long offt = i + (long)n0 * jt, offb = i + (long)n0 * jb;
 
     TC q[2 * R + 1];
 #pragma unroll
@@ -66,40 +74,69 @@ k_stencil(const T *__restrict__ Y, const TO *Yprev, TO *out, const TC *__restric
         const int kk = k0 - R + t;
         q[t] = (act && kk >= 0 && kk < n2) ? (TC)Yc[pij + (long)kk * plane] : (TC)0;
     }
+    {
+        const long pk = (long)k0 * plane;
+        s[0][ty + R][tx + R] = q[R];
+        if (hx) {
+            s[0][ty + R][tx] = okl ? (TC)Yc[pk + offl] : (TC)0;
+            s[0][ty + R][tx + BX + R] = okr ? (TC)Yc[pk + offr] : (TC)0;
+        }
+        if (hy) {
+            s[0][ty][tx + R] = okt ? (TC)Yc[pk + offt] : (TC)0;
+            s[0][ty + BY + R][tx + R] = okb ? (TC)Yc[pk + offb] : (TC)0;
+        }
+    }
+    TC vcur = act ? V[pij + (long)k0 * plane] : (TC)0;
+    TC pcur = (act && Pc) ? (TC)Pc[pij + (long)k0 * plane] : (TC)0;
+    __syncthreads();
     for (int k = k0; k < k1; ++k) {
+        const int b = (k - k0) & 1;
         const long pk = (long)k * plane;
-        __syncthreads();
-        s[ty + R][tx + R] = q[R];
-        if (tx < R) {
-            const int il = i0 - R + tx, ir = i0 + BX + tx;
-            const bool okj = j < n1;
-            s[ty + R][tx] = (okj && il >= 0) ? (TC)Yc[pk + il + (long)n0 * j] : (TC)0;
-            s[ty + R][tx + BX + R] = (okj && ir < n0) ? (TC)Yc[pk + ir + (long)n0 * j] : (TC)0;
+        const bool more = k + 1 < k1;
+        const long pk1 = pk + plane;
+        T gl = 0, gr = 0, gt = 0, gb = 0, gq = 0;
+        TC vnext = 0, pnext = 0;
+        if (more) {
+            if (okl) gl = Yc[pk1 + offl];
+            if (okr) gr = Yc[pk1 + offr];
+            if (okt) gt = Yc[pk1 + offt];
+            if (okb) gb = Yc[pk1 + offb];
+            if (act) {
+                vnext = V[pij + pk1];
+                if (Pc) pnext = (TC)Pc[pij + pk1];
+            }
         }
-        if (ty < R) {
-            const int jt = j0 - R + ty, jb = j0 + BY + ty;
-            const bool oki = i < n0;
-            s[ty][tx + R] = (oki && jt >= 0) ? (TC)Yc[pk + i + (long)n0 * jt] : (TC)0;
-            s[ty + BY + R][tx + R] = (oki && jb < n1) ? (TC)Yc[pk + i + (long)n0 * jb] : (TC)0;
-        }
-        __syncthreads();
+        const int kn = k + R + 1;
+        if (act && kn < n2) gq = Yc[pij + (long)kn * plane];
         if (act) {
-            const long p = pij + pk;
-            TC acc = (cf.c0 + cf.alpha * V[p]) * q[R];
+            TC acc = (cf.c0 + cf.alpha * vcur) * q[R];
 #pragma unroll
             for (int r = 1; r <= R; ++r) {
-                const TC t = (s[ty + R][tx + R + r] + s[ty + R][tx + R - r])
-                           + (s[ty + R + r][tx + R] + s[ty + R - r][tx + R])
+                const TC t = (s[b][ty + R][tx + R + r] + s[b][ty + R][tx + R - r])
+                           + (s[b][ty + R + r][tx + R] + s[b][ty + R - r][tx + R])
                            + (q[R + r] + q[R - r]);
                 acc += cf.w[r] * t;
             }
-            if (Pc) acc -= cf.beta * (TC)Pc[p];
-            Oc[p] = (TO)acc;
+            if (Pc) acc -= cf.beta * pcur;
+            Oc[pij + pk] = (TO)acc;
         }
 #pragma unroll
         for (int t = 0; t < 2 * R; ++t) q[t] = q[t + 1];
-        const int kn = k + R + 1;
-        q[2 * R] = (act && kn < n2) ? (TC)Yc[pij + (long)kn * plane] : (TC)0;
+        q[2 * R] = (TC)gq;
+        vcur = vnext;
+        pcur = pnext;
+        if (more) {
+            s[b ^ 1][ty + R][tx + R] = q[R];
+            if (hx) {
+                s[b ^ 1][ty + R][tx] = (TC)gl;
+                s[b ^ 1][ty + R][tx + BX + R] = (TC)gr;
+            }
+            if (hy) {
+                s[b ^ 1][ty][tx + R] = (TC)gt;
+                s[b ^ 1][ty + BY + R][tx + R] = (TC)gb;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -132,20 +169,13 @@ static cudaError_t launch(const DevHam &H, const T *Y, const TO *Yprev, TO *out,
     return cudaGetLastError();
 }
 
-cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, double *out,
-                        int ncols, long ld, double alpha, double shift, double beta,
-                        cudaStream_t st)
-{
-    if (H.f64_df)
-        return stencil_f64_df(H, Y, Yprev, out, ncols, ld, alpha, shift, beta, st);
-    return launch<double, double, double>(H, Y, Yprev, out, H.V, ncols, ld,
-                                          make_coef(H, alpha, shift, beta), st);
-}
-
 cudaError_t stencil_f32(const DevHam &H, const float *Y, const float *Yprev, float *out,
                         int ncols, long ld, double alpha, double shift, double beta,
                         cudaStream_t st)
 {
+    if (stencil_tma_ok(H, Y, Yprev, out, ld))
+        return stencil_f32_tma(H, Y, Yprev, out, ncols, ld,
+                               cast_coef<float>(make_coef(H, alpha, shift, beta)), H.err, st);
     return launch<float, float, float>(H, Y, Yprev, out, H.Vf, ncols, ld,
                                        make_coef(H, alpha, shift, beta), st);
 }

@@ -7,18 +7,18 @@
 // issues FP64 at 1/64 of its FP32 rate (about 0.6e12 FP64 FMA/s against 37e12 FP32 FMA/s),
 // so the native FP64 stencil (about 39 FP64 instructions per point) is bound by the FP64
 // pipe at roughly 5% of HBM bandwidth. Here each FP64 value becomes a pair of FP32 values
-// (hi, lo) with hi + lo = x to about 2^-48 relative, and the weighted sum runs in FP32
-// with error-free transformations:
-//   * split: hi = x truncated to 24 significant bits and lo = the remaining bits rounded
-//     to FP32, both built with integer operations on the bit pattern (no FP64 pipe);
-//   * the six neighbours of each radius are summed with Knuth's TwoSum on the hi parts,
-//     the lo parts and the rounding errors collected in a second FP32 accumulator;
+// (hi, lo) with hi + lo = x to about 2^-48 relative (split_double, df.cuh), and the
+// weighted sum runs in FP32 with error-free transformations:
+//   * the six neighbours of each radius are summed pairwise with Knuth's TwoSum on the hi
+//     parts, the lo parts and the rounding errors going to a second FP32 accumulator;
 //   * each radius sum is scaled with Dekker's exact product (TwoProduct via FMA) and
 //     added to the running sum with TwoSum, the error terms again going to the second
-//     accumulator (the compensated dot product of Ogita, Rump & Oishi, "Dot2", 2005).
-// Per point this leaves four FP64 operations: the centre coefficient alpha*V + c0, the
-// recombination hi + lo, and the recurrence term -beta*Y_{j-1}. The rounding error is
-// about 2^-48 of sum |terms| instead of FP64's 2^-53 per operation.
+//     accumulator (the compensated dot product of Ogita, Rump & Oishi, "Dot2", 2005);
+//   * the centre coefficient c0 + alpha V_p (V_eff kept as pairs) and the recurrence term
+//     -beta Y_{j-1} are formed in the same pair arithmetic.
+// Only the final hi + lo recombination uses the FP64 pipe (one add per point); the pair
+// parts are widened to FP64 with integer bit operations. The rounding error is about
+// 2^-48 of sum |terms| instead of FP64's 2^-53 per operation.
 #include "df.cuh"
 #include "internal.cuh"
 
@@ -27,17 +27,44 @@ namespace sparc {
 struct DfCoef {
     float wh[kRadius + 1];  // weights of radius r split as wh + wl
     float wl[kRadius + 1];
-    double c0, alpha, beta;
+    float c0h, c0l;         // centre constant c0 as a pair
+    float ah, al;           // alpha as a pair
+    float bh, bl;           // -beta as a pair
 };
+
+// (sh, sl) += (vh, vl) * (wh, wl), with sh updated by TwoSum and all error terms in sl.
+__device__ __forceinline__ void acc_mul(float vh, float vl, float wh, float wl, float &sh,
+                                        float &sl)
+{
+    const float p = wh * vh;
+    const float pe = fmaf(wh, vh, -p);
+    float s, e;
+    two_sum(sh, p, s, e);
+    sh = s;
+    sl += e;
+    sl += pe;
+    sl = fmaf(wh, vl, sl);
+    sl = fmaf(wl, vh, sl);
+}
+
+// (a.x + a.y) + (b.x + b.y) as a pair whose lo part is not renormalised
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b)
+{
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    return make_float2(s, (a.y + b.y) + e);
+}
 
 template <int BX, int BY>
 __global__ void __launch_bounds__(BX *BY)
 k_stencil_df(const double *__restrict__ Y, const double *Yprev, double *out,
-             const double *__restrict__ V, int n0, int n1, int n2, long ld, int nzc, int zchunk,
+             const float2 *__restrict__ Vdf, int n0, int n1, int n2, long ld, int nzc, int zchunk,
              DfCoef cf)
 {
     constexpr int R = kRadius;
-    __shared__ float2 s[BY + 2 * R][BX + 2 * R];
+    // plane k is read from s[b] while plane k+1 is staged into s[b ^ 1]: one barrier per
+    // plane, and the global loads of plane k+1 are in flight while plane k is computed
+    __shared__ float2 s[2][BY + 2 * R][BX + 2 * R];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
     const int i = i0 + tx, j = j0 + ty;
@@ -51,6 +78,13 @@ k_stencil_df(const double *__restrict__ Y, const double *Yprev, double *out,
     const bool act = (i < n0) && (j < n1);
     const long pij = (long)i + (long)n0 * j;
     const float2 zero = make_float2(0.0f, 0.0f);
+    // halo duties of this thread: x halos (tx < R) and y halos (ty < R)
+    const bool hx = tx < R, hy = ty < R;
+    const int il = i0 - R + tx, ir = i0 + BX + tx, jt = j0 - R + ty, jb = j0 + BY + ty;
+    const bool okl = hx && j < n1 && il >= 0, okr = hx && j < n1 && ir < n0;
+    const bool okt = hy && i < n0 && jt >= 0, okb = hy && i < n0 && jb < n1;
+    const long offl = il + (long)n0 * j, offr = ir + (long)n0 * j;
+    const long offt = i + (long)n0 * jt, offb = i + (long)n0 * jb;
 
     float2 q[2 * R + 1];
 #pragma unroll
@@ -58,91 +92,167 @@ k_stencil_df(const double *__restrict__ Y, const double *Yprev, double *out,
         const int kk = k0 - R + t;
         q[t] = (act && kk >= 0 && kk < n2) ? split_double(Yc[pij + (long)kk * plane]) : zero;
     }
+    {
+        const long pk = (long)k0 * plane;
+        s[0][ty + R][tx + R] = q[R];
+        if (hx) {
+            s[0][ty + R][tx] = okl ? split_double(Yc[pk + offl]) : zero;
+            s[0][ty + R][tx + BX + R] = okr ? split_double(Yc[pk + offr]) : zero;
+        }
+        if (hy) {
+            s[0][ty][tx + R] = okt ? split_double(Yc[pk + offt]) : zero;
+            s[0][ty + BY + R][tx + R] = okb ? split_double(Yc[pk + offb]) : zero;
+        }
+    }
+    float2 vcur = act ? Vdf[pij + (long)k0 * plane] : zero;
+    double pcur = (act && Pc) ? Pc[pij + (long)k0 * plane] : 0.0;
+    __syncthreads();
     for (int k = k0; k < k1; ++k) {
+        const int b = (k - k0) & 1;
         const long pk = (long)k * plane;
-        __syncthreads();
-        s[ty + R][tx + R] = q[R];
-        if (tx < R) {
-            const int il = i0 - R + tx, ir = i0 + BX + tx;
-            const bool okj = j < n1;
-            s[ty + R][tx] = (okj && il >= 0) ? split_double(Yc[pk + il + (long)n0 * j]) : zero;
-            s[ty + R][tx + BX + R] =
-                (okj && ir < n0) ? split_double(Yc[pk + ir + (long)n0 * j]) : zero;
+        // loads for plane k+1 (and the queue entry k+R+1), consumed after the compute
+        const bool more = k + 1 < k1;
+        const long pk1 = pk + plane;
+        double gl = 0.0, gr = 0.0, gt = 0.0, gb = 0.0, gq = 0.0, pnext = 0.0;
+        float2 vnext = zero;
+        if (more) {
+            if (okl) gl = Yc[pk1 + offl];
+            if (okr) gr = Yc[pk1 + offr];
+            if (okt) gt = Yc[pk1 + offt];
+            if (okb) gb = Yc[pk1 + offb];
+            if (act) {
+                vnext = Vdf[pij + pk1];
+                if (Pc) pnext = Pc[pij + pk1];
+            }
         }
-        if (ty < R) {
-            const int jt = j0 - R + ty, jb = j0 + BY + ty;
-            const bool oki = i < n0;
-            s[ty][tx + R] = (oki && jt >= 0) ? split_double(Yc[pk + i + (long)n0 * jt]) : zero;
-            s[ty + BY + R][tx + R] =
-                (oki && jb < n1) ? split_double(Yc[pk + i + (long)n0 * jb]) : zero;
-        }
-        __syncthreads();
+        const int kn = k + R + 1;
+        if (act && kn < n2) gq = Yc[pij + (long)kn * plane];
         if (act) {
             const long p = pij + pk;
-            // centre: (c0 + alpha V_p) y_p, coefficient formed in FP64 and split
-            const float2 c = split_double(fma(cf.alpha, V[p], cf.c0));
+            // centre coefficient cc = c0 + alpha V_p as a pair
+            const float2 v = vcur;
+            float ch = 0.0f, cl = 0.0f;
+            acc_mul(v.x, v.y, cf.ah, cf.al, ch, cl);
+            {
+                float t, e;
+                two_sum(ch, cf.c0h, t, e);
+                ch = t;
+                cl += e + cf.c0l;
+            }
+            // running sum (ah, al) starts with cc * y_p
             const float2 y = q[R];
-            float ah = c.x * y.x;
-            float al = fmaf(c.x, y.x, -ah);
-            al = fmaf(c.x, y.y, al);
-            al = fmaf(c.y, y.x, al);
+            float ah = 0.0f, al = 0.0f;
+            acc_mul(y.x, y.y, ch, cl, ah, al);
 #pragma unroll
             for (int r = 1; r <= R; ++r) {
-                const float2 v[6] = {s[ty + R][tx + R + r], s[ty + R][tx + R - r],
-                                     s[ty + R + r][tx + R], s[ty + R - r][tx + R], q[R + r],
-                                     q[R - r]};
-                float sh = v[0].x, sl = v[0].y;
-#pragma unroll
-                for (int u = 1; u < 6; ++u) {
-                    float t, e;
-                    two_sum(sh, v[u].x, t, e);
-                    sh = t;
-                    sl += e;
-                    sl += v[u].y;
-                }
-                const float pr = cf.wh[r] * sh;
-                const float pe = fmaf(cf.wh[r], sh, -pr);
-                float t, e;
-                two_sum(ah, pr, t, e);
-                ah = t;
-                al += e;
-                al += pe;
-                al = fmaf(cf.wh[r], sl, al);
-                al = fmaf(cf.wl[r], sh, al);
+                const float2 t0 = pair_add(s[b][ty + R][tx + R + r], s[b][ty + R][tx + R - r]);
+                const float2 t1 = pair_add(s[b][ty + R + r][tx + R], s[b][ty + R - r][tx + R]);
+                const float2 t2 = pair_add(q[R + r], q[R - r]);
+                const float2 t = pair_add(pair_add(t0, t1), t2);
+                acc_mul(t.x, t.y, cf.wh[r], cf.wl[r], ah, al);
             }
-            double d = (double)ah + (double)al;
-            if (Pc) d = fma(-cf.beta, Pc[p], d);
-            Oc[p] = d;
+            if (Pc) {
+                const float2 pv = split_double(pcur);
+                acc_mul(pv.x, pv.y, cf.bh, cf.bl, ah, al);
+            }
+            Oc[p] = pair_to_double(ah, al);
         }
 #pragma unroll
         for (int t = 0; t < 2 * R; ++t) q[t] = q[t + 1];
-        const int kn = k + R + 1;
-        q[2 * R] = (act && kn < n2) ? split_double(Yc[pij + (long)kn * plane]) : zero;
+        q[2 * R] = (act && kn < n2) ? split_double(gq) : zero;
+        vcur = vnext;
+        pcur = pnext;
+        if (more) {
+            s[b ^ 1][ty + R][tx + R] = q[R];
+            if (hx) {
+                s[b ^ 1][ty + R][tx] = okl ? split_double(gl) : zero;
+                s[b ^ 1][ty + R][tx + BX + R] = okr ? split_double(gr) : zero;
+            }
+            if (hy) {
+                s[b ^ 1][ty][tx + R] = okt ? split_double(gt) : zero;
+                s[b ^ 1][ty + BY + R][tx + R] = okb ? split_double(gb) : zero;
+            }
+        }
+        __syncthreads();
     }
 }
 
-cudaError_t stencil_f64_df(const DevHam &H, const double *Y, const double *Yprev, double *out,
-                           int ncols, long ld, double alpha, double shift, double beta,
+static void split_host(double x, float &h, float &l)
+{
+    h = (float)x;
+    l = (float)(x - (double)h);
+}
+
+// Nonlocal scatter for FP64 blocks in pair arithmetic: out(p, c) += sum_{q at p} sum_l
+// g(q, l) Cs(atom(q), l, c), Cs = alpha chi^T Y as pairs (k_project_df). A thread owns one
+// covered node and walks a strided subset of the columns (the node's entries stay in L1;
+// a warp holds 32 consecutive covered nodes of one column, so the out accesses coalesce).
+// The pair sum is added to the FP64 output with one FP64 add.
+__global__ void __launch_bounds__(256)
+k_scatter_df(double *out, long ld, int ncols, long nuniq, const int *__restrict__ uniq_node,
+             const int *__restrict__ uniq_ptr, const int *__restrict__ nl_atom,
+             const float2 *__restrict__ g, const float2 *__restrict__ Cs)
+{
+    const long u = (long)blockIdx.x * 32 + threadIdx.x;
+    if (u >= nuniq) return;
+    const long node = uniq_node[u];
+    const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
+    for (int c = threadIdx.y; c < ncols; c += blockDim.y) {
+        float vh = 0.0f, vl = 0.0f;
+        for (int q = q0; q < q1; ++q) {
+            const float2 *cs = Cs + (long)nl_atom[q] * 4 * ncols + c;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) mac(g[4L * q + l], cs[(long)l * ncols], vh, vl);
+        }
+        double *o = out + node + (long)c * ld;
+        *o = *o + pair_to_double(vh, vl);
+    }
+}
+
+cudaError_t scatter_f64_df(const DevHam &H, const float2 *Cs, double *out, int ncols, long ld,
                            cudaStream_t st)
+{
+    if (H.natoms == 0 || H.nuniq == 0 || ncols <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((H.nuniq + 31) / 32)), block(32, 8);
+    k_scatter_df<<<grid, block, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node, H.uniq_ptr,
+                                         H.nl_atom, H.nl_gdf, Cs);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, double *out,
+                        int ncols, long ld, double alpha, double shift, double beta,
+                        cudaStream_t st)
 {
     constexpr int BX = 32, BY = 16;
     if (ncols <= 0) return cudaSuccess;
     if (ncols > 65535) return cudaErrorInvalidValue;
     const StepCoef<double> d = make_coef(H, alpha, shift, beta);
     DfCoef cf;
-    for (int r = 0; r <= kRadius; ++r) {
-        cf.wh[r] = (float)d.w[r];
-        cf.wl[r] = (float)(d.w[r] - (double)cf.wh[r]);
-    }
-    cf.c0 = d.c0;
-    cf.alpha = d.alpha;
-    cf.beta = d.beta;
+    for (int r = 0; r <= kRadius; ++r) split_host(d.w[r], cf.wh[r], cf.wl[r]);
+    split_host(d.c0, cf.c0h, cf.c0l);
+    split_host(d.alpha, cf.ah, cf.al);
+    split_host(-d.beta, cf.bh, cf.bl);
     const int gx = (H.n0 + BX - 1) / BX, gy = (H.n1 + BY - 1) / BY;
     int nzc, zchunk;
     stencil_z_split(H.n2, (long)gx * gy, ncols, nzc, zchunk);
     dim3 grid(gx, gy, ncols * nzc), block(BX, BY);
-    k_stencil_df<BX, BY><<<grid, block, 0, st>>>(Y, Yprev, out, H.V, H.n0, H.n1, H.n2, ld, nzc,
+    k_stencil_df<BX, BY><<<grid, block, 0, st>>>(Y, Yprev, out, H.Vdf, H.n0, H.n1, H.n2, ld, nzc,
                                                  zchunk, cf);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void k_to_float_pair(const double *in, float2 *out, long n)
+{
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (long)gridDim.x * blockDim.x)
+        out[q] = split_double(in[q]);
+}
+
+cudaError_t to_float_pair(const double *in, float2 *out, long n, cudaStream_t st)
+{
+    k_to_float_pair<<<152 * 8, 256, 0, st>>>(in, out, n);
     note_launch();
     return cudaGetLastError();
 }

@@ -134,6 +134,37 @@ def test_apply_H_f32(c24):
     assert nrm_err(got, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("n3,pad", [((40, 29, 23), 0),   # TMA path: 2 x tiles, ragged y, z
+                                    ((40, 29, 23), 4),   # TMA path, padded ld
+                                    ((37, 29, 23), 0),   # n0 not a multiple of 4: plain path
+                                    ((40, 29, 23), 3)])  # ld not a multiple of 4: plain path
+def test_apply_H_and_filter_f32_both_stencil_paths(n3, pad):
+    h = 0.45
+    rng = np.random.default_rng(n3[0] + pad)
+    nd = n3[0] * n3[1] * n3[2]
+    R = np.array([[rng.uniform(2, (n3[0] - 1) * h - 2), rng.uniform(2, (n3[1] - 1) * h - 2),
+                   rng.uniform(2, (n3[2] - 1) * h - 2)] for _ in range(3)])
+    gamma = rng.uniform(-2, 2, (3, 4))
+    V = rng.uniform(-3, 1, nd)
+    H = oracle.Hamiltonian(n3, h, V, R, gamma)
+    ctx = sparc.Context(n3, h, R, None, gamma, veff=V)
+    ld = nd + pad
+    X = np.zeros((5, ld))
+    X[:, :nd] = rng.uniform(-0.5, 0.5, (5, nd))
+    Xd = to_dev(X, torch.float32)
+    X32 = Xd.double().cpu().numpy()[:, :nd].copy()
+    HXd = torch.full_like(Xd, 7.0)
+    ctx.apply_H(Xd, HXd)
+    got = HXd.double().cpu().numpy()
+    assert nrm_err(got[:, :nd], H.apply(X32)) <= 2e-6
+    assert np.all(got[:, nd:] == 7.0)
+    a0, a, b = -4.0, 5.0, 45.0
+    ref = H.cheb_filter(X32, 8, a, b, a0)
+    ctx.cheb_filter(Xd, torch.empty_like(Xd), 8, a, b, a0)
+    assert nrm_err(Xd.double().cpu().numpy()[:, :nd], ref) <= 1e-5
+    ctx.close()
+
+
 def test_apply_H_f64_smooth_block():
     # Smooth, bound-state-like columns: H x is a small difference of large stencil terms
     # (|H x| ~ |lambda x| while sum|terms| ~ 100 |x| at h = 0.3), the hardest case for the
