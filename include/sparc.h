@@ -186,6 +186,27 @@ sparc_status sparc_profile_reset(sparc_ctx *ctx);
 /* Number of kernels this library has launched in the calling process (all contexts). */
 sparc_status sparc_launch_count(long long *count);
 
+/* ---- synchronisation and failure detection ------------------------------------------ */
+
+/* Waits for all work enqueued on the context's stream and reports device-side errors
+ * that asynchronous calls cannot return. Every wait inside a kernel of this library is
+ * bounded; a kernel whose wait expires (a TMA load that never lands) stops, leaves no copy
+ * in flight, and raises a sticky device flag. sparc_apply_H and sparc_cheb_filter return
+ * before their kernels run, so such a flag is reported by the next synchronising call
+ * (this one, sparc_lanczos_bounds, sparc_orth_rr or sparc_chefsi_step) as
+ * SPARC_ERR_TIMEOUT, and cleared. The paper has no counterpart. */
+sparc_status sparc_sync(sparc_ctx *ctx);
+
+/* Self-test of the bounded waits, for failure-detection tests without a GPU fault.
+ * which = 0: an mbarrier that expects two arrivals and receives one (the wait of the TMA
+ * stencil pipeline); which = 1: a cooperative two-CTA grid barrier that expects three CTAs
+ * (the barrier of the multi-SM Jacobi solver). Neither wait can complete; each gives up
+ * after about 0.1 s. Returns SPARC_ERR_TIMEOUT when the kernel detected the expired wait
+ * and reported it through the host (the expected result), SPARC_OK if the wait completed
+ * (a defect), SPARC_ERR_ARG for another `which`. The context stays usable afterwards.
+ * The paper has no counterpart. */
+sparc_status sparc_selftest_timeout(sparc_ctx *ctx, int which);
+
 /* ---- allocation-free variant ---------------------------------------------------- */
 
 /* G = A^T B in FP64 without allocating any memory (the paper has no counterpart; it is

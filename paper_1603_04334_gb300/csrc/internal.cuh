@@ -181,6 +181,11 @@ struct GridBarrier {
 // sets *status = 3 if the sweeps do not converge; bar->err != 0 after a barrier timeout.
 cudaError_t jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrier *bar,
                         int *status, int *sweeps_out, cudaStream_t st);
+// Self-tests of the bounded waits (failure detection without a fault): a grid barrier
+// that can never complete (status <- 4 after its spin limit) and an mbarrier that never
+// completes (err <- 1 after its probe limit).
+cudaError_t barrier_selftest(GridBarrier *bar, int *status, cudaStream_t st);
+cudaError_t mbar_selftest(int *err, cudaStream_t st);
 
 // ---- lanczos.cu -------------------------------------------------------------------
 constexpr int kDotBlocks = 608;

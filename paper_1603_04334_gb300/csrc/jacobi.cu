@@ -45,11 +45,13 @@ __device__ __forceinline__ void pair_of(int r, int k, int m, int &p, int &q)
 }
 
 // Returns false (to every thread of the CTA) once any CTA has hit the spin limit.
-__device__ bool grid_barrier(GridBarrier *b, unsigned nblocks)
+__device__ bool grid_barrier(GridBarrier *b, unsigned nblocks,
+                             unsigned long long spins = kBarrierSpins)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *vg = &b->gen;
+        volatile int *ve = &b->err;
         const unsigned g = *vg;
         __threadfence();
         if (atomicAdd(&b->count, 1u) == nblocks - 1u) {
@@ -58,8 +60,10 @@ __device__ bool grid_barrier(GridBarrier *b, unsigned nblocks)
             atomicAdd(&b->gen, 1u);
         } else {
             unsigned long long it = 0;
-            while (*vg == g) {
-                if (++it > kBarrierSpins) {
+            // leaves when the generation moves on, when another CTA has given up, or after
+            // `spins` polls (then it raises the flag itself)
+            while (*vg == g && *ve == 0) {
+                if (++it > spins) {
                     atomicExch(&b->err, 1);
                     break;
                 }
@@ -196,6 +200,29 @@ cudaError_t jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, 
     if (e != cudaSuccess) return e;
     void *args[] = {&A0, &A1, &V, &diag, &n, &bar, &status, &sweeps_out};
     e = cudaLaunchCooperativeKernel((const void *)k_jacobi_grid, dim3(G), dim3(NT), args, 0, st);
+    note_launch();
+    return e;
+}
+
+// Failure-detection self-test: every CTA of a cooperative grid waits at a barrier that
+// expects one CTA more than the grid holds, so the wait can only end through its spin
+// limit (~65 ms here). status[0] = 4 when every CTA left through the timeout path, 0 if
+// the barrier (wrongly) completed.
+__global__ void __launch_bounds__(32) k_barrier_selftest(GridBarrier *bar, int *status)
+{
+    const bool ok = grid_barrier(bar, gridDim.x + 1u, 1ull << 20);
+    if (threadIdx.x == 0 && !ok) atomicExch(status, 4);
+}
+
+cudaError_t barrier_selftest(GridBarrier *bar, int *status, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(status, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&bar, &status};
+    e = cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, dim3(2), dim3(32), args, 0,
+                                    st);
     note_launch();
     return e;
 }

@@ -21,7 +21,9 @@ __device__ __forceinline__ T warp_sum(T v)
 
 // One CTA per (atom, column block of CB). Each thread accumulates 4*CB partial sums over
 // a strided share of the atom's support; the block reduces them in a fixed order.
-template <typename T, typename TC, int CB, int NT>
+// C layout: ILV = false: C[(J * 4 + l) * ncols + c]; ILV = true: C[(J * ncols + c) * 4 + l]
+// (the four channels of one atom and column contiguous, one 16-byte load in the scatter).
+template <typename T, typename TC, int CB, int NT, bool ILV>
 __global__ void __launch_bounds__(NT)
 k_project(const T *__restrict__ Y, long ld, int ncols, const int *__restrict__ atom_ptr,
           const int *__restrict__ idx, const TC *__restrict__ chi, TC *__restrict__ C, TC alpha)
@@ -35,20 +37,43 @@ k_project(const T *__restrict__ Y, long ld, int ncols, const int *__restrict__ a
     for (int l = 0; l < 4; ++l)
 #pragma unroll
         for (int cb = 0; cb < CB; ++cb) acc[l][cb] = (TC)0;
-    for (int s = b + threadIdx.x; s < e; s += NT) {
-        const long p = idx[s];
-        const TC x0 = chi[4 * (long)s], x1 = chi[4 * (long)s + 1], x2 = chi[4 * (long)s + 2],
-                 x3 = chi[4 * (long)s + 3];
+    // Two support points per trip, their node indices loaded one trip ahead, so a thread
+    // has 2 * CB independent loads of Y in flight instead of an index -> value chain.
+    auto load_chi = [&](int s, TC x[4]) {
+        if constexpr (sizeof(TC) == 4) {
+            const float4 v = reinterpret_cast<const float4 *>(chi)[s];
+            x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+        } else {
+            const double2 a = reinterpret_cast<const double2 *>(chi)[2 * (long)s];
+            const double2 q = reinterpret_cast<const double2 *>(chi)[2 * (long)s + 1];
+            x[0] = a.x, x[1] = a.y, x[2] = q.x, x[3] = q.y;
+        }
+    };
+    int s = b + threadIdx.x;
+    long pa = s < e ? idx[s] : 0, pb = s + NT < e ? idx[s + NT] : 0;
+    for (; s < e; s += 2 * NT) {
+        const bool vb = s + NT < e;
+        TC xa[4], xb[4] = {(TC)0, (TC)0, (TC)0, (TC)0};
+        TC ya[CB], yb[CB];
+        load_chi(s, xa);
+        if (vb) load_chi(s + NT, xb);
 #pragma unroll
         for (int cb = 0; cb < CB; ++cb) {
-            if (c0 + cb < ncols) {
-                const TC y = (TC)Y[p + (long)(c0 + cb) * ld];
-                acc[0][cb] += x0 * y;
-                acc[1][cb] += x1 * y;
-                acc[2][cb] += x2 * y;
-                acc[3][cb] += x3 * y;
-            }
+            const bool vc = c0 + cb < ncols;
+            ya[cb] = vc ? (TC)Y[pa + (long)(c0 + cb) * ld] : (TC)0;
+            yb[cb] = (vc && vb) ? (TC)Y[pb + (long)(c0 + cb) * ld] : (TC)0;
         }
+        const int sn = s + 2 * NT;
+        pa = sn < e ? idx[sn] : 0;
+        pb = sn + NT < e ? idx[sn + NT] : 0;
+#pragma unroll
+        for (int cb = 0; cb < CB; ++cb)
+#pragma unroll
+            for (int l = 0; l < 4; ++l) acc[l][cb] += xa[l] * ya[cb];
+#pragma unroll
+        for (int cb = 0; cb < CB; ++cb)
+#pragma unroll
+            for (int l = 0; l < 4; ++l) acc[l][cb] += xb[l] * yb[cb];
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -64,11 +89,15 @@ k_project(const T *__restrict__ Y, long ld, int ncols, const int *__restrict__ a
         TC v = (TC)0;
 #pragma unroll
         for (int w = 0; w < NT / 32; ++w) v += red[w][threadIdx.x];
-        if (c0 + cb < ncols) C[(long)(J * 4 + l) * ncols + c0 + cb] = alpha * v;
+        if (c0 + cb < ncols) {
+            const long o = ILV ? ((long)J * ncols + c0 + cb) * 4 + l
+                               : (long)(J * 4 + l) * ncols + c0 + cb;
+            C[o] = alpha * v;
+        }
     }
 }
 
-template <typename T, typename TC>
+template <typename T, typename TC, bool ILV>
 static cudaError_t project(const DevHam &H, const T *Y, int ncols, long ld, const TC *chi,
                            TC *C, TC alpha, cudaStream_t st)
 {
@@ -76,7 +105,8 @@ static cudaError_t project(const DevHam &H, const T *Y, int ncols, long ld, cons
     constexpr int CB = 8, NT = 256;
     dim3 grid(H.natoms, (ncols + CB - 1) / CB);
     if (grid.y > 65535) return cudaErrorInvalidValue;
-    k_project<T, TC, CB, NT><<<grid, NT, 0, st>>>(Y, ld, ncols, H.atom_ptr, H.idx, chi, C, alpha);
+    k_project<T, TC, CB, NT, ILV>
+        <<<grid, NT, 0, st>>>(Y, ld, ncols, H.atom_ptr, H.idx, chi, C, alpha);
     note_launch();
     return cudaGetLastError();
 }
@@ -84,12 +114,12 @@ static cudaError_t project(const DevHam &H, const T *Y, int ncols, long ld, cons
 cudaError_t project_f32(const DevHam &H, const float *Y, int ncols, long ld, double alpha,
                         float *C, cudaStream_t st)
 {
-    return project<float, float>(H, Y, ncols, ld, H.chi_f, C, (float)alpha, st);
+    return project<float, float, true>(H, Y, ncols, ld, H.chi_f, C, (float)alpha, st);
 }
 cudaError_t project_f32in_f64(const DevHam &H, const float *Y, int ncols, long ld, double *C,
                               cudaStream_t st)
 {
-    return project<float, double>(H, Y, ncols, ld, H.chi, C, 1.0, st);
+    return project<float, double, false>(H, Y, ncols, ld, H.chi, C, 1.0, st);
 }
 
 // ---- FP64 blocks in FP32-pair arithmetic (see df.cuh) ----------------------------------
@@ -177,21 +207,26 @@ cudaError_t project_f64_df(const DevHam &H, const double *Y, int ncols, long ld,
     return cudaGetLastError();
 }
 
-// Standalone FP64 scatter (used where H is applied in FP64 to an FP32 block; the filter
-// steps fuse the scatter into the stencil kernels). A thread owns one covered node and
-// walks a strided subset of the columns, so the node's entry data stays in L1; the 32
-// threads of a warp hold 32 consecutive covered nodes of the same column.
-__global__ void __launch_bounds__(256)
+// Native FP64 scatter, used where H is applied in FP64 to an FP32 block (the H Y_f of the
+// mixed-precision Rayleigh-Ritz step). Same grid as the FP32 scatter below: one covered
+// node per thread, kScatCols columns per CTA, covered nodes along the grid's x dimension.
+constexpr int kScatRegs = 4;
+constexpr int kScatNodes = 256;
+constexpr int kScatCols = 16;
+
+__global__ void __launch_bounds__(kScatNodes)
 k_scatter_f64(double *out, long ld, int ncols, long nuniq, const int *__restrict__ uniq_node,
               const int *__restrict__ uniq_ptr, const int *__restrict__ ent_list,
               const int *__restrict__ ent_atom, const double *__restrict__ gchi,
               const double *__restrict__ C, double alpha)
 {
-    const long u = (long)blockIdx.x * 32 + threadIdx.x;
+    const long u = (long)blockIdx.x * kScatNodes + threadIdx.x;
     if (u >= nuniq) return;
+    const int c0 = blockIdx.y * kScatCols, c1 = min(ncols, c0 + kScatCols);
     const long node = uniq_node[u];
     const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
-    for (int c = threadIdx.y; c < ncols; c += blockDim.y) {
+#pragma unroll 2
+    for (int c = c0; c < c1; ++c) {
         double v = 0.0;
         for (int q = q0; q < q1; ++q) {
             const int e = ent_list[q];
@@ -205,25 +240,72 @@ k_scatter_f64(double *out, long ld, int ncols, long nuniq, const int *__restrict
     }
 }
 
-// FP32 blocks: Cs already holds alpha chi^T Y (FP32); same layout as k_scatter_f64.
-__global__ void __launch_bounds__(256)
+// FP32 blocks: Cs holds alpha chi^T Y as one float4 per (atom, column), Cs4[J * ncols + c],
+// and g4[q] the four h^3 gamma chi values of entry q. A thread owns one covered node and a
+// group of kScatCols columns; the grid's x dimension (dispatched first) runs over the
+// covered nodes, so the CTAs resident at one time sweep consecutive nodes of the same
+// columns (DRAM page locality for the read-modify-write of the output). A node's entries
+// (the atoms whose support holds it, ascending) are loaded into registers once; each
+// column then costs one 16-byte load per entry (L1/L2-resident) and one read-modify-write.
+// Nodes covered by more than kScatRegs atoms take the generic loop.
+
+template <int N>
+__device__ __forceinline__ void scatter_node_f32(float *o, long ld, int c0, int c1, int q0,
+                                                 int ncols, const int *__restrict__ nl_atom,
+                                                 const float4 *__restrict__ g4,
+                                                 const float4 *__restrict__ Cs4)
+{
+    float4 gq[N];
+    const float4 *cq[N];
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+        gq[t] = g4[q0 + t];
+        cq[t] = Cs4 + (long)nl_atom[q0 + t] * ncols;
+    }
+#pragma unroll 4
+    for (int c = c0; c < c1; ++c) {
+        float v = 0.0f;
+#pragma unroll
+        for (int t = 0; t < N; ++t) {
+            const float4 cc = cq[t][c];
+            v += gq[t].x * cc.x;
+            v += gq[t].y * cc.y;
+            v += gq[t].z * cc.z;
+            v += gq[t].w * cc.w;
+        }
+        float *oc = o + (long)c * ld;
+        *oc = *oc + v;
+    }
+}
+
+__global__ void __launch_bounds__(kScatNodes)
 k_scatter_f32(float *out, long ld, int ncols, long nuniq, const int *__restrict__ uniq_node,
               const int *__restrict__ uniq_ptr, const int *__restrict__ nl_atom,
-              const float *__restrict__ g, const float *__restrict__ Cs)
+              const float4 *__restrict__ g4, const float4 *__restrict__ Cs4)
 {
-    const long u = (long)blockIdx.x * 32 + threadIdx.x;
+    const long u = (long)blockIdx.x * kScatNodes + threadIdx.x;
     if (u >= nuniq) return;
-    const long node = uniq_node[u];
+    const int c0 = blockIdx.y * kScatCols, c1 = min(ncols, c0 + kScatCols);
+    float *o = out + uniq_node[u];
     const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
-    for (int c = threadIdx.y; c < ncols; c += blockDim.y) {
+    switch (q1 - q0) {
+    case 1: scatter_node_f32<1>(o, ld, c0, c1, q0, ncols, nl_atom, g4, Cs4); return;
+    case 2: scatter_node_f32<2>(o, ld, c0, c1, q0, ncols, nl_atom, g4, Cs4); return;
+    case 3: scatter_node_f32<3>(o, ld, c0, c1, q0, ncols, nl_atom, g4, Cs4); return;
+    case 4: scatter_node_f32<kScatRegs>(o, ld, c0, c1, q0, ncols, nl_atom, g4, Cs4); return;
+    default: break;
+    }
+    for (int c = c0; c < c1; ++c) {
         float v = 0.0f;
         for (int q = q0; q < q1; ++q) {
-            const float *cs = Cs + (long)nl_atom[q] * 4 * ncols + c;
-#pragma unroll
-            for (int l = 0; l < 4; ++l) v += g[4L * q + l] * cs[(long)l * ncols];
+            const float4 g = g4[q], cc = Cs4[(long)nl_atom[q] * ncols + c];
+            v += g.x * cc.x;
+            v += g.y * cc.y;
+            v += g.z * cc.z;
+            v += g.w * cc.w;
         }
-        float *o = out + node + (long)c * ld;
-        *o = *o + v;
+        float *oc = o + (long)c * ld;
+        *oc = *oc + v;
     }
 }
 
@@ -231,9 +313,12 @@ cudaError_t scatter_f32(const DevHam &H, const float *Cs, float *out, int ncols,
                         cudaStream_t st)
 {
     if (H.natoms == 0 || H.nuniq == 0 || ncols <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((H.nuniq + 31) / 32)), block(32, 8);
-    k_scatter_f32<<<grid, block, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node, H.uniq_ptr,
-                                          H.nl_atom, H.nl_gf, Cs);
+    dim3 grid((unsigned)((H.nuniq + kScatNodes - 1) / kScatNodes),
+              (unsigned)((ncols + kScatCols - 1) / kScatCols));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    k_scatter_f32<<<grid, kScatNodes, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node, H.uniq_ptr,
+                                               H.nl_atom, reinterpret_cast<const float4 *>(H.nl_gf),
+                                               reinterpret_cast<const float4 *>(Cs));
     note_launch();
     return cudaGetLastError();
 }
@@ -242,9 +327,12 @@ cudaError_t scatter_f64(const DevHam &H, const double *C, double *out, int ncols
                         double alpha, cudaStream_t st)
 {
     if (H.natoms == 0 || H.nuniq == 0 || ncols <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((H.nuniq + 31) / 32)), block(32, 8);
-    k_scatter_f64<<<grid, block, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node, H.uniq_ptr,
-                                          H.ent_list, H.ent_atom, H.gchi, C, alpha);
+    dim3 grid((unsigned)((H.nuniq + kScatNodes - 1) / kScatNodes),
+              (unsigned)((ncols + kScatCols - 1) / kScatCols));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    k_scatter_f64<<<grid, kScatNodes, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node,
+                                               H.uniq_ptr, H.ent_list, H.ent_atom, H.gchi, C,
+                                               alpha);
     note_launch();
     return cudaGetLastError();
 }

@@ -787,7 +787,7 @@ sparc_status sparc_lanczos_bounds(sparc_ctx *ctx, int ksteps, unsigned long long
     { PHASE(SPARC_PHASE_OTHER); CK(lanczos_bounds_final(ev, Q, beta, ksteps, keff, outb, ctx->st)); }
     CK(cudaMemcpyAsync(ctx->pin, outb, sizeof(double) * 2, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(ctx->pin_i, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaStreamSynchronize(ctx->st));
+    TRY(sparc_sync(ctx));
     if (ctx->pin_i[0] != 0)
         return fail(ctx, SPARC_ERR_TIMEOUT, "tridiagonal eigensolve failed (status %d)", ctx->pin_i[0]);
     *lo = ctx->pin[0];
@@ -832,6 +832,41 @@ sparc_status sparc_launch_count(long long *count)
     if (!count) return SPARC_ERR_ARG;
     *count = g_launches.load(std::memory_order_relaxed);
     return SPARC_OK;
+}
+
+sparc_status sparc_sync(sparc_ctx *ctx)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    ctx->err.clear();
+    CK(cudaMemcpyAsync(ctx->pin_i + 14, ctx->flags + 14, sizeof(int), cudaMemcpyDeviceToHost,
+                       ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (ctx->pin_i[14] != 0) {
+        CK(cudaMemsetAsync(ctx->flags + 14, 0, sizeof(int), ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        return fail(ctx, SPARC_ERR_TIMEOUT, "a stencil launch timed out waiting for a TMA load");
+    }
+    return SPARC_OK;
+}
+
+sparc_status sparc_selftest_timeout(sparc_ctx *ctx, int which)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    ctx->err.clear();
+    if (which == 0) {
+        CK(mbar_selftest(ctx->flags + 14, ctx->st));
+        return sparc_sync(ctx);
+    }
+    if (which == 1) {
+        int *status = ctx->flags + 6;
+        CK(barrier_selftest(reinterpret_cast<GridBarrier *>(ctx->flags + 8), status, ctx->st));
+        CK(cudaMemcpyAsync(ctx->pin_i, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemsetAsync(ctx->flags + 8, 0, sizeof(GridBarrier), ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        if (ctx->pin_i[0] == 4) return fail(ctx, SPARC_ERR_TIMEOUT, "grid barrier timed out");
+        return SPARC_OK;
+    }
+    return fail(ctx, SPARC_ERR_ARG, "which must be 0 (mbarrier) or 1 (grid barrier), got %d", which);
 }
 
 }  // extern "C"

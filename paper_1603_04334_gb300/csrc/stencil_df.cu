@@ -185,19 +185,27 @@ static void split_host(double x, float &h, float &l)
 
 // Nonlocal scatter for FP64 blocks in pair arithmetic: out(p, c) += sum_{q at p} sum_l
 // g(q, l) Cs(atom(q), l, c), Cs = alpha chi^T Y as pairs (k_project_df). A thread owns one
-// covered node and walks a strided subset of the columns (the node's entries stay in L1;
-// a warp holds 32 consecutive covered nodes of one column, so the out accesses coalesce).
-// The pair sum is added to the FP64 output with one FP64 add.
-__global__ void __launch_bounds__(256)
+// covered node and a group of kScatCols columns; the grid's x dimension (dispatched first)
+// runs over the covered nodes, so the CTAs resident at one time sweep consecutive nodes of
+// the same columns (coalesced, DRAM-page-local read-modify-write of the output; the node's
+// entries stay in L1). The pair sum is added to the FP64 output with one FP64 add.
+namespace {
+constexpr int kScatNodes = 256;
+constexpr int kScatCols = 8;
+}  // namespace
+
+__global__ void __launch_bounds__(kScatNodes)
 k_scatter_df(double *out, long ld, int ncols, long nuniq, const int *__restrict__ uniq_node,
              const int *__restrict__ uniq_ptr, const int *__restrict__ nl_atom,
              const float2 *__restrict__ g, const float2 *__restrict__ Cs)
 {
-    const long u = (long)blockIdx.x * 32 + threadIdx.x;
+    const long u = (long)blockIdx.x * kScatNodes + threadIdx.x;
     if (u >= nuniq) return;
+    const int c0 = blockIdx.y * kScatCols, c1 = min(ncols, c0 + kScatCols);
     const long node = uniq_node[u];
     const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
-    for (int c = threadIdx.y; c < ncols; c += blockDim.y) {
+#pragma unroll 2
+    for (int c = c0; c < c1; ++c) {
         float vh = 0.0f, vl = 0.0f;
         for (int q = q0; q < q1; ++q) {
             const float2 *cs = Cs + (long)nl_atom[q] * 4 * ncols + c;
@@ -213,9 +221,11 @@ cudaError_t scatter_f64_df(const DevHam &H, const float2 *Cs, double *out, int n
                            cudaStream_t st)
 {
     if (H.natoms == 0 || H.nuniq == 0 || ncols <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((H.nuniq + 31) / 32)), block(32, 8);
-    k_scatter_df<<<grid, block, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node, H.uniq_ptr,
-                                         H.nl_atom, H.nl_gdf, Cs);
+    dim3 grid((unsigned)((H.nuniq + kScatNodes - 1) / kScatNodes),
+              (unsigned)((ncols + kScatCols - 1) / kScatCols));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    k_scatter_df<<<grid, kScatNodes, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node, H.uniq_ptr,
+                                              H.nl_atom, H.nl_gdf, Cs);
     note_launch();
     return cudaGetLastError();
 }

@@ -17,6 +17,12 @@
 // newly arrived plane. The queue needs planes t .. t+6 of the ring, so with kStages = 10
 // the loads run 4 planes ahead of the compute.
 //
+// Y_{j-1} (one third of the step's traffic) rides in the same ring: the TMA load that
+// brings plane t of Y also brings the halo-free tile of Y_{j-1} at the plane whose compute
+// first needs plane t (z - 6), completing on the same mbarrier, so every HBM stream of the
+// step is an asynchronous bulk copy. V_eff (one plane shared by all columns, L2-resident)
+// is prefetched into registers one plane ahead.
+//
 // Requirements (checked on the host, else the plain kernel of stencil.cu runs): n0 and ld
 // multiples of 4 and 16-byte aligned block pointers (TMA strides and float4 accesses).
 #include "internal.cuh"
@@ -34,16 +40,19 @@ constexpr int kR = kRadius;  // 6
 constexpr int kW = kBX + 16; // box width: 8 left (aligned) + 32 + 8 right
 constexpr int kH = kTY + 2 * kR;
 constexpr int kStages = 10;
-constexpr int kPlaneBytes = kW * kH * 4;
+constexpr int kPlaneBytes = kW * kH * 4;   // Y plane with halo
+constexpr int kTileBytes = kBX * kTY * 4;  // Y_{j-1} tile, no halo
+constexpr int kStageFloats = kW * kH + kBX * kTY;
 constexpr unsigned kWaitLimit = 1u << 22;
 }  // namespace
 
 __global__ void __launch_bounds__(kTX *kTY)
-k_stencil_f32_tma(const __grid_constant__ CUtensorMap tmY, const float *Yprev, float *out,
-                  const float *__restrict__ V, int n0, int n1, int n2, long ld, int nzc,
-                  int zchunk, StepCoef<float> cf, int *err)
+k_stencil_f32_tma(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmP,
+                  bool hasP, float *out, const float *__restrict__ V, int n0, int n1, int n2,
+                  long ld, int nzc, int zchunk, StepCoef<float> cf, int *err)
 {
-    extern __shared__ __align__(128) float sm[];  // [kStages][kH][kW]
+    // stage s: Y plane [kH][kW] then the Y_{j-1} tile [kTY][kBX]
+    extern __shared__ __align__(128) float sm[];
     __shared__ __align__(8) uint64_t full[kStages];
     __shared__ int timed_out;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -57,29 +66,34 @@ k_stencil_f32_tma(const __grid_constant__ CUtensorMap tmY, const float *Yprev, f
     const bool act = (i < n0) && (j < n1);
     const long plane = (long)n0 * n1;
     const long pij = (long)i + (long)n0 * j;
-    const float *Pc = Yprev ? Yprev + (long)col * ld : nullptr;
     float *Oc = out + (long)col * ld;
 
     if (tid == 0) {
         tma_prefetch_desc(&tmY);
+        if (hasP) tma_prefetch_desc(&tmP);
         for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
         mbar_fence_init();
         timed_out = 0;
     }
     __syncthreads();
     int issued = 0;  // planes 0 .. issued-1 have been handed to the TMA unit (thread 0)
-    auto issue = [&](int t) {  // plane t (z = k0 - 6 + t) into stage t % kStages
+    // plane t of Y (z = k0 - 6 + t) into stage t % kStages, with the Y_{j-1} tile of the
+    // plane computed when plane t completes the z queue (z - 6), if that plane is in range
+    auto issue = [&](int t) {
         const int s = t % kStages;
-        mbar_arrive_expect_tx(&full[s], kPlaneBytes);
-        tma_load_4d(sm + (long)s * kH * kW, &tmY, &full[s], i0 - 8, j0 - kR, k0 - kR + t, col);
+        const bool p = hasP && t >= 2 * kR;
+        float *st = sm + (long)s * kStageFloats;
+        mbar_arrive_expect_tx(&full[s], kPlaneBytes + (p ? kTileBytes : 0));
+        tma_load_4d(st, &tmY, &full[s], i0 - 8, j0 - kR, k0 - kR + t, col);
+        if (p) tma_load_4d(st + kH * kW, &tmP, &full[s], i0, j0, k0 - 2 * kR + t, col);
         issued = t + 1;
     };
     auto wait = [&](int t) -> bool {
         return mbar_wait(&full[t % kStages], (unsigned)((t / kStages) & 1), kWaitLimit);
     };
     auto center = [&](int t) -> float4 {
-        return *reinterpret_cast<const float4 *>(sm + ((long)(t % kStages) * kH + kR + ty) * kW +
-                                                 8 + 4 * tx);
+        return *reinterpret_cast<const float4 *>(sm + (long)(t % kStages) * kStageFloats +
+                                                 (kR + ty) * kW + 8 + 4 * tx);
     };
     if (tid == 0)
         for (int t = 0; t < kStages && t < T; ++t) issue(t);
@@ -103,17 +117,16 @@ k_stencil_f32_tma(const __grid_constant__ CUtensorMap tmY, const float *Yprev, f
     if (!ok) timed_out = 1;
     __syncthreads();
 
+    float4 vv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (act) vv = *reinterpret_cast<const float4 *>(V + pij + (long)k0 * plane);
     for (int tc = kR; tc < T - kR && !timed_out; ++tc) {  // plane tc is z = k0 - 6 + tc
         const int k = k0 - kR + tc;
         const long p = pij + (long)k * plane;
-        float4 vv = make_float4(0.f, 0.f, 0.f, 0.f), pv = vv;
-        if (act) {
-            vv = *reinterpret_cast<const float4 *>(V + p);
-            if (Pc) pv = *reinterpret_cast<const float4 *>(Pc + p);
-        }
+        float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act && k + 1 < k1) vn = *reinterpret_cast<const float4 *>(V + p + plane);
         if (!wait(tc + kR)) timed_out = 1;
         q[2 * kR] = center(tc + kR);
-        const float *pl = sm + (long)(tc % kStages) * kH * kW;
+        const float *pl = sm + (long)(tc % kStages) * kStageFloats;
         const float *row = pl + (kR + ty) * kW + 4 * tx;  // x offset 4tx = node i - 8
         float f[20];
 #pragma unroll
@@ -141,14 +154,18 @@ k_stencil_f32_tma(const __grid_constant__ CUtensorMap tmY, const float *Yprev, f
             }
         }
         if (act) {
-            const float *p4 = &pv.x;
-            float4 o;
-            o.x = Pc ? acc[0] - cf.beta * p4[0] : acc[0];
-            o.y = Pc ? acc[1] - cf.beta * p4[1] : acc[1];
-            o.z = Pc ? acc[2] - cf.beta * p4[2] : acc[2];
-            o.w = Pc ? acc[3] - cf.beta * p4[3] : acc[3];
+            float4 o = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            if (hasP) {
+                const float4 pv = *reinterpret_cast<const float4 *>(
+                    sm + (long)((tc + kR) % kStages) * kStageFloats + kH * kW + ty * kBX + 4 * tx);
+                o.x -= cf.beta * pv.x;
+                o.y -= cf.beta * pv.y;
+                o.z -= cf.beta * pv.z;
+                o.w -= cf.beta * pv.w;
+            }
             *reinterpret_cast<float4 *>(Oc + p) = o;
         }
+        vv = vn;
 #pragma unroll
         for (int t = 0; t < 2 * kR; ++t) q[t] = q[t + 1];
         __syncthreads();  // every thread is done with plane tc's stage
@@ -198,29 +215,61 @@ cudaError_t stencil_f32_tma(const DevHam &H, const float *Y, const float *Yprev,
     cudaError_t e = get_encoder();
     if (e != cudaSuccess) return e;
     static bool attr_set = false;
-    const int smem = kStages * kPlaneBytes;
+    const int smem = kStages * kStageFloats * 4;
     if (!attr_set) {
         e = cudaFuncSetAttribute(k_stencil_f32_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    CUtensorMap map;
-    cuuint64_t dims[4] = {(cuuint64_t)H.n0, (cuuint64_t)H.n1, (cuuint64_t)H.n2, (cuuint64_t)ncols};
-    cuuint64_t strides[3] = {(cuuint64_t)H.n0 * 4, (cuuint64_t)H.n0 * H.n1 * 4,
-                             (cuuint64_t)ld * 4};
-    cuuint32_t box[4] = {(cuuint32_t)kW, (cuuint32_t)kH, 1, 1};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)Y, dims, strides, box,
-                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    // both maps view a block as (x, y, z, column); they differ in base and box
+    auto encode = [&](CUtensorMap *m, const float *base, cuuint32_t bx, cuuint32_t by) {
+        cuuint64_t dims[4] = {(cuuint64_t)H.n0, (cuuint64_t)H.n1, (cuuint64_t)H.n2,
+                              (cuuint64_t)ncols};
+        cuuint64_t strides[3] = {(cuuint64_t)H.n0 * 4, (cuuint64_t)H.n0 * H.n1 * 4,
+                                 (cuuint64_t)ld * 4};
+        cuuint32_t box[4] = {bx, by, 1, 1};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)base, dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    };
+    CUtensorMap mapY, mapP;
+    if (encode(&mapY, Y, kW, kH) != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    if (Yprev) {
+        if (encode(&mapP, Yprev, kBX, kTY) != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    } else {
+        mapP = mapY;  // never dereferenced: the kernel issues no Y_{j-1} load
+    }
     const int gx = (H.n0 + kBX - 1) / kBX, gy = (H.n1 + kTY - 1) / kTY;
     int nzc, zchunk;
     stencil_z_split(H.n2, (long)gx * gy, ncols, nzc, zchunk);
     dim3 grid(gx, gy, ncols * nzc), block(kTX, kTY);
-    k_stencil_f32_tma<<<grid, block, smem, st>>>(map, Yprev, out, H.Vf, H.n0, H.n1, H.n2, ld, nzc,
-                                                 zchunk, cf, err);
+    k_stencil_f32_tma<<<grid, block, smem, st>>>(mapY, mapP, Yprev != nullptr, out, H.Vf, H.n0,
+                                                 H.n1, H.n2, ld, nzc, zchunk, cf, err);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Failure-detection self-test of the bounded mbarrier wait used above: the barrier expects
+// two arrivals and gets one, so every thread's wait ends through its probe limit
+// (~65 ms here); *err is set to 1 exactly as the stencil does on a lost TMA load.
+__global__ void __launch_bounds__(32) k_mbar_selftest(int *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 2);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_arrive(&bar);
+    const bool ok = mbar_wait(&bar, 0u, 1u << 20);
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+cudaError_t mbar_selftest(int *err, cudaStream_t st)
+{
+    k_mbar_selftest<<<1, 32, 0, st>>>(err);
     note_launch();
     return cudaGetLastError();
 }

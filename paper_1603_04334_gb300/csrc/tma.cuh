@@ -35,6 +35,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned by
                  : "memory");
 }
 
+// Plain arrival (no transaction count).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // One non-blocking probe (test_wait never suspends): true once the phase with the given
 // parity has completed.
 __device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned parity)

@@ -37,7 +37,7 @@ EXPORTS = ("sparc_create", "sparc_destroy", "sparc_last_error", "sparc_get_veff"
            "sparc_cheb_filter", "sparc_orth_rr", "sparc_gram", "sparc_chefsi_step",
            "sparc_profile_enable",
            "sparc_profile_read", "sparc_profile_reset", "sparc_launch_count",
-           "sparc_gram_noalloc")
+           "sparc_gram_noalloc", "sparc_sync", "sparc_selftest_timeout")
 
 PHASES = ("stencil", "project", "scatter", "gram", "dense", "rotate", "other")
 
@@ -95,6 +95,8 @@ def load(build_if_missing: bool = True):
     L.sparc_profile_read.argtypes = [vp, ip, C.POINTER(C.c_longlong), dp]
     L.sparc_profile_reset.argtypes = [vp]
     L.sparc_launch_count.argtypes = [C.POINTER(C.c_longlong)]
+    L.sparc_sync.argtypes = [vp]
+    L.sparc_selftest_timeout.argtypes = [vp, ip]
     # allocation-free G = A^T B: (A, B, nd, ncols, ld, G, stream)
     L.sparc_gram_noalloc.argtypes = [vp, vp, C.c_long, ip, C.c_long, vp, vp]
     for name in EXPORTS:
@@ -208,6 +210,16 @@ class Context:
 
     def profile_reset(self):
         self._check(self._L.sparc_profile_reset(self._h))
+
+    def sync(self):
+        """Waits for the context's stream; raises SparcError (SPARC_ERR_TIMEOUT) if a kernel
+        of an earlier asynchronous call gave up a bounded wait."""
+        self._check(self._L.sparc_sync(self._h))
+
+    def selftest_timeout(self, which: int) -> int:
+        """Runs a kernel whose bounded wait cannot complete (0: mbarrier, 1: grid barrier)
+        and returns the status code the library reports (SPARC_ERR_TIMEOUT expected)."""
+        return int(self._L.sparc_selftest_timeout(self._h, int(which)))
 
     def profile_read(self) -> dict:
         """{phase: (launches, device ms)} accumulated since the last reset."""
