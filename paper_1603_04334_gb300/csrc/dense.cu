@@ -15,8 +15,10 @@
 // Eigenvalues are sorted ascending and each eigenvector column is signed so that its
 // largest-magnitude entry is positive (lowest index on ties).
 //
-// Every kernel here is one CTA of 1024 threads working on column-major matrices in
-// global memory (L1/L2 resident for the sizes used). All loops are bounded.
+// Matrices are column-major in global memory (L2-resident for the sizes used). The k x k
+// Lanczos eigensolve and the final sort run in one CTA of 1024 threads; the Ns x Ns
+// reduction runs on many SMs (below). All loops and waits are bounded.
+#include "grid.cuh"
 #include "internal.cuh"
 
 namespace sparc {
@@ -174,137 +176,178 @@ __device__ void sort_and_sign(const double *dg, long ds, const double *V, int n,
 }
 }  // namespace
 
-long dense_work_elems(int ns) { return 3L * ns * ns + 8L * ns + 64; }
+long dense_work_elems(int ns) { return 5L * ns * ns + 8L * ns + 64; }
 
-// Symmetrise, Cholesky M = L L^T (L overwrites M), A = L^-1 H_s L^-T into work + n^2.
-__global__ void __launch_bounds__(NT)
-k_dense_pre(double *M, double *Hs, int n, double *work, int *status)
+// ---- multi-SM reduction of the generalized problem ----------------------------------
+// Cholesky M_s = L L^T on a cooperative grid (right-looking, one bounded grid barrier per
+// column), the triangular inverse U = L^-T (one warp per column, no barrier), and the
+// products A = U^T (H_s U) and Cf = U Q as FP32-pair GEMMs (gram_df.cu); the eigensolve
+// in between is the multi-SM Jacobi of jacobi.cu. Same reduction and pivot rule as the
+// dsygv-style single-CTA path it replaces, with the dense products spread over all SMs.
+namespace {
+constexpr int CT = 256;       // threads per CTA of the cooperative Cholesky
+constexpr int kInvWarps = 4;  // columns per CTA of the triangular inverse
+}  // namespace
+
+// Symmetrise M_s and H_s and check them for non-finite entries (status 2); Cholesky with
+// the pivot rule pivot_j > 4 n eps M_jj (status 1 otherwise); writes L row-major into Lr
+// (Lr[k + r n] = L_rk, zero above the diagonal) and 1 / L_jj into dinv. Every CTA reads
+// the same pivot after the barrier, so all take the same decision. M is overwritten by the
+// Schur complements; odiag holds the original diagonal. A barrier that times out sets
+// status 4.
+__global__ void __launch_bounds__(CT)
+k_chol_grid(double *M, double *Hs, int n, double *Lr, double *dinv, double *odiag,
+            GridBarrier *bar, int *status)
 {
-    __shared__ int flag;
-    const int tid = threadIdx.x;
+    const unsigned nb = gridDim.x;
+    const long gtid = (long)blockIdx.x * CT + threadIdx.x, gs = (long)nb * CT;
     const long nn = (long)n * n;
-    double *W = work;            // L^-1 H_s
-    double *A = work + nn;       // L^-1 H_s L^-T, then Jacobi working copy
-    double *V = work + 2 * nn;   // Jacobi eigenvectors
-    if (tid == 0) flag = 0;
-    __syncthreads();
-    // 1. symmetrise, check finiteness
-    for (long t = tid; t < nn; t += NT) {
+    auto sync = [&]() -> bool {
+        if (grid_barrier(bar, nb)) return true;
+        if (threadIdx.x == 0) atomicExch(status, 4);
+        return false;
+    };
+    for (long t = gtid; t < nn; t += gs) {
         const int i = (int)(t % n), j = (int)(t / n);
         if (i < j) {
-            const double m = 0.5 * (M[i + (long)j * n] + M[j + (long)i * n]);
-            const double h = 0.5 * (Hs[i + (long)j * n] + Hs[j + (long)i * n]);
-            M[i + (long)j * n] = m;
-            M[j + (long)i * n] = m;
-            Hs[i + (long)j * n] = h;
-            Hs[j + (long)i * n] = h;
+            const long tt = j + (long)i * n;
+            const double m = 0.5 * (M[t] + M[tt]), h = 0.5 * (Hs[t] + Hs[tt]);
+            M[t] = m;
+            M[tt] = m;
+            Hs[t] = h;
+            Hs[tt] = h;
+            if (!isfinite(m) || !isfinite(h)) atomicExch(status, 2);
+        } else if (i == j) {
+            if (!isfinite(M[t]) || !isfinite(Hs[t])) atomicExch(status, 2);
+            odiag[i] = M[t];
         }
-        if (!isfinite(M[t]) || !isfinite(Hs[t])) flag = 2;
     }
-    __syncthreads();
-    if (flag) {
-        if (tid == 0) *status = flag;
-        return;
-    }
-    // 2. Cholesky M = L L^T (lower, in place), right-looking. M_s counts as numerically
-    //    positive definite when every pivot exceeds 4 n eps times its original diagonal
-    //    entry (pivot / diagonal = squared sine of the angle between a column and the span
-    //    of the previous ones). The diagonal is saved in V before it is overwritten.
-    for (int j = tid; j < n; j += NT) V[j] = M[j + (long)j * n];
-    __syncthreads();
+    if (!sync()) return;
+    if (*((volatile int *)status) != 0) return;
     for (int j = 0; j < n; ++j) {
-        if (tid == 0) {
-            const double d = M[j + (long)j * n];
-            if (!(d > 4.0 * n * kEps * V[j]) || !isfinite(d))
-                flag = 1;
-            else
-                M[j + (long)j * n] = sqrt(d);
-        }
-        __syncthreads();
-        if (flag) {
-            if (tid == 0) *status = 1;
+        const double d = __ldcg(M + j + (long)j * n);
+        if (!(d > 4.0 * n * kEps * __ldcg(odiag + j)) || !isfinite(d)) {
+            if (gtid == 0) atomicExch(status, 1);
             return;
         }
-        const double djj = M[j + (long)j * n];
-        for (int i = j + 1 + tid; i < n; i += NT) M[i + (long)j * n] /= djj;
-        __syncthreads();
-        const int mrem = n - j - 1;
-        for (long t = tid; t < (long)mrem * mrem; t += NT) {
-            const int rr = j + 1 + (int)(t % mrem), cc = j + 1 + (int)(t / mrem);
-            if (rr >= cc) M[rr + (long)cc * n] -= M[rr + (long)j * n] * M[cc + (long)j * n];
+        const double inv = 1.0 / d;
+        const int m = n - 1 - j;
+        for (long t = gtid; t < (long)m * m; t += gs) {
+            const int rr = j + 1 + (int)(t % m), cc = j + 1 + (int)(t / m);
+            if (rr >= cc) {
+                const double a = __ldcg(M + rr + (long)j * n), b = __ldcg(M + cc + (long)j * n);
+                M[rr + (long)cc * n] = __ldcg(M + rr + (long)cc * n) - a * b * inv;
+            }
         }
-        __syncthreads();
+        if (!sync()) return;
     }
-    // 3. W = L^-1 H_s (forward substitution, one thread per column)
-    for (int c = tid; c < n; c += NT) {
-        for (int r = 0; r < n; ++r) {
-            double s = Hs[r + (long)c * n];
-            for (int k = 0; k < r; ++k) s -= M[r + (long)k * n] * W[k + (long)c * n];
-            W[r + (long)c * n] = s / M[r + (long)r * n];
-        }
+    // L_jj = sqrt(pivot_j), L_rj = M_rj / L_jj
+    for (long t = gtid; t < n; t += gs) {
+        const double l = sqrt(__ldcg(M + t + t * n));
+        odiag[t] = l;
+        dinv[t] = 1.0 / l;
     }
-    __syncthreads();
-    // 4. A = L^-1 W^T  (= L^-1 H_s L^-T), then symmetrise
-    for (int c = tid; c < n; c += NT) {
-        for (int r = 0; r < n; ++r) {
-            double s = W[c + (long)r * n];
-            for (int k = 0; k < r; ++k) s -= M[r + (long)k * n] * A[k + (long)c * n];
-            A[r + (long)c * n] = s / M[r + (long)r * n];
-        }
+    if (!sync()) return;
+    for (long t = gtid; t < nn; t += gs) {
+        const int r = (int)(t % n), k = (int)(t / n);  // column-major walk of M
+        double v = 0.0;
+        if (k < r)
+            v = __ldcg(M + t) * __ldcg(dinv + k);
+        else if (k == r)
+            v = __ldcg(odiag + r);
+        Lr[k + (long)r * n] = v;
     }
-    __syncthreads();
-    for (long t = tid; t < nn; t += NT) {
-        const int i = (int)(t % n), j = (int)(t / n);
-        if (i < j) {
-            const double a = 0.5 * (A[i + (long)j * n] + A[j + (long)i * n]);
-            A[i + (long)j * n] = a;
-            A[j + (long)i * n] = a;
-        }
-    }
-    if (tid == 0) *status = 0;
 }
 
-// After the multi-SM Jacobi (jacobi.cu): sort and sign the eigenpairs (Q into W) and form
-// Cf = L^-T Q by backward substitution, one thread per column.
+// U = L^-T: warp c solves L x = e_c by forward substitution (rows c .. n-1; each row's dot
+// product is split over the lanes in a fixed order and lane 0's sum is used), then writes
+// row c of U (U_cr = x_r, zero for r < c).
+__global__ void __launch_bounds__(32 * kInvWarps)
+k_tri_inv(const double *__restrict__ Lr, const double *__restrict__ dinv, int n, double *U,
+          const int *status)
+{
+    __shared__ double xs[kInvWarps][kMaxDense];
+    if (*((volatile const int *)status) != 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kInvWarps + warp;
+    if (c >= n) return;
+    double *x = xs[warp];
+    for (int r = c; r < n; ++r) {
+        const double *row = Lr + (long)r * n;
+        double sum = 0.0;
+        for (int k = c + lane; k < r; k += 32) sum += row[k] * x[k];
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        sum = __shfl_sync(0xffffffffu, sum, 0);
+        if (lane == 0) x[r] = ((r == c ? 1.0 : 0.0) - sum) * dinv[r];
+        __syncwarp();
+    }
+    for (int r = lane; r < n; r += 32) U[c + (long)r * n] = r >= c ? x[r] : 0.0;
+}
+
+// After the multi-SM Jacobi: sort the eigenvalues ascending and sign the eigenvectors
+// (largest |entry| positive, lowest index on ties) into Q.
 __global__ void __launch_bounds__(NT)
-k_dense_post(const double *L, int n, const double *diag, const double *V, double *ritz,
-             double *Cf, double *W, int *status, const GridBarrier *bar)
+k_dense_sort(int n, const double *diag, const double *V, double *ritz, double *Q, int *status,
+             const GridBarrier *bar)
 {
     __shared__ int rank[kMaxDense];
-    const int tid = threadIdx.x;
     if (*status != 0) return;
     if (bar->err) {
-        if (tid == 0) *status = 4;
+        if (threadIdx.x == 0) *status = 4;
         return;
     }
-    sort_and_sign(diag, 1, V, n, ritz, W, rank);
-    const double *M = L;
-    for (int c = tid; c < n; c += NT) {
-        for (int r = n - 1; r >= 0; --r) {
-            double s = W[r + (long)c * n];
-            for (int k = r + 1; k < n; ++k) s -= M[k + (long)r * n] * Cf[k + (long)c * n];
-            Cf[r + (long)c * n] = s / M[r + (long)r * n];
-        }
-    }
-    if (tid == 0) *status = 0;
+    sort_and_sign(diag, 1, V, n, ritz, Q, rank);
 }
+
+static int g_chol_blocks = 0;  // co-resident CTAs of k_chol_grid (queried once)
 
 cudaError_t dense_rr(double *M, double *Hs, int ns, double *ritz, double *Cf, double *work,
                      int *status, cudaStream_t st)
 {
     if (ns <= 0 || ns > kMaxDense) return cudaErrorInvalidValue;
     const long nn = (long)ns * ns;
-    double *W = work, *A = work + nn, *V = work + 2 * nn, *diag = work + 3 * nn;
+    double *R0 = work;            // L row-major, then H_s U, then Jacobi's second copy, then Q
+    double *A = work + nn;        // U^T H_s U, Jacobi's working copy
+    double *V = work + 2 * nn;    // Jacobi eigenvectors
+    double *U = work + 3 * nn;    // L^-T
+    double *part = work + 4 * nn; // Gram partials (one row slice for ns <= 2048 rows)
+    double *diag = work + 5 * nn, *dinv = diag + ns, *odiag = dinv + ns;
     GridBarrier *bar = (GridBarrier *)(status + 8);
-    k_dense_pre<<<1, NT, 0, st>>>(M, Hs, ns, work, status);
+    cudaError_t e;
+    if (g_chol_blocks == 0) {
+        int dev = 0, sms = 0, per = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_grid, CT, 0)) !=
+            cudaSuccess)
+            return e;
+        g_chol_blocks = sms * (per > 0 ? per : 1);
+    }
+    long want = (nn / 2 + CT - 1) / CT;
+    if (want < 1) want = 1;
+    int G = (int)(want < g_chol_blocks ? want : g_chol_blocks);
+    if (G > 152) G = 152;
+    if ((e = cudaMemsetAsync(status, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return e;
+    {
+        void *args[] = {&M, &Hs, &ns, &R0, &dinv, &odiag, &bar, &status};
+        e = cudaLaunchCooperativeKernel((const void *)k_chol_grid, dim3(G), dim3(CT), args, 0, st);
+        note_launch();
+        if (e != cudaSuccess) return e;
+    }
+    k_tri_inv<<<(ns + kInvWarps - 1) / kInvWarps, 32 * kInvWarps, 0, st>>>(R0, dinv, ns, U,
+                                                                            status);
     note_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = jacobi_grid(A, W, V, diag, ns, bar, status, status + 12, st);
-    if (e != cudaSuccess) return e;
-    k_dense_post<<<1, NT, 0, st>>>(M, ns, diag, V, ritz, Cf, W, status, bar);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = rotate_f64(Hs, ns, ns, ns, U, R0, ns, st)) != cudaSuccess) return e;  // H_s U
+    if ((e = gram_f64(U, ns, R0, ns, ns, ns, A, part, st, true)) != cudaSuccess) return e;
+    if ((e = jacobi_grid(A, R0, V, diag, ns, bar, status, status + 12, st)) != cudaSuccess)
+        return e;
+    k_dense_sort<<<1, NT, 0, st>>>(ns, diag, V, ritz, R0, status, bar);
     note_launch();
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return rotate_f64(U, ns, ns, ns, R0, Cf, ns, st);  // Cf = U Q
 }
 
 __global__ void __launch_bounds__(NT)

@@ -18,6 +18,7 @@
 // cooperatively (all CTAs co-resident), and every wait is bounded: after kBarrierSpins
 // polls the waiting CTA raises an error flag, every CTA leaves at its next barrier and the
 // host reports SPARC_ERR_TIMEOUT.
+#include "grid.cuh"
 #include "internal.cuh"
 
 namespace sparc {
@@ -26,7 +27,6 @@ namespace {
 constexpr int NT = 256;
 constexpr int kMaxSweeps = 60;
 constexpr double kEps = 2.220446049250313e-16;
-constexpr unsigned long long kBarrierSpins = 1ull << 25;  // ~2 s of 64 ns sleeps
 
 __device__ __forceinline__ void pair_of(int r, int k, int m, int &p, int &q)
 {
@@ -45,36 +45,6 @@ __device__ __forceinline__ void pair_of(int r, int k, int m, int &p, int &q)
 }
 
 // Returns false (to every thread of the CTA) once any CTA has hit the spin limit.
-__device__ bool grid_barrier(GridBarrier *b, unsigned nblocks,
-                             unsigned long long spins = kBarrierSpins)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *vg = &b->gen;
-        volatile int *ve = &b->err;
-        const unsigned g = *vg;
-        __threadfence();
-        if (atomicAdd(&b->count, 1u) == nblocks - 1u) {
-            atomicExch(&b->count, 0u);
-            __threadfence();
-            atomicAdd(&b->gen, 1u);
-        } else {
-            unsigned long long it = 0;
-            // leaves when the generation moves on, when another CTA has given up, or after
-            // `spins` polls (then it raises the flag itself)
-            while (*vg == g && *ve == 0) {
-                if (++it > spins) {
-                    atomicExch(&b->err, 1);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return *((volatile int *)&b->err) == 0;
-}
 }  // namespace
 
 __global__ void __launch_bounds__(NT)
@@ -112,9 +82,10 @@ k_jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrie
                 pair_of(r, k, m, p, q);
                 double c = 1.0, s = 0.0;
                 if (q < n) {
-                    const double apq = cur[p + (long)q * n];
+                    const double apq = __ldcg(cur + p + (long)q * n);
                     if (fabs(apq) > thr) {
-                        const double app = cur[p + (long)p * n], aqq = cur[q + (long)q * n];
+                        const double app = __ldcg(cur + p + (long)p * n);
+                        const double aqq = __ldcg(cur + q + (long)q * n);
                         const double tau = (aqq - app) / (2.0 * apq);
                         const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                         c = 1.0 / sqrt(1.0 + t * t);
@@ -134,10 +105,10 @@ k_jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrie
                 const int p1 = sp[k1], q1 = sq[k1], p2 = sp[k2], q2 = sq[k2];
                 const bool v1 = q1 < n, v2 = q2 < n;
                 const double c1 = sc[k1], s1 = ss[k1], c2 = sc[k2], s2 = ss[k2];
-                const double app = cur[p1 + (long)p2 * n];
-                const double apq = v2 ? cur[p1 + (long)q2 * n] : 0.0;
-                const double aqp = v1 ? cur[q1 + (long)p2 * n] : 0.0;
-                const double aqq = (v1 && v2) ? cur[q1 + (long)q2 * n] : 0.0;
+                const double app = __ldcg(cur + p1 + (long)p2 * n);
+                const double apq = v2 ? __ldcg(cur + p1 + (long)q2 * n) : 0.0;
+                const double aqp = v1 ? __ldcg(cur + q1 + (long)p2 * n) : 0.0;
+                const double aqq = (v1 && v2) ? __ldcg(cur + q1 + (long)q2 * n) : 0.0;
                 const double bpp = c1 * app - s1 * aqp, bpq = c1 * apq - s1 * aqq;
                 const double bqp = s1 * app + c1 * aqp, bqq = s1 * apq + c1 * aqq;
                 nxt[p1 + (long)p2 * n] = c2 * bpp - s2 * bpq;
@@ -152,7 +123,7 @@ k_jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrie
                 if (s == 0.0) continue;
                 const double c = sc[k];
                 const int p = sp[k], q = sq[k];
-                const double vp = V[row + (long)p * n], vq = V[row + (long)q * n];
+                const double vp = __ldcg(V + row + (long)p * n), vq = __ldcg(V + row + (long)q * n);
                 V[row + (long)p * n] = c * vp - s * vq;
                 V[row + (long)q * n] = s * vp + c * vq;
             }
@@ -168,7 +139,7 @@ k_jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrie
             break;
         }
     }
-    for (long i = gtid; i < n; i += gstride) diag[i] = cur[i + i * n];
+    for (long i = gtid; i < n; i += gstride) diag[i] = __ldcg(cur + i + i * n);
     if (gtid == 0) {
         *sweeps_out = sweeps;
         if (sweeps < 0) *status = 3;

@@ -180,11 +180,4 @@ cudaError_t stencil_f32(const DevHam &H, const float *Y, const float *Yprev, flo
                                        make_coef(H, alpha, shift, beta), st);
 }
 
-cudaError_t stencil_f32in_f64(const DevHam &H, const float *Y, double *out, int ncols,
-                              long ld, cudaStream_t st)
-{
-    return launch<float, double, double>(H, Y, (const double *)nullptr, out, H.V, ncols, ld,
-                                         make_coef(H, 1.0, 0.0, 0.0), st);
-}
-
 }  // namespace sparc

@@ -55,9 +55,11 @@ __device__ __forceinline__ float2 pair_add(float2 a, float2 b)
     return make_float2(s, (a.y + b.y) + e);
 }
 
-template <int BX, int BY>
+// TI is the input block's type: FP64, or FP32 (an FP32 value is the exact pair (y, 0); the
+// mixed-precision Rayleigh-Ritz step applies H in FP64 to the FP32 filtered block).
+template <typename TI, int BX, int BY>
 __global__ void __launch_bounds__(BX *BY)
-k_stencil_df(const double *__restrict__ Y, const double *Yprev, double *out,
+k_stencil_df(const TI *__restrict__ Y, const double *Yprev, double *out,
              const float2 *__restrict__ Vdf, int n0, int n1, int n2, long ld, int nzc, int zchunk,
              DfCoef cf)
 {
@@ -72,7 +74,7 @@ k_stencil_df(const double *__restrict__ Y, const double *Yprev, double *out,
     const int k0 = (blockIdx.z % nzc) * zchunk;
     const int k1 = min(n2, k0 + zchunk);
     const long plane = (long)n0 * n1;
-    const double *Yc = Y + (long)col * ld;
+    const TI *Yc = Y + (long)col * ld;
     const double *Pc = Yprev ? Yprev + (long)col * ld : nullptr;
     double *Oc = out + (long)col * ld;
     const bool act = (i < n0) && (j < n1);
@@ -113,7 +115,8 @@ k_stencil_df(const double *__restrict__ Y, const double *Yprev, double *out,
         // loads for plane k+1 (and the queue entry k+R+1), consumed after the compute
         const bool more = k + 1 < k1;
         const long pk1 = pk + plane;
-        double gl = 0.0, gr = 0.0, gt = 0.0, gb = 0.0, gq = 0.0, pnext = 0.0;
+        TI gl = 0, gr = 0, gt = 0, gb = 0, gq = 0;
+        double pnext = 0.0;
         float2 vnext = zero;
         if (more) {
             if (okl) gl = Yc[pk1 + offl];
@@ -230,9 +233,10 @@ cudaError_t scatter_f64_df(const DevHam &H, const float2 *Cs, double *out, int n
     return cudaGetLastError();
 }
 
-cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, double *out,
-                        int ncols, long ld, double alpha, double shift, double beta,
-                        cudaStream_t st)
+template <typename TI>
+static cudaError_t stencil_df_launch(const DevHam &H, const TI *Y, const double *Yprev,
+                                     double *out, int ncols, long ld, double alpha, double shift,
+                                     double beta, cudaStream_t st)
 {
     constexpr int BX = 32, BY = 16;
     if (ncols <= 0) return cudaSuccess;
@@ -247,10 +251,23 @@ cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, d
     int nzc, zchunk;
     stencil_z_split(H.n2, (long)gx * gy, ncols, nzc, zchunk);
     dim3 grid(gx, gy, ncols * nzc), block(BX, BY);
-    k_stencil_df<BX, BY><<<grid, block, 0, st>>>(Y, Yprev, out, H.Vdf, H.n0, H.n1, H.n2, ld, nzc,
-                                                 zchunk, cf);
+    k_stencil_df<TI, BX, BY><<<grid, block, 0, st>>>(Y, Yprev, out, H.Vdf, H.n0, H.n1, H.n2, ld,
+                                                     nzc, zchunk, cf);
     note_launch();
     return cudaGetLastError();
+}
+
+cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, double *out,
+                        int ncols, long ld, double alpha, double shift, double beta,
+                        cudaStream_t st)
+{
+    return stencil_df_launch<double>(H, Y, Yprev, out, ncols, ld, alpha, shift, beta, st);
+}
+
+cudaError_t stencil_f32in_f64(const DevHam &H, const float *Y, double *out, int ncols, long ld,
+                              cudaStream_t st)
+{
+    return stencil_df_launch<float>(H, Y, nullptr, out, ncols, ld, 1.0, 0.0, 0.0, st);
 }
 
 __global__ void k_to_float_pair(const double *in, float2 *out, long n)

@@ -318,6 +318,22 @@ def test_orth_rr_f64(c24):
     assert np.max(np.abs(Xg @ Xg.T - np.eye(w.ns))) <= 1e-12
 
 
+@pytest.mark.parametrize("ns", [97, 300])
+def test_orth_rr_f64_many_columns(c24, ns):
+    # enough columns to spread the Cholesky over many CTAs (and an odd count for the
+    # Jacobi's padded round-robin)
+    w, cl, H, ctx = c24
+    X0 = synth.initial_block(9, w.nd, ns)
+    Yf = H.cheb_filter(X0, 2, 7.6, 40.1, -3.3)
+    Xo, HXo, lam, res, _ = oracle.orth_rr(Yf, H.apply(Yf))
+    Yd = to_dev(Yf)
+    ritz, resid = ctx.orth_rr(Yd)
+    assert np.max(np.abs(ritz - lam)) <= 1e-10
+    assert np.max(np.abs(resid - res)) <= 1e-9
+    Xg = Yd.cpu().numpy()
+    assert np.max(np.abs(Xg @ Xg.T - np.eye(ns))) <= 1e-12
+
+
 def test_orth_rr_not_spd_leaves_block(c24):
     w, cl, H, ctx = c24
     X = synth.initial_block(6, w.nd, 3)
