@@ -43,8 +43,8 @@ UNIT = "point-orbitals/s"
 ORACLE_COLS = 16      # column slice of the block the oracle timing runs on
 SM_COUNT = 152
 # kernel sources whose DRAM traffic the committed ncu summary was taken on, per dtype
-STENCIL_SOURCES = {"f64": ("stencil_df.cu", "df.cuh", "internal.cuh"),
-                   "f32": ("stencil_tma.cu", "tma.cuh", "internal.cuh")}
+STENCIL_SOURCES = {"f64": ("stencil_df.cu", "df.cuh"),
+                   "f32": ("stencil_tma.cu",)}
 
 
 def reduce_max(value_ms: float, world: int, device=None) -> float:
@@ -169,7 +169,7 @@ def stencil_traffic(dtype: str):
     ent = d.get(dtype)
     if not ent or ent.get("source_sha256") != h.hexdigest():
         return None
-    return ent.get("bytes_per_launch_full")
+    return ent
 
 
 def stencil_algorithmic(w, dtype: str, prof: dict, steps: int) -> dict:
@@ -288,9 +288,15 @@ def run_ours(args, rank, world, local_rank):
             "frac": gbs / peak if gbs else None,
             "peak_source": "of measured (hbm_gbs, copy)" if peaks.get("hbm_gbs")
             else "of fallback (6.8 TB/s)",
-            "traffic": stencil_traffic(dtype),
+            "traffic": None,
             "avg_launch_ms": alg["ms"] / max(alg["launches"], 1),
             "launches": alg["launches"]}
+    tr = stencil_traffic(dtype)
+    if tr:
+        # DRAM bytes of one captured launch (ncu) next to that launch's algorithmic bytes
+        roof["traffic"] = tr["dram_bytes"]
+        roof["traffic_launch"] = tr["launch"]
+        roof["traffic_algorithmic_bytes"] = tr["algorithmic_bytes"]
     if dtype == "f64":
         # The FP64 step runs in FP32-pair arithmetic on the FP32 pipe; its FP64-equivalent
         # flop rate is compared with the FP64 pipe's issue limit as context.

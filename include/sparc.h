@@ -150,6 +150,23 @@ sparc_status sparc_orth_rr(sparc_ctx *ctx, sparc_dtype dtype, void *Xf, void *HX
 sparc_status sparc_gram(sparc_ctx *ctx, sparc_dtype dtype_a, const void *A, sparc_dtype dtype_b,
                         const void *B, int ncols, long ld, double *G);
 
+/* The same contraction on the tensor cores, as the mixed-precision form uses it for M_s
+ * and H_s (Sec. 3.4 with the FP32 filter). Each operand is rounded, per 256-row chunk and
+ * column, to 23 bits of that chunk's largest magnitude (three 8-bit digits in BF16), the
+ * digit products are summed exactly on the tensor cores (tcgen05), and the chunks are
+ * combined in FP32-pair arithmetic. Error bound per entry: |dG_ij| <= 2^-21 sum_k
+ * (m_i(k) m_j(k) + m_i(k) |B_kj| + |A_ki| m_j(k)), m_i(k) the largest |A_.i| of row k's
+ * chunk (m_j likewise for B) -- the rounding an FP32 block already carries, with no
+ * growth along Nd; sparc_gram is exact for FP32 data. Types (F32, F32), (F32, F64) or
+ * (F64, F64); a chunk column holding Inf or NaN makes the affected entries NaN. G: device,
+ * ncols x ncols, column-major FP64, overwritten; bitwise repeatable. Uses context
+ * workspace of about 6 x ncols x Nd bytes per distinct operand (allocated on first use or
+ * growth). Asynchronous; a bounded internal wait that expires is reported as
+ * SPARC_ERR_TIMEOUT by the next synchronising call. The paper's contractions are FP64
+ * throughout; this is the GB300 form of them. */
+sparc_status sparc_gram_tc(sparc_ctx *ctx, sparc_dtype dtype_a, const void *A,
+                           sparc_dtype dtype_b, const void *B, int ncols, long ld, double *G);
+
 /* One CheFSI iteration, Sec. 3.4: sparc_cheb_filter with bounds_inout = [a, b, a0],
  * then sparc_orth_rr. Afterwards bounds_inout is updated for the next iteration:
  * a = largest Ritz value, a0 = smallest Ritz value, b unchanged. work as in

@@ -1,0 +1,504 @@
+// gram_tc.cu -- the subspace contractions of the mixed-precision form on the tensor cores:
+//   M_s = Y^T Y  and  H_s = Y^T (H Y)   (projection onto the filtered block, Sec. 3.4),
+// Y the FP32 filtered block and H Y its FP64 image, G = A^T B over the Nd grid rows.
+//
+// Representation. The rows are cut into chunks of kChunk = 256. For chunk c and column j
+// of an operand, e = e(c, j) is the smallest integer with max_{k in c} |x_kj| < 2^e, and
+// each entry is rounded to N = round(|x| 2^(23 - e)), an integer in [0, 2^23], written in
+// three balanced base-256 digits N = d1 2^16 + d2 2^8 + d3 with 0 <= d1 <= 128 and
+// -128 <= d2, d3 <= 127 (signs carried by the digits). Every digit is an integer of at most
+// 8 bits, held exactly by BF16. So x = 2^(e - 23) (d1 2^16 + d2 2^8 + d3) up to 2^-24 of
+// the chunk's largest entry (about the rounding the FP32 block already carries).
+//
+// Exact accumulation. A product of two digits is an integer below 2^14 in magnitude,
+// exact in the tensor core's FP32 accumulator. The digit pairs (s, t) are grouped by
+// class w = s + t (0-based digits), whose weight is 2^(-8 w) relative to class 0; classes
+// 0, 1, 2 are kept (6 MMAs per 16 rows, one tensor-memory accumulator per class) and
+// classes 3, 4 (products below 2^-22 of the leading term) are dropped. Per chunk a class
+// accumulator holds at most 3 x 2^14 x 256 < 2^24 in magnitude, so its FP32 sums are
+// exact integers. After each chunk the epilogue warps read the three accumulators from
+// tensor memory, combine them exactly into an FP32 pair (TwoSum), scale the pair by the
+// chunk's power of two 2^(e_i + e_j - 14) and add it to FP32-pair running sums (error about
+// 2^-48 relative). The result is the Gram matrix of the 23-bit rounded block with no error
+// growth along Nd; the FP32-pair Gram of gram_df.cu remains the exact one.
+//
+// Layout and pipeline. A pre-pass (k_tc_digits) writes the digits of an operand in the
+// shared-memory order the MMA reads (no swizzle, K-major, 8-row x 16-byte core matrices)
+// as 8 KB blobs, one per (128-column block, 32-row step, digit), plus the exponents
+// e(c, j). A CTA owns one 128 x 128 tile of G over a range of chunks (split-K): warp 0
+// streams the blobs of A and B into a two-stage ring with untiled bulk copies (48 KB a
+// stage), one thread of warp 1 issues the tcgen05.mma (M = N = 128, K = 16) into the three
+// class accumulators (384 tensor-memory columns) and commits stage releases and chunk
+// completions to mbarriers, and eight epilogue warps (two per tensor-memory lane quarter,
+// 64 columns each; high parts of the running sums in registers, low parts in shared
+// memory) flush every chunk. Partial tiles of the K splits are summed by a
+// second kernel in a fixed order (deterministic). Every wait is bounded; on a timeout the
+// kernel raises *err, drains its copies and MMAs (bounded), frees its tensor memory and
+// returns.
+#include "internal.cuh"
+#include "tma.cuh"
+
+#include <cstdint>
+#include <cuda_bf16.h>
+
+namespace sparc {
+
+namespace {
+constexpr int kTile = 128;                     // MMA M = N = 128
+constexpr int kChunk = 256;                    // rows per exactness chunk
+constexpr int kStep = 32;                      // rows per pipeline stage
+constexpr int kStepsPerChunk = kChunk / kStep;
+constexpr int kDigits = 3;
+constexpr int kClasses = 3;
+constexpr int kBlobElems = kTile * kStep;      // 4096 BF16 = 8 KB
+constexpr unsigned kOperandBytes = kDigits * kBlobElems * 2;  // 24 KB
+constexpr unsigned kStageBytes = 2 * kOperandBytes;           // 48 KB
+constexpr int kStages = 2;
+constexpr int kEpiWarps = 8;
+constexpr int kEpiCols = 64;                   // G columns per epilogue thread
+// ring, then the low parts of the epilogue's running pair sums ([warp][column][lane])
+constexpr unsigned kLowBytes = kEpiWarps * kEpiCols * 32 * 4;  // 64 KB
+constexpr unsigned kSmemBytes = kStages * kStageBytes + kLowBytes + 1024;
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr unsigned kWaitLimit = 1u << 22;
+constexpr int kTmemCols = 512;
+constexpr int kNonFinite = INT32_MIN;          // exponent sentinel of a chunk with Inf/NaN
+
+// core-matrix offsets inside a blob (elements): K-adjacent cores 2048 B apart, M/N-adjacent
+// cores 128 B apart
+constexpr unsigned kLbo = 2048, kSbo = 128;
+
+__device__ __forceinline__ long blob_offset(int cb, long step, int s, long nstep)
+{
+    return (((long)cb * nstep + step) * kDigits + s) * kBlobElems;
+}
+
+__device__ __forceinline__ int in_blob(int k, int c)  // k: row in step, c: column (0..127)
+{
+    return ((((k >> 3) * 16 + (c >> 3)) * 8 + (c & 7)) * 8) + (k & 7);
+}
+
+// |x| as an unsigned integer (monotonic in |x| for finite x), exponent bits and significand
+template <typename T> struct FBits;
+template <> struct FBits<float> {
+    using U = uint32_t;
+    static constexpr int kMant = 23, kBias = 127, kExpMask = 0xFF;
+    __device__ static U mag(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
+    __device__ static bool neg(float x) { return (__float_as_uint(x) >> 31) != 0; }
+};
+template <> struct FBits<double> {
+    using U = unsigned long long;
+    static constexpr int kMant = 52, kBias = 1023, kExpMask = 0x7FF;
+    __device__ static U mag(double x) { return (U)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull; }
+    __device__ static bool neg(double x) { return __double_as_longlong(x) < 0; }
+};
+}  // namespace
+
+// Digits and exponents of one operand. CTA: one chunk (blockIdx.y) x 8 columns
+// (blockIdx.x), one warp per column, 8 rows per lane. Rows past nd and columns past ns are
+// zero; a chunk column holding Inf or NaN gets the exponent kNonFinite.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_tc_digits(const T *__restrict__ X, long ld, long nd, int ns, long nstep,
+            __nv_bfloat16 *__restrict__ D, int *__restrict__ E, int ns_pad)
+{
+    using B = FBits<T>;
+    using U = typename B::U;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int col = blockIdx.x * 8 + warp;
+    const long chunk = blockIdx.y;
+    const long k0 = chunk * kChunk;
+    U mag[8];
+    bool ng[8];
+    U mx = 0;
+    bool bad = false;
+    const U inf = (U)B::kExpMask << B::kMant;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const long k = k0 + lane + 32 * u;
+        T x = (T)0;
+        if (col < ns && k < nd) x = X[k + (long)col * ld];
+        mag[u] = B::mag(x);
+        ng[u] = B::neg(x);
+        bad |= mag[u] >= inf;
+        mx = mag[u] > mx ? mag[u] : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const U t = (U)__shfl_xor_sync(0xffffffffu, (unsigned long long)mx, o);
+        mx = t > mx ? t : mx;
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    // max |x| < 2^e: e = unbiased exponent of the max + 1 (normal), 1 - bias + 1 for
+    // subnormals; 0 for an all-zero chunk column
+    const int bxm = (int)(mx >> B::kMant);
+    const int e = mx == 0 ? 0 : (bxm == 0 ? 2 - B::kBias : bxm - B::kBias + 1);
+    if (lane == 0 && col < ns_pad) E[chunk * ns_pad + col] = bad ? kNonFinite : e;
+    const int cb = col >> 7, c = col & 127;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const long k = k0 + lane + 32 * u;
+        long N = 0;
+        if (!bad && mag[u] != 0) {
+            const int bx = (int)(mag[u] >> B::kMant);
+            const U m = (mag[u] & (((U)1 << B::kMant) - 1)) | (bx ? ((U)1 << B::kMant) : 0);
+            const int ebx = bx ? bx : 1;
+            // N = round(m 2^(ebx - bias - mant + 23 - e)); the shift is >= 1 since |x| < 2^e
+            const int sh = e + B::kBias + B::kMant - 23 - ebx;
+            if (sh <= 0)
+                N = (long)m << (-sh);  // cannot happen for |x| < 2^e; kept total
+            else if (sh < 8 * (int)sizeof(U))
+                N = (long)((m + ((U)1 << (sh - 1))) >> sh);
+        }
+        const int d3 = (int)(((N + 128) & 255) - 128);
+        const long N1 = (N - d3) >> 8;
+        const int d2 = (int)(((N1 + 128) & 255) - 128);
+        const int d1 = (int)((N1 - d2) >> 8);
+        const int sg = ng[u] ? -1 : 1;
+        const long step = k / kStep;
+        const int kl = (int)(k % kStep);
+        if (col < ns_pad) {
+            const long base = ((long)cb * nstep + step) * kDigits * kBlobElems + in_blob(kl, c);
+            D[base] = __float2bfloat16_rn((float)(sg * d1));
+            D[base + kBlobElems] = __float2bfloat16_rn((float)(sg * d2));
+            D[base + 2 * kBlobElems] = __float2bfloat16_rn((float)(sg * d3));
+        }
+    }
+}
+
+// 2^(e - 7) as an FP32 factor (the chunk scale 2^(e_i + e_j - 14) is applied as two such
+// factors, each exact); 0 below the FP32 normal range, NaN for a non-finite chunk.
+__device__ __forceinline__ float pow2_factor(int e)
+{
+    if (e == kNonFinite) return __int_as_float(0x7FC00000);
+    const int b = e - 7 + 127;
+    if (b <= 0) return 0.0f;
+    if (b >= 255) return __int_as_float(0x7F800000);
+    return __int_as_float(b << 23);
+}
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// tiles[t] = (A column block, B column block); part: nsplit x ntiles x 128 x 128 doubles,
+// element (r, c) of a tile at r * 128 + c (r: A column, c: B column).
+__global__ void __launch_bounds__(kThreads, 1)
+k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
+          const __nv_bfloat16 *__restrict__ DB, const int *__restrict__ EB, int ns_pad, long nstep,
+          const int2 *__restrict__ tiles, int ntiles, int nsplit, double *__restrict__ part,
+          int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full, acc_empty, drain;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+
+    unsigned char *smem =
+        (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x % ntiles, split = blockIdx.x / ntiles;
+    const int2 tb = tiles[tile];
+    const long nchunk = nstep / kStepsPerChunk;
+    const long c0 = (long)split * nchunk / nsplit, c1 = (long)(split + 1) * nchunk / nsplit;
+    const long st0 = c0 * kStepsPerChunk, st1 = c1 * kStepsPerChunk;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&acc_full, 1);
+        mbar_init(&acc_empty, kEpiWarps);
+        mbar_init(&drain, 1);
+        mbar_fence_init();
+        abort_flag = 0;
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    auto fail = [&]() {
+        abort_flag = 1;
+        atomicExch(err, 1);
+    };
+
+    if (warp == 0) {
+        // ---- producer: A and B blobs of each 64-row step into the ring ----
+        if (lane == 0) {
+            long issued = 0;
+            for (long st = st0; st < st1 && !abort_flag; ++st) {
+                const long j = st - st0;
+                const int s = (int)(j % kStages);
+                if (j >= kStages &&
+                    !mbar_wait(&empty[s], (unsigned)(((j / kStages) & 1) ^ 1), kWaitLimit)) {
+                    fail();
+                    break;
+                }
+                unsigned char *dst = smem + (size_t)s * kStageBytes;
+                mbar_arrive_expect_tx(&full[s], kStageBytes);
+                bulk_load(dst, DA + blob_offset(tb.x, st, 0, nstep), kOperandBytes, &full[s]);
+                bulk_load(dst + kOperandBytes, DB + blob_offset(tb.y, st, 0, nstep), kOperandBytes,
+                          &full[s]);
+                issued = j + 1;
+            }
+            if (abort_flag) {
+                // wait (bounded) for the last copy issued into each stage
+                for (int s = 0; s < kStages; ++s) {
+                    long last = -1;
+                    for (long j = s; j < issued; j += kStages) last = j;
+                    if (last >= 0)
+                        mbar_wait(&full[s], (unsigned)((last / kStages) & 1), kWaitLimit);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16_f32(kTile, kTile);
+            for (long st = st0; st < st1 && !abort_flag; ++st) {
+                const long j = st - st0;
+                const int s = (int)(j % kStages);
+                const int kin = (int)(j % kStepsPerChunk);
+                const long chunk = j / kStepsPerChunk;
+                if (kin == 0 && chunk > 0) {
+                    if (!mbar_wait(&acc_empty, (unsigned)((chunk - 1) & 1), kWaitLimit)) {
+                        fail();
+                        break;
+                    }
+                    tc_fence_after();
+                }
+                if (!mbar_wait(&full[s], (unsigned)((j / kStages) & 1), kWaitLimit)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                const unsigned char *a = smem + (size_t)s * kStageBytes;
+                const unsigned char *b = a + kOperandBytes;
+#pragma unroll
+                for (int ks = 0; ks < kStep / 16; ++ks) {
+#pragma unroll
+                    for (int sa = 0; sa < kDigits; ++sa) {
+#pragma unroll
+                        for (int sb = 0; sb < kDigits; ++sb) {
+                            const int w = sa + sb;
+                            if (w >= kClasses) continue;
+                            // in this loop order the first product of every class is the one
+                            // with sa = 0; at the start of a chunk it overwrites the accumulator
+                            const bool first = kin == 0 && ks == 0 && sa == 0;
+                            const uint64_t ad =
+                                smem_desc(a + sa * kBlobElems * 2 + ks * 2 * kLbo, kLbo, kSbo);
+                            const uint64_t bd =
+                                smem_desc(b + sb * kBlobElems * 2 + ks * 2 * kLbo, kLbo, kSbo);
+                            tc_mma_bf16(tmem + (uint32_t)(w * kTile), ad, bd, idesc, !first);
+                        }
+                    }
+                }
+                tc_commit(&empty[s]);                      // stage free once these MMAs are done
+                if (kin == kStepsPerChunk - 1) tc_commit(&acc_full);  // chunk complete
+            }
+            // all MMAs issued by this thread are complete before tensor memory is freed
+            tc_commit(&drain);
+            if (!mbar_wait(&drain, 0u, kWaitLimit)) fail();
+        }
+    } else {
+        // ---- epilogue: flush each chunk's class accumulators into FP32-pair sums ----
+        const int q = warp & 3;                 // tensor-memory lane quarter of this warp
+        const int half = (warp - 2) >> 2;       // columns 64 half .. 64 half + 63
+        const int r = q * 32 + lane;            // tile row = A column within the block
+        const int colA = tb.x * kTile + r;
+        float H[kEpiCols];
+        float *Lw = reinterpret_cast<float *>(smem + (size_t)kStages * kStageBytes) +
+                    (size_t)(warp - 2) * kEpiCols * 32 + lane;  // Lw[u * 32]: column u
+#pragma unroll
+        for (int u = 0; u < kEpiCols; ++u) {
+            H[u] = 0.0f;
+            Lw[u * 32] = 0.0f;
+        }
+        for (long c = c0; c < c1; ++c) {
+            bool ok = mbar_wait(&acc_full, (unsigned)((c - c0) & 1), kWaitLimit) && !abort_flag;
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) fail();
+                break;
+            }
+            tc_fence_after();
+            const float fA = pow2_factor(EA[c * ns_pad + colA]);
+            const int *eb = EB + c * ns_pad + tb.y * kTile + half * 64;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 64 + g * 8);
+                uint32_t v0[8], v1[8], v2[8];
+                tmem_ld8(ta, v0);
+                tmem_ld8(ta + kTile, v1);
+                tmem_ld8(ta + 2 * kTile, v2);
+                tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float a0 = __uint_as_float(v0[u]);
+                    const float a1 = __uint_as_float(v1[u]) * 0.00390625f;      // 2^-8
+                    const float a2 = __uint_as_float(v2[u]) * 1.52587890625e-05f;  // 2^-16
+                    float h, l, h2, l2;
+                    two_sum_f(a0, a1, h, l);
+                    two_sum_f(h, a2, h2, l2);
+                    const float f = fA * pow2_factor(eb[g * 8 + u]);
+                    const float ph = h2 * f, pl = (l + l2) * f;
+                    float sh, se;
+                    two_sum_f(H[g * 8 + u], ph, sh, se);
+                    H[g * 8 + u] = sh;
+                    Lw[(g * 8 + u) * 32] += se + pl;
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty);
+        }
+        double *o = part + ((long)split * ntiles + tile) * kTile * kTile + (long)r * kTile + half * 64;
+#pragma unroll
+        for (int u = 0; u < kEpiCols; ++u) o[u] = (double)H[u] + (double)Lw[u * 32];
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// G from the split partials, summed in split order; sym mirrors each off-diagonal tile.
+__global__ void k_gram_tc_reduce(const double *__restrict__ part, const int2 *__restrict__ tiles,
+                                 int ntiles, int nsplit, int ns, bool sym, double *G)
+{
+    const long tot = (long)ntiles * kTile * kTile;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+         t += (long)gridDim.x * blockDim.x) {
+        const int tile = (int)(t / (kTile * kTile));
+        const int e = (int)(t % (kTile * kTile));
+        const int r = e / kTile, c = e % kTile;
+        const int2 tb = tiles[tile];
+        const int i = tb.x * kTile + r, j = tb.y * kTile + c;
+        if (i >= ns || j >= ns) continue;
+        double v = 0.0;
+        for (int s = 0; s < nsplit; ++s) v += part[((long)s * ntiles + tile) * kTile * kTile + e];
+        G[i + (long)j * ns] = v;
+        if (sym && tb.x != tb.y) G[j + (long)i * ns] = v;
+    }
+}
+
+// ---- host side -------------------------------------------------------------------------
+
+namespace {
+struct TcPlan {
+    int ns_pad, nblk, ntiles, nsplit;
+    long nstep, nchunk;
+    size_t digits_bytes, exps_bytes, part_bytes, tiles_bytes;
+};
+
+TcPlan tc_plan(long nd, int ns, bool sym)
+{
+    TcPlan p;
+    p.nblk = (ns + kTile - 1) / kTile;
+    p.ns_pad = p.nblk * kTile;
+    p.nchunk = (nd + kChunk - 1) / kChunk;
+    p.nstep = p.nchunk * kStepsPerChunk;
+    p.ntiles = sym ? p.nblk * (p.nblk + 1) / 2 : p.nblk * p.nblk;
+    long s = (152 + p.ntiles - 1) / p.ntiles;
+    if (s > p.nchunk) s = p.nchunk;
+    if (s < 1) s = 1;
+    p.nsplit = (int)s;
+    p.digits_bytes = (size_t)kDigits * p.ns_pad * p.nstep * kStep * 2;
+    p.exps_bytes = (size_t)p.nchunk * p.ns_pad * sizeof(int);
+    p.part_bytes = (size_t)p.nsplit * p.ntiles * kTile * kTile * sizeof(double);
+    p.tiles_bytes = (size_t)p.ntiles * sizeof(int2);
+    return p;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+}  // namespace
+
+size_t gram_tc_workspace(long nd, int ns, bool same_operand, bool sym)
+{
+    const TcPlan p = tc_plan(nd, ns, sym);
+    const int nops = same_operand ? 1 : 2;
+    return nops * (align256(p.digits_bytes) + align256(p.exps_bytes)) + align256(p.part_bytes) +
+           align256(p.tiles_bytes);
+}
+
+template <typename T>
+static cudaError_t tc_digits(const T *X, long ld, long nd, int ns, const TcPlan &p,
+                             __nv_bfloat16 *D, int *E, cudaStream_t st)
+{
+    if (p.nchunk > 65535) return cudaErrorInvalidValue;
+    dim3 grid(p.ns_pad / 8, (unsigned)p.nchunk);
+    k_tc_digits<T><<<grid, 256, 0, st>>>(X, ld, nd, ns, p.nstep, D, E, p.ns_pad);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename TA, typename TB>
+cudaError_t gram_tc(const TA *A, long lda, const TB *B, long ldb, long nd, int ns, double *G,
+                    void *ws, size_t ws_bytes, bool sym, int *err, cudaStream_t st)
+{
+    if (ns <= 0 || nd <= 0) return cudaErrorInvalidValue;
+    const bool same = (const void *)A == (const void *)B && sizeof(TA) == sizeof(TB) && lda == ldb;
+    const TcPlan p = tc_plan(nd, ns, sym);
+    if (ws_bytes < gram_tc_workspace(nd, ns, same, sym)) return cudaErrorInvalidValue;
+    unsigned char *w = (unsigned char *)ws;
+    auto take = [&](size_t b) {
+        unsigned char *r = w;
+        w += align256(b);
+        return r;
+    };
+    __nv_bfloat16 *DA = (__nv_bfloat16 *)take(p.digits_bytes);
+    int *EA = (int *)take(p.exps_bytes);
+    __nv_bfloat16 *DB = DA;
+    int *EB = EA;
+    if (!same) {
+        DB = (__nv_bfloat16 *)take(p.digits_bytes);
+        EB = (int *)take(p.exps_bytes);
+    }
+    double *part = (double *)take(p.part_bytes);
+    int2 *tiles = (int2 *)take(p.tiles_bytes);
+
+    static bool attr_set = false;
+    cudaError_t e;
+    if (!attr_set) {
+        e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    // tile list (host-built, a few hundred entries at most)
+    static thread_local int2 host_tiles[64 * 65 / 2 + 64 * 64];
+    if (p.ntiles > (int)(sizeof(host_tiles) / sizeof(int2))) return cudaErrorInvalidValue;
+    int n = 0;
+    for (int a = 0; a < p.nblk; ++a)
+        for (int b = (sym ? a : 0); b < p.nblk; ++b) host_tiles[n++] = make_int2(a, b);
+    e = cudaMemcpyAsync(tiles, host_tiles, p.tiles_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    if ((e = tc_digits<TA>(A, lda, nd, ns, p, DA, EA, st)) != cudaSuccess) return e;
+    if (!same && (e = tc_digits<TB>(B, ldb, nd, ns, p, DB, EB, st)) != cudaSuccess) return e;
+    k_gram_tc<<<p.ntiles * p.nsplit, kThreads, kSmemBytes, st>>>(DA, EA, DB, EB, p.ns_pad, p.nstep,
+                                                                  tiles, p.ntiles, p.nsplit, part,
+                                                                  err);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_gram_tc_reduce<<<152 * 4, 256, 0, st>>>(part, tiles, p.ntiles, p.nsplit, ns, sym, G);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t gram_tc<float, float>(const float *, long, const float *, long, long, int,
+                                           double *, void *, size_t, bool, int *, cudaStream_t);
+template cudaError_t gram_tc<float, double>(const float *, long, const double *, long, long, int,
+                                            double *, void *, size_t, bool, int *, cudaStream_t);
+template cudaError_t gram_tc<double, double>(const double *, long, const double *, long, long,
+                                             int, double *, void *, size_t, bool, int *,
+                                             cudaStream_t);
+
+}  // namespace sparc

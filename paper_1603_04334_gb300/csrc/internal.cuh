@@ -145,6 +145,15 @@ cudaError_t rotate_f64_df(const double *A, long lda, long nd, int ns, const doub
                           long ldo, cudaStream_t st);
 // FP64 Gram with a caller-chosen number of row slices (part: nsplit * ns * ns doubles).
 int gram_default_splits(int ns, long nd);
+// Tensor-core Gram of the mixed-precision form (gram_tc.cu): G = A^T B (ns x ns FP64,
+// column-major) from operands rounded to 23 bits of each 256-row chunk's largest entry,
+// accumulated exactly on the tensor cores; sym computes the tiles on and above the
+// diagonal and mirrors them. ws: at least gram_tc_workspace(nd, ns, A == B, sym) bytes,
+// 256-byte aligned. A bounded wait that expires sets *err.
+size_t gram_tc_workspace(long nd, int ns, bool same_operand, bool sym);
+template <typename TA, typename TB>
+cudaError_t gram_tc(const TA *A, long lda, const TB *B, long ldb, long nd, int ns, double *G,
+                    void *ws, size_t ws_bytes, bool sym, int *err, cudaStream_t st);
 cudaError_t gram_f64_nsplit(const double *A, long lda, const double *B, long ldb, long nd, int ns,
                             double *G, double *part, int nsplit, cudaStream_t st);
 // out (nd x ns, ldo) = A (nd x ns, lda) Q (ns x ns, column-major FP64)

@@ -58,6 +58,7 @@ struct sparc_ctx {
     void *rotx = nullptr;    size_t rotx_bytes = 0;  // rotated block
     void *roth = nullptr;    size_t roth_bytes = 0;  // rotated H block (residuals)
     void *part = nullptr;    size_t part_bytes = 0;  // Gram split-K partials
+    void *tcws = nullptr;    size_t tcws_bytes = 0;  // tensor-core Gram digits, exponents, partials
     void *dm = nullptr;      size_t dm_bytes = 0;    // M, Hs, Cf, ritz, resid, dense work
     void *lz = nullptr;      size_t lz_bytes = 0;    // Lanczos vectors and scalars
     int *flags = nullptr;                            // device status words
@@ -349,8 +350,10 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
         { PHASE(SPARC_PHASE_GRAM); CK(gram_f64((const double *)Yf, ld, (const double *)Yf, ld, nd, ns, d.M, part, ctx->st, true)); }
         { PHASE(SPARC_PHASE_GRAM); CK(gram_f64((const double *)Yf, ld, HX, ld, nd, ns, d.Hs, part, ctx->st, true)); }
     } else {
-        { PHASE(SPARC_PHASE_GRAM); CK(gram_f32_f32((const float *)Yf, ld, (const float *)Yf, ld, nd, ns, d.M, part, ctx->st, true)); }
-        { PHASE(SPARC_PHASE_GRAM); CK(gram_f32_f64((const float *)Yf, ld, HX, ld, nd, ns, d.Hs, part, ctx->st, true)); }
+        // mixed-precision form: both contractions on the tensor cores (gram_tc.cu)
+        TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, gram_tc_workspace(nd, ns, false, true)));
+        { PHASE(SPARC_PHASE_GRAM); CK((gram_tc<float, float>((const float *)Yf, ld, (const float *)Yf, ld, nd, ns, d.M, ctx->tcws, ctx->tcws_bytes, true, ctx->H.err, ctx->st))); }
+        { PHASE(SPARC_PHASE_GRAM); CK((gram_tc<float, double>((const float *)Yf, ld, HX, ld, nd, ns, d.Hs, ctx->tcws, ctx->tcws_bytes, true, ctx->H.err, ctx->st))); }
     }
     { PHASE(SPARC_PHASE_DENSE); CK(dense_rr(d.M, d.Hs, ns, d.ritz, d.Cf, d.work, ctx->flags, ctx->st)); }
     CK(cudaMemcpyAsync(ctx->pin_i, ctx->flags, sizeof(int) * 16, cudaMemcpyDeviceToHost, ctx->st));
@@ -415,7 +418,7 @@ void free_ctx(sparc_ctx *c)
     if (!c) return;
     void *ps[] = {c->V, c->Vf, c->Vdf, c->atom_ptr, c->idx, c->ent_atom, c->chi, c->gchi, c->chi_f,
                   c->gchi_f, c->chi_df, c->uniq_node, c->uniq_ptr, c->ent_list, c->nl_atom, c->nl_gf, c->nl_gdf, c->C, c->hx, c->rotx, c->roth, c->part,
-                  c->dm, c->lz, c->flags};
+                  c->tcws, c->dm, c->lz, c->flags};
     for (void *p : ps) dfree(p);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->prof.used) cudaEventDestroy(e);
@@ -703,6 +706,33 @@ sparc_status sparc_gram(sparc_ctx *ctx, sparc_dtype dtype_a, const void *A, spar
         CK(gram_f32_f32((const float *)A, ld, (const float *)B, ld, nd, ncols, G, part, ctx->st));
     else if (dtype_a == SPARC_F32 && dtype_b == SPARC_F64)
         CK(gram_f32_f64((const float *)A, ld, (const double *)B, ld, nd, ncols, G, part, ctx->st));
+    else
+        return fail(ctx, SPARC_ERR_ARG, "unsupported dtype pair (%d, %d)", (int)dtype_a,
+                    (int)dtype_b);
+    return SPARC_OK;
+}
+
+sparc_status sparc_gram_tc(sparc_ctx *ctx, sparc_dtype dtype_a, const void *A, sparc_dtype dtype_b,
+                           const void *B, int ncols, long ld, double *G)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    ctx->err.clear();
+    TRY(check_block(ctx, A, ncols, ld, "A"));
+    TRY(check_block(ctx, B, ncols, ld, "B"));
+    if (!G) return fail(ctx, SPARC_ERR_ARG, "G is NULL");
+    const long nd = ctx->H.nd;
+    const bool same = A == B && dtype_a == dtype_b;
+    TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, gram_tc_workspace(nd, ncols, same, false)));
+    PHASE(SPARC_PHASE_GRAM);
+    if (dtype_a == SPARC_F32 && dtype_b == SPARC_F32)
+        CK((gram_tc<float, float>((const float *)A, ld, (const float *)B, ld, nd, ncols, G,
+                                 ctx->tcws, ctx->tcws_bytes, false, ctx->H.err, ctx->st)));
+    else if (dtype_a == SPARC_F32 && dtype_b == SPARC_F64)
+        CK((gram_tc<float, double>((const float *)A, ld, (const double *)B, ld, nd, ncols, G,
+                                  ctx->tcws, ctx->tcws_bytes, false, ctx->H.err, ctx->st)));
+    else if (dtype_a == SPARC_F64 && dtype_b == SPARC_F64)
+        CK((gram_tc<double, double>((const double *)A, ld, (const double *)B, ld, nd, ncols, G,
+                                   ctx->tcws, ctx->tcws_bytes, false, ctx->H.err, ctx->st)));
     else
         return fail(ctx, SPARC_ERR_ARG, "unsupported dtype pair (%d, %d)", (int)dtype_a,
                     (int)dtype_b);

@@ -37,7 +37,8 @@ EXPORTS = ("sparc_create", "sparc_destroy", "sparc_last_error", "sparc_get_veff"
            "sparc_cheb_filter", "sparc_orth_rr", "sparc_gram", "sparc_chefsi_step",
            "sparc_profile_enable",
            "sparc_profile_read", "sparc_profile_reset", "sparc_launch_count",
-           "sparc_gram_noalloc", "sparc_sync", "sparc_selftest_timeout")
+           "sparc_gram_noalloc", "sparc_sync", "sparc_selftest_timeout",
+           "sparc_gram_tc")
 
 PHASES = ("stencil", "project", "scatter", "gram", "dense", "rotate", "other")
 
@@ -91,6 +92,7 @@ def load(build_if_missing: bool = True):
     L.sparc_orth_rr.argtypes = [vp, ip, vp, vp, ip, C.c_long, dp, dp]
     L.sparc_chefsi_step.argtypes = [vp, ip, vp, vp, ip, C.c_long, ip, dp, dp, dp]
     L.sparc_gram.argtypes = [vp, ip, vp, ip, vp, ip, C.c_long, vp]
+    L.sparc_gram_tc.argtypes = [vp, ip, vp, ip, vp, ip, C.c_long, vp]
     L.sparc_profile_enable.argtypes = [vp, ip]
     L.sparc_profile_read.argtypes = [vp, ip, C.POINTER(C.c_longlong), dp]
     L.sparc_profile_reset.argtypes = [vp]
@@ -275,6 +277,20 @@ class Context:
         self._check(self._L.sparc_gram(self._h, _dtype_code(A), C.c_void_p(A.data_ptr()),
                                        _dtype_code(B), C.c_void_p(B.data_ptr()), ncols, ld,
                                        C.c_void_p(G.data_ptr())))
+        return G
+
+    def gram_tc(self, A, B, G=None):
+        """G = A^T B on the tensor cores (23-bit chunk rounding, exact accumulation; see
+        sparc_gram_tc); same layout as gram()."""
+        import torch
+        ncols, ld = _block(A, "A")
+        if B.shape != A.shape:
+            raise ValueError("A and B must have the same shape")
+        if G is None:
+            G = torch.empty((ncols, ncols), dtype=torch.float64, device=A.device)
+        self._check(self._L.sparc_gram_tc(self._h, _dtype_code(A), C.c_void_p(A.data_ptr()),
+                                          _dtype_code(B), C.c_void_p(B.data_ptr()), ncols, ld,
+                                          C.c_void_p(G.data_ptr())))
         return G
 
     def chefsi_step(self, X, work, degree: int, bounds: Sequence[float],

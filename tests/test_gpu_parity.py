@@ -438,3 +438,60 @@ def test_gram_matches_fp64_products(c24, ncols, dt):
     assert nrm_err(G, ref) <= 1e-13
     G2 = ctx.gram(Ad, Bd).cpu().numpy().T
     assert np.array_equal(G, G2)
+
+
+# --------------------------------------------------------------------------------------
+# tensor-core contraction of the mixed-precision form
+# --------------------------------------------------------------------------------------
+def _chunk_max(X, chunk=256):
+    """|X| maximum over each 256-row chunk of every column, expanded back to rows.
+    X: (ncols, nd) rows are columns of the Nd x ncols block."""
+    nc, nd = X.shape
+    nchunk = (nd + chunk - 1) // chunk
+    P = np.zeros((nc, nchunk * chunk))
+    P[:, :nd] = np.abs(X)
+    m = P.reshape(nc, nchunk, chunk).max(axis=2)
+    return np.repeat(m, chunk, axis=1)[:, :nd]
+
+
+@pytest.mark.parametrize("n3,ncols,dts", [((24, 24, 24), 12, ("f32", "f32")),
+                                          ((37, 29, 23), 130, ("f32", "f64")),
+                                          ((37, 29, 23), 33, ("f64", "f64")),
+                                          ((24, 24, 24), 257, ("f32", "f32"))])
+def test_gram_tc_within_chunk_rounding_bound(n3, ncols, dts):
+    # G = A^T B against the exact FP64 product of the same data; bound of sparc_gram_tc:
+    # |dG_ij| <= 2^-21 sum_k (m_i m_j + m_i |B_kj| + |A_ki| m_j), m = chunk maxima
+    w = synth.preset("cluster24")
+    cl = synth.make_cluster(w, 0)
+    ctx = make_ctx(cl, n=n3)
+    nd = int(np.prod(n3))
+    rng = np.random.default_rng(11)
+    scale = 10.0 ** rng.uniform(-3, 3, size=(ncols, 1))     # columns of very different size
+    A = (rng.standard_normal((ncols, nd)) * scale)
+    A[:, ::7] *= 1e-4                                         # small entries inside chunks
+    B = rng.standard_normal((ncols, nd)) * scale[::-1]
+    tA = torch.float32 if dts[0] == "f32" else torch.float64
+    tB = torch.float32 if dts[1] == "f32" else torch.float64
+    Ad, Bd = to_dev(A, tA), to_dev(B, tB)
+    A64, B64 = Ad.double().cpu().numpy(), Bd.double().cpu().numpy()
+    Gd = ctx.gram_tc(Ad, Bd)
+    G = Gd.cpu().numpy().T                                    # G[i, j] = entry (i, j)
+    ref = A64 @ B64.T
+    mA, mB = _chunk_max(A64), _chunk_max(B64)
+    bound = 2.0 ** -21 * (mA @ mB.T + mA @ np.abs(B64).T + np.abs(A64) @ mB.T)
+    err = np.abs(G - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    # bitwise repeatable
+    assert torch.equal(ctx.gram_tc(Ad, Bd), Gd)
+    ctx.close()
+
+
+def test_gram_tc_symmetric_and_nonfinite(c24):
+    w, cl, H, ctx = c24
+    X = synth.initial_block(4, w.nd, 40)
+    Xd = to_dev(X, torch.float32)
+    G = ctx.gram_tc(Xd, Xd).cpu().numpy()
+    assert np.array_equal(G, G.T)                 # exact digit sums: bitwise symmetric
+    X[5, 300] = np.inf
+    Gn = ctx.gram_tc(to_dev(X, torch.float32), to_dev(X, torch.float32)).cpu().numpy()
+    assert np.all(np.isnan(Gn[5, :])) and np.all(np.isfinite(np.delete(np.delete(Gn, 5, 0), 5, 1)))
