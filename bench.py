@@ -63,13 +63,19 @@ def job_value(work_per_rank_step: int, steps: int, world: int, ms: float) -> flo
     return work_per_rank_step * steps * world / (ms / 1e3)
 
 
-def work_per_step(w) -> int:
-    return w.lanczos_k * w.nd + w.iters * (w.degree + 1) * w.nd * w.ns
+def work_per_step(w, dtype: str = "f64") -> int:
+    """Point-orbital updates of one solve: k Lanczos applications of H to one vector, and
+    m + 1 applications to the block per CheFSI iteration (m filter steps, H Y_f in the
+    Rayleigh-Ritz step); the mixed form adds its FP64 refinement iteration."""
+    its = w.iters + (1 if dtype == "f32" else 0)
+    return w.lanczos_k * w.nd + its * (w.degree + 1) * w.nd * w.ns
 
 
 def workload_config(w, dtype: str) -> dict:
+    form = ("FP32 filter, FP64 Rayleigh-Ritz, + 1 FP64 refinement iteration" if dtype == "f32"
+            else "FP64")
     return {"workload": f"{w.name}: {w.n}^3 grid h={w.h} bohr, {w.natoms} atoms, Ns={w.ns}, "
-                        f"Chebyshev degree {w.degree}, {w.iters} CheFSI iterations, {dtype}",
+                        f"Chebyshev degree {w.degree}, {w.iters} CheFSI iterations, {form}",
             "n": w.n, "h": w.h, "natoms": w.natoms, "ns": w.ns, "degree": w.degree,
             "iters": w.iters, "lanczos_k": w.lanczos_k, "dtype": dtype,
             "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
@@ -173,25 +179,37 @@ def stencil_traffic(dtype: str):
 
 
 def stencil_algorithmic(w, dtype: str, prof: dict, steps: int) -> dict:
-    """Algorithmic bytes and flops of the stencil phase over the timed steps.
+    """Algorithmic bytes and flops of all stencil launches of the timed steps.
 
-    Per point-orbital: a filter step reads Y_j and Y_{j-1} and writes Y_{j+1}
-    (3 elements), H X reads X and writes HX (2 elements); V_eff adds one value per node
-    per launch. Flops per point-orbital: 6 radii x (5 adds + 1 FMA) + centre
-    (1 FMA + 1 multiply) + recurrence (1 FMA) = 47 (45 for H X)."""
-    es = 8 if dtype == "f64" else 4
-    nd, ns, m, it = w.nd, w.ns, w.degree, w.iters
-    # per iteration: first filter step without Y_{j-1}, m-1 with it, one H X in RR
-    three = (m - 1) * ns
-    two = 2 * ns
-    per_it_bytes = nd * (three * 3 * es + two * 2 * es) + (m + 1) * nd * es
-    per_it_flops = nd * (three * 47 + two * 45)
+    Per point-orbital a filter step reads Y_j and Y_{j-1} and writes Y_{j+1} (3 elements);
+    the first step of a filter and an H X read one block and write one (2 elements); each
+    launch also reads V_eff once per node (8 B as an FP32 pair in the FP64 kernels, 4 B in
+    the FP32 kernel). Flops per point-orbital: 6 radii x (5 adds + 1 FMA) + centre
+    (1 FMA + 1 multiply) + recurrence (1 FMA) = 47 (45 without the recurrence term).
+    FP64 form per iteration: 2-stream first step, m - 1 3-stream steps, 2-stream H Y_f, all
+    FP64. Mixed form per FP32 iteration: FP32 steps (4-byte elements) and the FP64 H Y_f of
+    the FP32 block (4 B in, 8 B out); then one FP64 refinement iteration. Lanczos: k
+    single-column FP64 H x."""
+    nd, ns, m = w.nd, w.ns, w.degree
+
+    def iteration(ein: int, eh_in: int, eh_out: int, vbytes_step: int):
+        # ein: element bytes of the filter steps; eh_*: bytes of the H Y_f launch
+        b = nd * ns * (2 * ein + (m - 1) * 3 * ein + eh_in + eh_out) + nd * (m * vbytes_step + 8)
+        f = nd * ns * (45 + (m - 1) * 47 + 45)
+        return b, f
+
+    if dtype == "f64":
+        b1, f1 = iteration(8, 8, 8, 8)
+        it_b, it_f = w.iters * b1, w.iters * f1
+    else:
+        b1, f1 = iteration(4, 4, 8, 4)
+        b2, f2 = iteration(8, 8, 8, 8)
+        it_b, it_f = w.iters * b1 + b2, w.iters * f1 + f2
     lz_bytes = w.lanczos_k * nd * (2 * 8 + 8)
     lz_flops = w.lanczos_k * nd * 45
-    tot_bytes = steps * (it * per_it_bytes + lz_bytes)
-    tot_flops = steps * (it * per_it_flops + lz_flops)
     n_launch, ms = prof["stencil"]
-    return {"bytes": tot_bytes, "flops": tot_flops, "launches": n_launch, "ms": ms}
+    return {"bytes": steps * (it_b + lz_bytes), "flops": steps * (it_f + lz_flops),
+            "launches": n_launch, "ms": ms}
 
 
 # ----------------------------------------------------------------------------------
@@ -214,6 +232,9 @@ def run_ours(args, rank, world, local_rank):
     X0 = torch.from_numpy(X0h).to(dev, dtype=tdt)
     X = torch.empty_like(X0)
     W = torch.empty_like(X0)
+    mixed = dtype == "f32"
+    X64 = torch.empty(X0.shape, dtype=torch.float64, device=dev) if mixed else None
+    W64 = torch.empty_like(X64) if mixed else None
 
     def solve(Xsrc):
         X.copy_(Xsrc, non_blocking=True)
@@ -221,7 +242,11 @@ def run_ours(args, rank, world, local_rank):
         b = sparc.first_bounds(lo, hi)
         ritz = resid = None
         for it in range(w.iters):
-            ritz, resid, b = ctx.chefsi_step(X, W, w.degree, b, want_resid=(it == w.iters - 1))
+            last = it == w.iters - 1 and not mixed
+            ritz, resid, b = ctx.chefsi_step(X, W, w.degree, b, want_resid=last)
+        if mixed:  # refinement sweep: one FP64 iteration from the FP32 result
+            X64.copy_(X)
+            ritz, resid, b = ctx.chefsi_step(X64, W64, w.degree, b, want_resid=True)
         return ritz, resid
 
     def barrier():
@@ -257,8 +282,8 @@ def run_ours(args, rank, world, local_rank):
     ctx.profile_enable(False)
     prof = ctx.profile_read()
     ms = reduce_max(ms, world, dev)
-    work = work_per_step(w) * args.steps * world
-    value = job_value(work_per_step(w), args.steps, world, ms)
+    work = work_per_step(w, dtype) * args.steps * world
+    value = job_value(work_per_step(w, dtype), args.steps, world, ms)
 
     # ---- end-to-end: host block in pinned memory -> device each step ------------------
     e2e = None
@@ -305,7 +330,8 @@ def run_ours(args, rank, world, local_rank):
         roof["fp64_equiv_tflops"] = fl
         roof["fp64_pipe_peak_tflops"] = fp64_alu_peak_tflops(sm_max)
     else:
-        roof["kernel"] = "k_stencil_f32_tma (fused stencil + V_eff + recurrence, TMA-fed)"
+        roof["kernel"] = ("stencil phase: k_stencil_f32_tma filter steps (TMA-fed FP32) + "
+                          "k_stencil_df for H Y_f, the FP64 refinement and Lanczos")
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
