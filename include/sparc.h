@@ -131,8 +131,10 @@ sparc_status sparc_cheb_filter(sparc_ctx *ctx, sparc_dtype dtype, void *X, void 
  * Each column of Q is signed so that its largest-magnitude entry is positive.
  * On return Xf holds Euclidean-orthonormal Ritz vectors (ascending Ritz values),
  * ritz_host[ncols] the Ritz values, and resid_host[ncols] (if not NULL) the residual
- * norms ||H x_n - ritz_n x_n||_2. For dtype F32 the block stays FP32 while H Xf, the
- * projected matrices and the eigensolve are FP64. HXf_or_null: optional FP64 device
+ * norms ||H x_n - ritz_n x_n||_2. For dtype F32 the block stays FP32, H Xf is applied
+ * in FP64, M_s and H_s come from the tensor-core contraction (see sparc_gram_tc) and the
+ * eigensolve is FP64; the rotated H X of the residuals is then formed in FP32 arithmetic
+ * (residuals good to about 1e-7 of ||H x_n||). HXf_or_null: optional FP64 device
  * block (ncols x ld) used as the H Xf workspace; when NULL the context allocates one.
  * Fails with SPARC_ERR_NOT_SPD if M_s is not numerically positive definite and with
  * SPARC_ERR_NONFINITE on NaN/Inf, leaving Xf unrotated. ncols <= 1024. Synchronises. */
@@ -202,6 +204,10 @@ sparc_status sparc_profile_reset(sparc_ctx *ctx);
 
 /* Number of kernels this library has launched in the calling process (all contexts). */
 sparc_status sparc_launch_count(long long *count);
+
+/* Upper bound of the device memory the context has held at any time (bytes it allocated,
+ * its set-up temporaries counted as if never freed). */
+sparc_status sparc_device_bytes(const sparc_ctx *ctx, size_t *peak_bytes);
 
 /* ---- synchronisation and failure detection ------------------------------------------ */
 

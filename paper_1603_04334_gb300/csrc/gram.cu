@@ -68,9 +68,11 @@ cudaError_t gram_f32_f64(const float *A, long lda, const double *B, long ldb, lo
 // ---- rotation of FP32 blocks: out = A Q in FP32 arithmetic (the rotated block is stored
 // in FP32, and span(A Q') = span(A) for any invertible Q' close to Q, so the subspace the
 // next filter starts from does not depend on this rounding). Tile 64 rows x 64 columns,
-// Q staged 16 rows at a time. FP64 blocks use k_rotate_df (gram_df.cu).
+// Q staged 16 rows at a time. FP64 blocks use k_rotate_df (gram_df.cu). TA = double reads
+// an FP64 block (rounded to FP32 on load): the FP32 form's rotated H Y_f for the residuals.
+template <typename TA>
 __global__ void __launch_bounds__(256)
-k_rotate_f32(const float *__restrict__ A, long lda, long nd, int ns, const double *__restrict__ Q,
+k_rotate_f32(const TA *__restrict__ A, long lda, long nd, int ns, const double *__restrict__ Q,
              float *__restrict__ out, long ldo)
 {
     __shared__ float As[GK][GT + 1];   // [k][row]
@@ -91,7 +93,7 @@ k_rotate_f32(const float *__restrict__ A, long lda, long nd, int ns, const doubl
             for (int u = 0; u < 4; ++u) {
                 const int k = kc + 4 * u;
                 const long row = r0 + rr;
-                As[k][rr] = (row < nd && k0 + k < ns) ? A[row + (long)(k0 + k) * lda] : 0.0f;
+                As[k][rr] = (row < nd && k0 + k < ns) ? (float)A[row + (long)(k0 + k) * lda] : 0.0f;
             }
         }
         // Q tile: 16 rows (k) x 64 columns; thread loads k = t % 16, columns t/16 + 16u
@@ -135,32 +137,43 @@ cudaError_t rotate_f64(const double *A, long lda, long nd, int ns, const double 
 {
     return rotate_f64_df(A, lda, nd, ns, Q, out, ldo, st);
 }
-cudaError_t rotate_f32(const float *A, long lda, long nd, int ns, const double *Q, float *out,
-                       long ldo, cudaStream_t st)
+template <typename TA>
+static cudaError_t rotate_to_f32(const TA *A, long lda, long nd, int ns, const double *Q,
+                                 float *out, long ldo, cudaStream_t st)
 {
     if (ns <= 0 || nd <= 0) return cudaSuccess;
     const long gx = (nd + GT - 1) / GT;
     if (gx > 2147483647L) return cudaErrorInvalidValue;
     dim3 grid((unsigned)gx, (ns + GT - 1) / GT);
-    k_rotate_f32<<<grid, 256, 0, st>>>(A, lda, nd, ns, Q, out, ldo);
+    k_rotate_f32<TA><<<grid, 256, 0, st>>>(A, lda, nd, ns, Q, out, ldo);
     note_launch();
     return cudaGetLastError();
 }
+cudaError_t rotate_f32(const float *A, long lda, long nd, int ns, const double *Q, float *out,
+                       long ldo, cudaStream_t st)
+{
+    return rotate_to_f32<float>(A, lda, nd, ns, Q, out, ldo, st);
+}
+cudaError_t rotate_f64in_f32(const double *A, long lda, long nd, int ns, const double *Q,
+                             float *out, long ldo, cudaStream_t st)
+{
+    return rotate_to_f32<double>(A, lda, nd, ns, Q, out, ldo, st);
+}
 
 // ---- residual norms: one CTA per column, fixed-order reduction -----------------------
-template <typename T>
+template <typename T, typename TH>
 __global__ void __launch_bounds__(256)
-k_resid(const T *__restrict__ X, const double *__restrict__ HX, long ld, long nd,
+k_resid(const T *__restrict__ X, const TH *__restrict__ HX, long ld, long nd,
         const double *__restrict__ ritz, double *__restrict__ resid)
 {
     __shared__ double red[8];
     const int c = blockIdx.x;
     const double lam = ritz[c];
     const T *x = X + (long)c * ld;
-    const double *hx = HX + (long)c * ld;
+    const TH *hx = HX + (long)c * ld;
     double s = 0.0;
     for (long p = threadIdx.x; p < nd; p += 256) {
-        const double r = hx[p] - lam * (double)x[p];
+        const double r = (double)hx[p] - lam * (double)x[p];
         s += r * r;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -177,15 +190,15 @@ cudaError_t resid_f64(const double *X, const double *HX, long ld, long nd, int n
                       const double *ritz, double *resid, cudaStream_t st)
 {
     if (ncols <= 0) return cudaSuccess;
-    k_resid<double><<<ncols, 256, 0, st>>>(X, HX, ld, nd, ritz, resid);
+    k_resid<double, double><<<ncols, 256, 0, st>>>(X, HX, ld, nd, ritz, resid);
     note_launch();
     return cudaGetLastError();
 }
-cudaError_t resid_f32(const float *X, const double *HX, long ld, long nd, int ncols,
+cudaError_t resid_f32(const float *X, const float *HX, long ld, long nd, int ncols,
                       const double *ritz, double *resid, cudaStream_t st)
 {
     if (ncols <= 0) return cudaSuccess;
-    k_resid<float><<<ncols, 256, 0, st>>>(X, HX, ld, nd, ritz, resid);
+    k_resid<float, float><<<ncols, 256, 0, st>>>(X, HX, ld, nd, ritz, resid);
     note_launch();
     return cudaGetLastError();
 }

@@ -26,7 +26,7 @@
 // shared-memory order the MMA reads (no swizzle, K-major, 8-row x 16-byte core matrices)
 // as 8 KB blobs, one per (128-column block, 32-row step, digit), plus the exponents
 // e(c, j). A CTA owns one 128 x 128 tile of G over a range of chunks (split-K): warp 0
-// streams the blobs of A and B into a two-stage ring with untiled bulk copies (48 KB a
+// streams the blobs of A and B into a three-stage ring with untiled bulk copies (48 KB a
 // stage), one thread of warp 1 issues the tcgen05.mma (M = N = 128, K = 16) into the three
 // class accumulators (384 tensor-memory columns) and commits stage releases and chunk
 // completions to mbarriers, and eight epilogue warps (two per tensor-memory lane quarter,
@@ -53,7 +53,7 @@ constexpr int kClasses = 3;
 constexpr int kBlobElems = kTile * kStep;      // 4096 BF16 = 8 KB
 constexpr unsigned kOperandBytes = kDigits * kBlobElems * 2;  // 24 KB
 constexpr unsigned kStageBytes = 2 * kOperandBytes;           // 48 KB
-constexpr int kStages = 2;
+constexpr int kStages = 3;
 constexpr int kEpiWarps = 8;
 constexpr int kEpiCols = 64;                   // G columns per epilogue thread
 // ring, then the low parts of the epilogue's running pair sums ([warp][column][lane])

@@ -161,6 +161,9 @@ cudaError_t rotate_f64(const double *A, long lda, long nd, int ns, const double 
                        double *out, long ldo, cudaStream_t st);
 cudaError_t rotate_f32(const float *A, long lda, long nd, int ns, const double *Q, float *out,
                        long ldo, cudaStream_t st);
+// out = A Q in FP32 arithmetic from an FP64 block (the FP32 form's residuals)
+cudaError_t rotate_f64in_f32(const double *A, long lda, long nd, int ns, const double *Q,
+                             float *out, long ldo, cudaStream_t st);
 
 // ---- dense.cu -------------------------------------------------------------------
 // Small dense Rayleigh-Ritz on the device (single CTA kernels), ns <= kMaxDense.
@@ -224,7 +227,7 @@ cudaError_t lanczos_bounds_final(const double *ev, const double *Q, const double
 // resid[c] = || HX[:,c] - ritz[c] X[:,c] ||_2 (deterministic per-column reduction)
 cudaError_t resid_f64(const double *X, const double *HX, long ld, long nd, int ncols,
                       const double *ritz, double *resid, cudaStream_t st);
-cudaError_t resid_f32(const float *X, const double *HX, long ld, long nd, int ncols,
+cudaError_t resid_f32(const float *X, const float *HX, long ld, long nd, int ncols,
                       const double *ritz, double *resid, cudaStream_t st);
 // flag |= 1 if any of n values is NaN or Inf
 cudaError_t check_finite(const double *a, long n, int *flag, cudaStream_t st);

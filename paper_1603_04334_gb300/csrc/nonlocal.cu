@@ -102,7 +102,9 @@ static cudaError_t project(const DevHam &H, const T *Y, int ncols, long ld, cons
                            TC *C, TC alpha, cudaStream_t st)
 {
     if (H.natoms == 0 || ncols <= 0) return cudaSuccess;
-    constexpr int CB = 8, NT = 256;
+    // FP32 accumulators leave room for 16 columns per CTA (32 loads of Y in flight per
+    // thread); FP64 ones for 8
+    constexpr int CB = sizeof(TC) == 4 ? 16 : 8, NT = 256;
     dim3 grid(H.natoms, (ncols + CB - 1) / CB);
     if (grid.y > 65535) return cudaErrorInvalidValue;
     k_project<T, TC, CB, NT, ILV>
@@ -249,8 +251,11 @@ k_scatter_f64(double *out, long ld, int ncols, long nuniq, const int *__restrict
 // column then costs one 16-byte load per entry (L1/L2-resident) and one read-modify-write.
 // Nodes covered by more than kScatRegs atoms take the generic loop.
 
+// The sums of the thread's kScatCols columns are formed first (coefficient loads hit L1 /
+// L2), then all output loads are issued before any store, so a thread keeps kScatCols
+// independent DRAM reads in flight (the kernel is bound by that latency, not by bytes).
 template <int N>
-__device__ __forceinline__ void scatter_node_f32(float *o, long ld, int c0, int c1, int q0,
+__device__ __forceinline__ void scatter_node_f32(float *o, long ld, int c0, int nc, int q0,
                                                  int ncols, const int *__restrict__ nl_atom,
                                                  const float4 *__restrict__ g4,
                                                  const float4 *__restrict__ Cs4)
@@ -260,22 +265,29 @@ __device__ __forceinline__ void scatter_node_f32(float *o, long ld, int c0, int 
 #pragma unroll
     for (int t = 0; t < N; ++t) {
         gq[t] = g4[q0 + t];
-        cq[t] = Cs4 + (long)nl_atom[q0 + t] * ncols;
+        cq[t] = Cs4 + (long)nl_atom[q0 + t] * ncols + c0;
     }
-#pragma unroll 4
-    for (int c = c0; c < c1; ++c) {
-        float v = 0.0f;
+    float v[kScatCols], x[kScatCols];
 #pragma unroll
-        for (int t = 0; t < N; ++t) {
-            const float4 cc = cq[t][c];
-            v += gq[t].x * cc.x;
-            v += gq[t].y * cc.y;
-            v += gq[t].z * cc.z;
-            v += gq[t].w * cc.w;
+    for (int c = 0; c < kScatCols; ++c) {
+        v[c] = 0.0f;
+        if (c < nc) {
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                const float4 cc = cq[t][c];
+                v[c] += gq[t].x * cc.x;
+                v[c] += gq[t].y * cc.y;
+                v[c] += gq[t].z * cc.z;
+                v[c] += gq[t].w * cc.w;
+            }
         }
-        float *oc = o + (long)c * ld;
-        *oc = *oc + v;
     }
+    float *oc = o + (long)c0 * ld;
+#pragma unroll
+    for (int c = 0; c < kScatCols; ++c) x[c] = c < nc ? oc[(long)c * ld] : 0.0f;
+#pragma unroll
+    for (int c = 0; c < kScatCols; ++c)
+        if (c < nc) oc[(long)c * ld] = x[c] + v[c];
 }
 
 __global__ void __launch_bounds__(kScatNodes)
@@ -285,17 +297,17 @@ k_scatter_f32(float *out, long ld, int ncols, long nuniq, const int *__restrict_
 {
     const long u = (long)blockIdx.x * kScatNodes + threadIdx.x;
     if (u >= nuniq) return;
-    const int c0 = blockIdx.y * kScatCols, c1 = min(ncols, c0 + kScatCols);
+    const int c0 = blockIdx.y * kScatCols, nc = min(ncols - c0, kScatCols);
     float *o = out + uniq_node[u];
     const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
     switch (q1 - q0) {
-    case 1: scatter_node_f32<1>(o, ld, c0, c1, q0, ncols, nl_atom, g4, Cs4); return;
-    case 2: scatter_node_f32<2>(o, ld, c0, c1, q0, ncols, nl_atom, g4, Cs4); return;
-    case 3: scatter_node_f32<3>(o, ld, c0, c1, q0, ncols, nl_atom, g4, Cs4); return;
-    case 4: scatter_node_f32<kScatRegs>(o, ld, c0, c1, q0, ncols, nl_atom, g4, Cs4); return;
+    case 1: scatter_node_f32<1>(o, ld, c0, nc, q0, ncols, nl_atom, g4, Cs4); return;
+    case 2: scatter_node_f32<2>(o, ld, c0, nc, q0, ncols, nl_atom, g4, Cs4); return;
+    case 3: scatter_node_f32<3>(o, ld, c0, nc, q0, ncols, nl_atom, g4, Cs4); return;
+    case 4: scatter_node_f32<kScatRegs>(o, ld, c0, nc, q0, ncols, nl_atom, g4, Cs4); return;
     default: break;
     }
-    for (int c = c0; c < c1; ++c) {
+    for (int c = c0; c < c0 + nc; ++c) {
         float v = 0.0f;
         for (int q = q0; q < q1; ++q) {
             const float4 g = g4[q], cc = Cs4[(long)nl_atom[q] * ncols + c];

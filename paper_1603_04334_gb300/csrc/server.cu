@@ -1,0 +1,364 @@
+// server.cu -- request loop for cluster eigensolves on one GPU (include/sparc_server.h).
+//
+// A fixed pool of worker threads, one CUDA stream each; an arrival-ordered queue; an HBM
+// budget charged with each request's device-memory estimate on admission and credited
+// back when it finishes. A worker takes the first queued request that fits what is left
+// of the budget, runs its whole solve on its own stream (context, blocks, bounds resident
+// on the device throughout), publishes the result and takes the next one, so requests join
+// while others run and their kernels overlap on the device. The estimate follows the
+// library's own allocation rules (the same size helpers the context uses), and the solve
+// reports an upper bound of what it actually held next to it.
+#include "internal.cuh"
+#include "sparc.h"
+#include "sparc_server.h"
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+namespace sparc {
+namespace {
+
+constexpr int kMaxPassOver = 8;
+constexpr int kLanczosSteps = 10;
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// start block: X[c ld + p] = u(mix64(key ^ (c nd + p))) - 0.5, u(z) = (z >> 11) 2^-53
+template <typename T>
+__global__ void k_start_block(T *X, long nd, int ns, long ld, unsigned long long key)
+{
+    const long tot = nd * ns;
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < tot;
+         q += (long)gridDim.x * blockDim.x) {
+        const long c = q / nd, p = q % nd;
+        const double u = (double)(mix64(key ^ (unsigned long long)q) >> 11) * 0x1.0p-53;
+        X[c * ld + p] = (T)(u - 0.5);
+    }
+}
+
+unsigned long long host_mix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct Request {
+    long long id = 0;
+    sparc_request spec{};
+    std::vector<double> R, Z, gamma;
+    size_t est = 0;
+    int passed_over = 0;
+    bool done = false;
+    sparc_result_info info{};
+    std::vector<double> ritz, resid;
+};
+
+double now_since(std::chrono::steady_clock::time_point t0)
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+long nodes_in_support_box(double h, double rcut)
+{
+    const long w = 2 * (long)std::ceil(rcut / h) + 1;  // cube around the sphere
+    return w * w * w;
+}
+
+}  // namespace
+}  // namespace sparc
+
+using namespace sparc;
+
+struct sparc_server {
+    size_t budget = 0, reserved = 0, peak_reserved = 0;
+    int slots = 0;
+    bool simulate = false;
+    int running = 0, max_running = 0;
+    int device = 0;  // CUDA device of the creating thread; every worker uses it
+    long long completed = 0, next_id = 1;
+    bool stop = false;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> queue;
+    std::map<long long, std::unique_ptr<Request>> all;
+    std::vector<std::thread> workers;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+};
+
+namespace {
+
+// First queued request that fits what is left of the budget. Each waiting request ahead of
+// the one admitted counts one pass-over; a request passed over kMaxPassOver times blocks
+// the requests behind it until it fits.
+Request *pick(sparc_server *S)
+{
+    const size_t left = S->budget - S->reserved;
+    for (size_t i = 0; i < S->queue.size(); ++i) {
+        Request *r = S->queue[i];
+        if (r->est <= left) {
+            for (size_t j = 0; j < i; ++j) S->queue[j]->passed_over++;
+            S->queue.erase(S->queue.begin() + (long)i);
+            return r;
+        }
+        if (r->passed_over >= kMaxPassOver) return nullptr;
+    }
+    return nullptr;
+}
+
+sparc_status solve(const Request &r, cudaStream_t st, sparc_result_info &info,
+                   std::vector<double> &ritz, std::vector<double> &resid)
+{
+    const sparc_request &q = r.spec;
+    const long nd = (long)q.n[0] * q.n[1] * q.n[2];
+    const size_t es = q.dtype == SPARC_F32 ? 4 : 8;
+    sparc_grid g{{q.n[0], q.n[1], q.n[2]}, q.h, kRadius};
+    sparc_atoms a{q.natoms, r.R.data(), r.Z.data(), r.gamma.data(), 0.8, 3.0, 1.0};
+    sparc_ctx *ctx = nullptr;
+    sparc_status s = sparc_create(&g, nullptr, &a, st, &ctx);
+    if (s != SPARC_OK) return s;
+    void *X = nullptr, *W = nullptr;
+    const size_t bb = es * (size_t)nd * q.ns;
+    auto finish = [&](sparc_status rs) {
+        size_t peak = 0;
+        sparc_device_bytes(ctx, &peak);
+        info.used_bytes = peak + (X ? bb : 0) + (W ? bb : 0);
+        if (X) cudaFree(X);
+        if (W) cudaFree(W);
+        sparc_destroy(ctx);
+        return rs;
+    };
+    if (cudaMalloc(&X, bb) != cudaSuccess || cudaMalloc(&W, bb) != cudaSuccess) {
+        cudaGetLastError();
+        return finish(SPARC_ERR_OOM);
+    }
+    const unsigned long long key = host_mix64(q.seed);
+    if (q.dtype == SPARC_F32)
+        k_start_block<float><<<152 * 8, 256, 0, st>>>((float *)X, nd, q.ns, nd, key);
+    else
+        k_start_block<double><<<152 * 8, 256, 0, st>>>((double *)X, nd, q.ns, nd, key);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) return finish(SPARC_ERR_CUDA);
+    double lo = 0, hi = 0;
+    s = sparc_lanczos_bounds(ctx, kLanczosSteps, q.seed, &lo, &hi);
+    if (s != SPARC_OK) return finish(s);
+    double b[3] = {lo + 0.25 * (hi - lo), hi, lo};  // first iteration: a = a0 + (b - a0) / 4
+    ritz.assign(q.ns, 0.0);
+    resid.assign(q.ns, 0.0);
+    for (int it = 0; it < q.max_iters; ++it) {
+        s = sparc_chefsi_step(ctx, q.dtype, X, W, q.ns, nd, q.degree, b, ritz.data(),
+                              resid.data());
+        if (s != SPARC_OK) return finish(s);
+        info.iters = it + 1;
+        const double mr = *std::max_element(resid.begin(), resid.end());
+        if (mr <= q.tol) {
+            info.converged = 1;
+            break;
+        }
+    }
+    return finish(SPARC_OK);
+}
+
+void worker(sparc_server *S)
+{
+    cudaStream_t st = nullptr;
+    if (!S->simulate && (cudaSetDevice(S->device) != cudaSuccess ||
+                         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess))
+        st = nullptr;
+    for (;;) {
+        Request *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] { return S->stop || (r = pick(S)) != nullptr; });
+            if (!r) break;
+            S->reserved += r->est;
+            S->peak_reserved = std::max(S->peak_reserved, S->reserved);
+            S->running++;
+            S->max_running = std::max(S->max_running, S->running);
+            r->info.t_admit = now_since(S->t0);
+        }
+        sparc_result_info info = r->info;
+        std::vector<double> ritz, resid;
+        sparc_status s;
+        if (S->simulate) {
+            std::this_thread::sleep_for(std::chrono::duration<double>(r->spec.sim_seconds));
+            ritz.assign(r->spec.ns, 0.0);
+            resid.assign(r->spec.ns, 0.0);
+            info.iters = r->spec.max_iters;
+            info.converged = 1;
+            info.used_bytes = r->est;
+            s = SPARC_OK;
+        } else if (!st) {
+            s = SPARC_ERR_CUDA;
+        } else {
+            s = solve(*r, st, info, ritz, resid);
+        }
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            info.status = s;
+            info.t_done = now_since(S->t0);
+            r->info = info;
+            r->ritz = std::move(ritz);
+            r->resid = std::move(resid);
+            r->done = true;
+            S->reserved -= r->est;
+            S->running--;
+            S->completed++;
+        }
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();
+    }
+    if (st) cudaStreamDestroy(st);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t sparc_request_bytes(const sparc_request *q)
+{
+    if (!q) return 0;
+    const long nd = (long)q->n[0] * q->n[1] * q->n[2];
+    const int ns = q->ns;
+    const size_t es = q->dtype == SPARC_F32 ? 4 : 8;
+    const size_t na = q->natoms > 0 ? (size_t)q->natoms : 1;
+    // context: V_eff (FP64, FP32, FP32 pair) and set-up scratch per node, projector entries
+    // (index, chi and gamma chi in FP64 / FP32 / pairs, inverse map), bounded by the cube
+    // around each support sphere
+    const size_t per_node = 8 + 4 + 8 + 4 * 8 + 8;
+    const size_t per_entry = 4 + 4 + 32 + 32 + 16 + 16 + 32 + 4 + 4 + 16 + 32 + 16;
+    const size_t entries = na * (size_t)nodes_in_support_box(q->h, 3.0);
+    size_t b = per_node * (size_t)nd + per_entry * entries + 4096 * 64;
+    // workspaces: projection coefficients, H Y_f (FP64), rotated H X (residuals), Gram
+    // partials (FP64 form) or the tensor-core Gram (mixed form), Ns x Ns matrices, Lanczos
+    b += sizeof(double) * 4 * na * ns;
+    b += sizeof(double) * (size_t)nd * ns;
+    b += es * (size_t)nd * ns;
+    if (q->dtype == SPARC_F32)
+        b += gram_tc_workspace(nd, ns, false, true);
+    else
+        b += sizeof(double) * (size_t)gram_part_elems(ns, nd);
+    b += sizeof(double) * (4 * (size_t)ns * ns + 2 * (size_t)ns + (size_t)dense_work_elems(ns));
+    b += sizeof(double) * (3 * (size_t)nd + kDotBlocks + 4096);
+    // the request's two orbital blocks
+    b += 2 * es * (size_t)nd * ns;
+    return b + b / 16;  // allocation granularity
+}
+
+sparc_status sparc_server_create(size_t hbm_budget_bytes, int slots, int simulate,
+                                 sparc_server **out)
+{
+    if (!out || slots < 1 || slots > 64 || hbm_budget_bytes == 0) return SPARC_ERR_ARG;
+    sparc_server *S = new (std::nothrow) sparc_server();
+    if (!S) return SPARC_ERR_OOM;
+    S->budget = hbm_budget_bytes;
+    S->slots = slots;
+    S->simulate = simulate != 0;
+    if (!S->simulate && cudaGetDevice(&S->device) != cudaSuccess) {
+        delete S;
+        return SPARC_ERR_CUDA;
+    }
+    for (int i = 0; i < slots; ++i) S->workers.emplace_back(worker, S);
+    *out = S;
+    return SPARC_OK;
+}
+
+sparc_status sparc_server_submit(sparc_server *S, const sparc_request *q, long long *id)
+{
+    if (!S || !q || !id) return SPARC_ERR_ARG;
+    if (q->n[0] < 1 || q->n[1] < 1 || q->n[2] < 1 || !(q->h > 0) || q->ns < 1 ||
+        q->ns > kMaxDense || q->degree < 1 || q->max_iters < 1 || q->natoms < 0 ||
+        (q->natoms > 0 && (!q->R || !q->Z || !q->gamma)) ||
+        (q->dtype != SPARC_F32 && q->dtype != SPARC_F64) ||
+        (long)q->n[0] * q->n[1] * q->n[2] < q->ns)
+        return SPARC_ERR_ARG;
+    auto r = std::make_unique<Request>();
+    r->spec = *q;
+    r->R.assign(q->R ? q->R : nullptr, q->R ? q->R + 3 * (size_t)q->natoms : nullptr);
+    r->Z.assign(q->Z ? q->Z : nullptr, q->Z ? q->Z + (size_t)q->natoms : nullptr);
+    r->gamma.assign(q->gamma ? q->gamma : nullptr, q->gamma ? q->gamma + 4 * (size_t)q->natoms : nullptr);
+    r->spec.R = r->spec.Z = r->spec.gamma = nullptr;
+    r->est = sparc_request_bytes(q);
+    if (r->est > S->budget) return SPARC_ERR_BUDGET;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) return SPARC_ERR_ARG;
+        r->id = S->next_id++;
+        r->info.ns = q->ns;
+        r->info.est_bytes = r->est;
+        r->info.t_submit = now_since(S->t0);
+        r->info.t_admit = r->info.t_done = -1.0;
+        *id = r->id;
+        S->queue.push_back(r.get());
+        S->all.emplace(r->id, std::move(r));
+    }
+    S->cv_work.notify_all();
+    return SPARC_OK;
+}
+
+sparc_status sparc_server_wait(sparc_server *S, long long id, double timeout_s,
+                               sparc_result_info *info, double *ritz, double *resid)
+{
+    if (!S) return SPARC_ERR_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end()) return SPARC_ERR_ARG;
+    Request *r = it->second.get();
+    auto ready = [&] { return r->done; };
+    if (timeout_s < 0)
+        S->cv_done.wait(lk, ready);
+    else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready))
+        return SPARC_ERR_TIMEOUT;
+    if (info) *info = r->info;
+    if (ritz && !r->ritz.empty()) std::memcpy(ritz, r->ritz.data(), sizeof(double) * r->ritz.size());
+    if (resid && !r->resid.empty())
+        std::memcpy(resid, r->resid.data(), sizeof(double) * r->resid.size());
+    return SPARC_OK;
+}
+
+sparc_status sparc_server_stats(sparc_server *S, long long *completed, int *max_running,
+                                size_t *peak_reserved)
+{
+    if (!S) return SPARC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (completed) *completed = S->completed;
+    if (max_running) *max_running = S->max_running;
+    if (peak_reserved) *peak_reserved = S->peak_reserved;
+    return SPARC_OK;
+}
+
+sparc_status sparc_server_destroy(sparc_server *S)
+{
+    if (!S) return SPARC_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        for (Request *r : S->queue) {
+            r->info.status = SPARC_ERR_ARG;
+            r->done = true;
+        }
+        S->queue.clear();
+    }
+    S->cv_work.notify_all();
+    S->cv_done.notify_all();
+    for (std::thread &t : S->workers) t.join();
+    delete S;
+    return SPARC_OK;
+}
+
+}  // extern "C"

@@ -59,6 +59,7 @@ struct sparc_ctx {
     void *roth = nullptr;    size_t roth_bytes = 0;  // rotated H block (residuals)
     void *part = nullptr;    size_t part_bytes = 0;  // Gram split-K partials
     void *tcws = nullptr;    size_t tcws_bytes = 0;  // tensor-core Gram digits, exponents, partials
+    size_t dev_bytes = 0, dev_peak = 0;  // device bytes allocated (see dmalloc)
     void *dm = nullptr;      size_t dm_bytes = 0;    // M, Hs, Cf, ritz, resid, dense work
     void *lz = nullptr;      size_t lz_bytes = 0;    // Lanczos vectors and scalars
     int *flags = nullptr;                            // device status words
@@ -163,10 +164,13 @@ sparc_status ensure(sparc_ctx *ctx, void *&p, size_t &cap, size_t bytes)
 {
     if (bytes <= cap) return SPARC_OK;
     if (p) CK(cudaFree(p));
+    ctx->dev_bytes -= cap;
     p = nullptr;
     cap = 0;
     CK(cudaMalloc(&p, bytes));
     cap = bytes;
+    ctx->dev_bytes += bytes;
+    if (ctx->dev_bytes > ctx->dev_peak) ctx->dev_peak = ctx->dev_bytes;
     return SPARC_OK;
 }
 
@@ -174,6 +178,10 @@ template <typename T>
 sparc_status dmalloc(sparc_ctx *ctx, T *&p, size_t n)
 {
     CK(cudaMalloc((void **)&p, sizeof(T) * (n ? n : 1)));
+    // counted until the context is destroyed (set-up temporaries included): an upper
+    // bound of the context's peak device memory
+    ctx->dev_bytes += sizeof(T) * (n ? n : 1);
+    if (ctx->dev_bytes > ctx->dev_peak) ctx->dev_peak = ctx->dev_bytes;
     return SPARC_OK;
 }
 
@@ -380,13 +388,18 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
     else
         { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f32((const float *)Yf, ld, nd, ns, d.Cf, (float *)xout, ld, ctx->st)); }
     if (resid_host) {
-        TRY(ensure(ctx, ctx->roth, ctx->roth_bytes, sizeof(double) * (size_t)ns * ld));
-        double *hxr = (double *)ctx->roth;
-        { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64(HX, ld, nd, ns, d.Cf, hxr, ld, ctx->st)); }
-        if (sizeof(T) == 8)
+        // H X = (H Y_f) (L^-T Q); residuals against the rotated block. The FP32 form rotates
+        // in FP32 arithmetic (the block itself is FP32; about 1e-7 relative of |H X|).
+        TRY(ensure(ctx, ctx->roth, ctx->roth_bytes, sizeof(T) * (size_t)ns * ld));
+        if (sizeof(T) == 8) {
+            double *hxr = (double *)ctx->roth;
+            { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64(HX, ld, nd, ns, d.Cf, hxr, ld, ctx->st)); }
             { PHASE(SPARC_PHASE_OTHER); CK(resid_f64((const double *)xout, hxr, ld, nd, ns, d.ritz, d.resid, ctx->st)); }
-        else
+        } else {
+            float *hxr = (float *)ctx->roth;
+            { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64in_f32(HX, ld, nd, ns, d.Cf, hxr, ld, ctx->st)); }
             { PHASE(SPARC_PHASE_OTHER); CK(resid_f32((const float *)xout, hxr, ld, nd, ns, d.ritz, d.resid, ctx->st)); }
+        }
     }
     if (xout != dst) TRY(copy_block<T>(ctx, dst, xout, ns, ld));
     CK(cudaMemcpyAsync(ctx->pin, d.ritz, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, ctx->st));
@@ -861,6 +874,13 @@ sparc_status sparc_launch_count(long long *count)
 {
     if (!count) return SPARC_ERR_ARG;
     *count = g_launches.load(std::memory_order_relaxed);
+    return SPARC_OK;
+}
+
+sparc_status sparc_device_bytes(const sparc_ctx *ctx, size_t *peak_bytes)
+{
+    if (!ctx || !peak_bytes) return SPARC_ERR_ARG;
+    *peak_bytes = ctx->dev_peak;
     return SPARC_OK;
 }
 

@@ -207,17 +207,28 @@ k_scatter_df(double *out, long ld, int ncols, long nuniq, const int *__restrict_
     const int c0 = blockIdx.y * kScatCols, c1 = min(ncols, c0 + kScatCols);
     const long node = uniq_node[u];
     const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
-#pragma unroll 2
-    for (int c = c0; c < c1; ++c) {
-        float vh = 0.0f, vl = 0.0f;
-        for (int q = q0; q < q1; ++q) {
-            const float2 *cs = Cs + (long)nl_atom[q] * 4 * ncols + c;
+    // all column sums first (coefficients from L1 / L2), then every output read is issued
+    // before any store: kScatCols independent DRAM reads in flight per thread
+    double v[kScatCols], x[kScatCols];
 #pragma unroll
-            for (int l = 0; l < 4; ++l) mac(g[4L * q + l], cs[(long)l * ncols], vh, vl);
+    for (int k = 0; k < kScatCols; ++k) {
+        const int c = c0 + k;
+        float vh = 0.0f, vl = 0.0f;
+        if (c < c1) {
+            for (int q = q0; q < q1; ++q) {
+                const float2 *cs = Cs + (long)nl_atom[q] * 4 * ncols + c;
+#pragma unroll
+                for (int l = 0; l < 4; ++l) mac(g[4L * q + l], cs[(long)l * ncols], vh, vl);
+            }
         }
-        double *o = out + node + (long)c * ld;
-        *o = *o + pair_to_double(vh, vl);
+        v[k] = pair_to_double(vh, vl);
     }
+    double *o = out + node + (long)c0 * ld;
+#pragma unroll
+    for (int k = 0; k < kScatCols; ++k) x[k] = c0 + k < c1 ? o[(long)k * ld] : 0.0;
+#pragma unroll
+    for (int k = 0; k < kScatCols; ++k)
+        if (c0 + k < c1) o[(long)k * ld] = x[k] + v[k];
 }
 
 cudaError_t scatter_f64_df(const DevHam &H, const float2 *Cs, double *out, int ncols, long ld,

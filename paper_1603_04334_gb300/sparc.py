@@ -38,7 +38,7 @@ EXPORTS = ("sparc_create", "sparc_destroy", "sparc_last_error", "sparc_get_veff"
            "sparc_profile_enable",
            "sparc_profile_read", "sparc_profile_reset", "sparc_launch_count",
            "sparc_gram_noalloc", "sparc_sync", "sparc_selftest_timeout",
-           "sparc_gram_tc")
+           "sparc_gram_tc", "sparc_device_bytes")
 
 PHASES = ("stencil", "project", "scatter", "gram", "dense", "rotate", "other")
 

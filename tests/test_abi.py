@@ -1,7 +1,8 @@
 """C-ABI checks that need no GPU: the library builds for sm_103a, loads, and exports every
-entry point include/sparc.h declares; the binding names the same set; the product path
-and the oracle share no code."""
+entry point the headers in include/ declare; the bindings name the same set; the product
+path and the oracle share no code."""
 import ctypes
+import glob
 import os
 import re
 import shutil
@@ -10,16 +11,19 @@ import subprocess
 import pytest
 
 from paper_1603_04334_gb300 import build as pkg_build
-from paper_1603_04334_gb300 import sparc
+from paper_1603_04334_gb300 import serve, sparc
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "sparc.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
-def header_symbols(path=HEADER):
-    txt = open(path).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(sparc_[A-Za-z0-9_]+)\s*\(", txt)))
+def header_symbols(paths=HEADERS):
+    syms = set()
+    for path in paths:
+        txt = open(path).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        syms |= set(re.findall(r"\b(sparc_[A-Za-z0-9_]+)\s*\(", txt))
+    return sorted(syms)
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +38,7 @@ def test_library_exports_every_declared_symbol(lib_path):
     syms = header_symbols()
     assert len(syms) >= 11
     for s in syms:
-        assert hasattr(L, s), f"{s} declared in sparc.h but not exported"
+        assert hasattr(L, s), f"{s} declared in include/ but not exported"
     out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True,
                          text=True).stdout
     exported = set(re.findall(r"\bT (sparc_[A-Za-z0-9_]+)$", out, flags=re.M))
@@ -44,7 +48,7 @@ def test_library_exports_every_declared_symbol(lib_path):
 
 
 def test_binding_names_match_header():
-    assert sorted(sparc.EXPORTS) == header_symbols()
+    assert sorted(sparc.EXPORTS + serve.EXPORTS) == header_symbols()
 
 
 def test_library_is_built_for_sm103a(lib_path):
