@@ -205,6 +205,8 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
     const long nchunk = nstep / kStepsPerChunk;
     const long c0 = (long)split * nchunk / nsplit, c1 = (long)(split + 1) * nchunk / nsplit;
     const long st0 = c0 * kStepsPerChunk, st1 = c1 * kStepsPerChunk;
+    // a diagonal tile of A^T A reads one operand: B's descriptors point at A's blobs
+    const bool one = DA == DB && tb.x == tb.y;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -241,10 +243,11 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                     break;
                 }
                 unsigned char *dst = smem + (size_t)s * kStageBytes;
-                mbar_arrive_expect_tx(&full[s], kStageBytes);
+                mbar_arrive_expect_tx(&full[s], one ? kOperandBytes : kStageBytes);
                 bulk_load(dst, DA + blob_offset(tb.x, st, 0, nstep), kOperandBytes, &full[s]);
-                bulk_load(dst + kOperandBytes, DB + blob_offset(tb.y, st, 0, nstep), kOperandBytes,
-                          &full[s]);
+                if (!one)
+                    bulk_load(dst + kOperandBytes, DB + blob_offset(tb.y, st, 0, nstep),
+                              kOperandBytes, &full[s]);
                 issued = j + 1;
             }
             if (abort_flag) {
@@ -279,7 +282,7 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                 }
                 tc_fence_after();
                 const unsigned char *a = smem + (size_t)s * kStageBytes;
-                const unsigned char *b = a + kOperandBytes;
+                const unsigned char *b = one ? a : a + kOperandBytes;
 #pragma unroll
                 for (int ks = 0; ks < kStep / 16; ++ks) {
 #pragma unroll
@@ -440,6 +443,40 @@ static cudaError_t tc_digits(const T *X, long ld, long nd, int ns, const TcPlan 
     return cudaGetLastError();
 }
 
+// Tile list (host-built, uploaded) and the kernel's shared-memory attribute.
+static cudaError_t tc_prepare(const TcPlan &p, bool sym, int2 *tiles, cudaStream_t st)
+{
+    static bool attr_set = false;
+    cudaError_t e;
+    if (!attr_set) {
+        e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    static thread_local int2 host_tiles[64 * 65 / 2 + 64 * 64];
+    if (p.ntiles > (int)(sizeof(host_tiles) / sizeof(int2))) return cudaErrorInvalidValue;
+    int n = 0;
+    for (int a = 0; a < p.nblk; ++a)
+        for (int b = (sym ? a : 0); b < p.nblk; ++b) host_tiles[n++] = make_int2(a, b);
+    return cudaMemcpyAsync(tiles, host_tiles, p.tiles_bytes, cudaMemcpyHostToDevice, st);
+}
+
+static cudaError_t tc_run(const TcPlan &p, const __nv_bfloat16 *DA, const int *EA,
+                          const __nv_bfloat16 *DB, const int *EB, const int2 *tiles,
+                          double *part, int ns, bool sym, double *G, int *err, cudaStream_t st)
+{
+    k_gram_tc<<<p.ntiles * p.nsplit, kThreads, kSmemBytes, st>>>(DA, EA, DB, EB, p.ns_pad, p.nstep,
+                                                                  tiles, p.ntiles, p.nsplit, part,
+                                                                  err);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_gram_tc_reduce<<<152 * 4, 256, 0, st>>>(part, tiles, p.ntiles, p.nsplit, ns, sym, G);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <typename TA, typename TB>
 cudaError_t gram_tc(const TA *A, long lda, const TB *B, long ldb, long nd, int ns, double *G,
                     void *ws, size_t ws_bytes, bool sym, int *err, cudaStream_t st)
@@ -465,34 +502,45 @@ cudaError_t gram_tc(const TA *A, long lda, const TB *B, long ldb, long nd, int n
     double *part = (double *)take(p.part_bytes);
     int2 *tiles = (int2 *)take(p.tiles_bytes);
 
-    static bool attr_set = false;
     cudaError_t e;
-    if (!attr_set) {
-        e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmemBytes);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    // tile list (host-built, a few hundred entries at most)
-    static thread_local int2 host_tiles[64 * 65 / 2 + 64 * 64];
-    if (p.ntiles > (int)(sizeof(host_tiles) / sizeof(int2))) return cudaErrorInvalidValue;
-    int n = 0;
-    for (int a = 0; a < p.nblk; ++a)
-        for (int b = (sym ? a : 0); b < p.nblk; ++b) host_tiles[n++] = make_int2(a, b);
-    e = cudaMemcpyAsync(tiles, host_tiles, p.tiles_bytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
+    if ((e = tc_prepare(p, sym, tiles, st)) != cudaSuccess) return e;
     if ((e = tc_digits<TA>(A, lda, nd, ns, p, DA, EA, st)) != cudaSuccess) return e;
     if (!same && (e = tc_digits<TB>(B, ldb, nd, ns, p, DB, EB, st)) != cudaSuccess) return e;
-    k_gram_tc<<<p.ntiles * p.nsplit, kThreads, kSmemBytes, st>>>(DA, EA, DB, EB, p.ns_pad, p.nstep,
-                                                                  tiles, p.ntiles, p.nsplit, part,
-                                                                  err);
-    note_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_gram_tc_reduce<<<152 * 4, 256, 0, st>>>(part, tiles, p.ntiles, p.nsplit, ns, sym, G);
-    note_launch();
-    return cudaGetLastError();
+    return tc_run(p, DA, EA, DB, EB, tiles, part, ns, sym, G, err, st);
 }
 
+template <typename TA, typename TB>
+cudaError_t gram_tc_pair(const TA *A, long lda, const TB *B, long ldb, long nd, int ns,
+                         double *M, double *Hm, void *ws, size_t ws_bytes, int *err,
+                         cudaStream_t st)
+{
+    if (ns <= 0 || nd <= 0) return cudaErrorInvalidValue;
+    const TcPlan p = tc_plan(nd, ns, true);
+    if (ws_bytes < gram_tc_workspace(nd, ns, false, true)) return cudaErrorInvalidValue;
+    unsigned char *w = (unsigned char *)ws;
+    auto take = [&](size_t b) {
+        unsigned char *r = w;
+        w += align256(b);
+        return r;
+    };
+    __nv_bfloat16 *DA = (__nv_bfloat16 *)take(p.digits_bytes);
+    int *EA = (int *)take(p.exps_bytes);
+    __nv_bfloat16 *DB = (__nv_bfloat16 *)take(p.digits_bytes);
+    int *EB = (int *)take(p.exps_bytes);
+    double *part = (double *)take(p.part_bytes);
+    int2 *tiles = (int2 *)take(p.tiles_bytes);
+    cudaError_t e;
+    if ((e = tc_prepare(p, true, tiles, st)) != cudaSuccess) return e;
+    if ((e = tc_digits<TA>(A, lda, nd, ns, p, DA, EA, st)) != cudaSuccess) return e;
+    if ((e = tc_digits<TB>(B, ldb, nd, ns, p, DB, EB, st)) != cudaSuccess) return e;
+    if ((e = tc_run(p, DA, EA, DA, EA, tiles, part, ns, true, M, err, st)) != cudaSuccess)
+        return e;
+    return tc_run(p, DA, EA, DB, EB, tiles, part, ns, true, Hm, err, st);
+}
+
+template cudaError_t gram_tc_pair<float, double>(const float *, long, const double *, long, long,
+                                                 int, double *, double *, void *, size_t, int *,
+                                                 cudaStream_t);
 template cudaError_t gram_tc<float, float>(const float *, long, const float *, long, long, int,
                                            double *, void *, size_t, bool, int *, cudaStream_t);
 template cudaError_t gram_tc<float, double>(const float *, long, const double *, long, long, int,

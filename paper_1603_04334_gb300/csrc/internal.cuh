@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+struct sparc_ctx;  // include/sparc.h
+
 namespace sparc {
 
 constexpr int kRadius = 6;  // stencil radius the kernels are written for (n_o <= 6)
@@ -73,6 +75,66 @@ cudaError_t scatter_f64_df(const DevHam &H, const float2 *Cs, double *out, int n
 // out += V_nl part from Cs = alpha chi^T Y, FP32 blocks (nonlocal.cu)
 cudaError_t scatter_f32(const DevHam &H, const float *Cs, float *out, int ncols, long ld,
                         cudaStream_t st);
+// ---- batched FP32 filter steps over many clusters (batch.cu) --------------------------
+// One unit of work of a batched launch. stencil: column `col`, tile (a, b) of the x-y
+// plane, planes k0 .. k1-1; projection: atom a, columns col .. col+15; scatter: covered
+// nodes a*256 .. a*256+255, columns col .. col+15.
+struct BatchItem {
+    int cluster, col, a, b, k0, k1;
+};
+// Per cluster and step: where the stencil reads and writes, and its coefficients.
+struct BatchStencil {
+    const float *Y;
+    const float *Yprev;  // null in the first filter step
+    float *out;
+    const float *V;
+    int n0, n1, n2;
+    long ld;
+    StepCoef<float> cf;
+};
+// Per cluster and step: the nonlocal term's tables, input, output and coefficient buffer.
+struct BatchNonlocal {
+    const float *Y;
+    float *out;
+    float *C;  // alpha chi^T Y, [atom][column][4]
+    const int *atom_ptr, *idx, *uniq_node, *uniq_ptr, *nl_atom;
+    const float *chi_f, *nl_gf;
+    long ld, nuniq;
+    int ncols;
+    float alpha;
+};
+// Per cluster and step for the TMA-fed batched stencil: device addresses of the tensor maps
+// of Y_j (halo box) and Y_{j-1} (tile box; null in the first step), and the rest as above.
+struct BatchTma {
+    const void *mY;
+    const void *mP;
+    float *out;
+    const float *V;
+    int n0, n1, n2;
+    long ld;
+    StepCoef<float> cf;
+};
+cudaError_t encode_f32_maps(const DevHam &H, const float *base, int ncols, long ld, void *maps);
+size_t tensor_map_bytes();
+void batch_tma_tile(int &bx, int &by);
+cudaError_t batch_stencil_tma(const BatchItem *items, int nitems, const BatchTma *cs, int grid,
+                              int *err, cudaStream_t st);
+int batch_stencil_shapes();
+void batch_stencil_tile(int shape, int &bx, int &by);
+cudaError_t batch_stencil(int shape, const BatchItem *items, int nitems, const BatchStencil *cs,
+                          int grid, cudaStream_t st);
+cudaError_t batch_project(const BatchItem *items, int nitems, const BatchNonlocal *cs, int grid,
+                          cudaStream_t st);
+cudaError_t batch_scatter(const BatchItem *items, int nitems, const BatchNonlocal *cs, int grid,
+                          cudaStream_t st);
+StepCoef<float> coef_f32(const DevHam &H, double alpha, double shift, double beta);
+// context accessors for the batch layer (sparc.cu)
+const DevHam *ctx_ham(const sparc_ctx *ctx);
+cudaStream_t ctx_stream(const sparc_ctx *ctx);
+float *ctx_coef_buffer(sparc_ctx *ctx, int ncols);  // grows the context's C buffer
+constexpr int kBatchCols = 16;     // columns per nonlocal work item
+constexpr int kBatchNodes = 256;   // covered nodes per scatter work item
+
 cudaError_t stencil_f32(const DevHam &H, const float *Y, const float *Yprev, float *out,
                         int ncols, long ld, double alpha, double shift, double beta,
                         cudaStream_t st);
@@ -154,6 +216,12 @@ size_t gram_tc_workspace(long nd, int ns, bool same_operand, bool sym);
 template <typename TA, typename TB>
 cudaError_t gram_tc(const TA *A, long lda, const TB *B, long ldb, long nd, int ns, double *G,
                     void *ws, size_t ws_bytes, bool sym, int *err, cudaStream_t st);
+// M = A^T A and Hm = A^T B (both symmetric-tiled and mirrored) with one digit pass of A;
+// ws: gram_tc_workspace(nd, ns, false, true) bytes.
+template <typename TA, typename TB>
+cudaError_t gram_tc_pair(const TA *A, long lda, const TB *B, long ldb, long nd, int ns,
+                         double *M, double *Hm, void *ws, size_t ws_bytes, int *err,
+                         cudaStream_t st);
 cudaError_t gram_f64_nsplit(const double *A, long lda, const double *B, long ldb, long nd, int ns,
                             double *G, double *part, int nsplit, cudaStream_t st);
 // out (nd x ns, ldo) = A (nd x ns, lda) Q (ns x ns, column-major FP64)

@@ -23,15 +23,16 @@ __device__ __forceinline__ T warp_sum(T v)
 // a strided share of the atom's support; the block reduces them in a fixed order.
 // C layout: ILV = false: C[(J * 4 + l) * ncols + c]; ILV = true: C[(J * ncols + c) * 4 + l]
 // (the four channels of one atom and column contiguous, one 16-byte load in the scatter).
+// project_block: atom J (support entries b .. e-1), columns c0 .. c0+CB-1; ends with a CTA
+// barrier so the caller may reuse the shared memory.
 template <typename T, typename TC, int CB, int NT, bool ILV>
-__global__ void __launch_bounds__(NT)
-k_project(const T *__restrict__ Y, long ld, int ncols, const int *__restrict__ atom_ptr,
-          const int *__restrict__ idx, const TC *__restrict__ chi, TC *__restrict__ C, TC alpha)
+__device__ __forceinline__ void project_block(const T *__restrict__ Y, long ld, int ncols, int J,
+                                              int b, int e, int c0,
+                                              const int *__restrict__ idx,
+                                              const TC *__restrict__ chi, TC *__restrict__ C,
+                                              TC alpha)
 {
     __shared__ TC red[NT / 32][4 * CB];
-    const int J = blockIdx.x;
-    const int c0 = blockIdx.y * CB;
-    const int b = atom_ptr[J], e = atom_ptr[J + 1];
     TC acc[4][CB];
 #pragma unroll
     for (int l = 0; l < 4; ++l)
@@ -95,6 +96,39 @@ k_project(const T *__restrict__ Y, long ld, int ncols, const int *__restrict__ a
             C[o] = alpha * v;
         }
     }
+    __syncthreads();
+}
+
+template <typename T, typename TC, int CB, int NT, bool ILV>
+__global__ void __launch_bounds__(NT)
+k_project(const T *__restrict__ Y, long ld, int ncols, const int *__restrict__ atom_ptr,
+          const int *__restrict__ idx, const TC *__restrict__ chi, TC *__restrict__ C, TC alpha)
+{
+    const int J = blockIdx.x;
+    project_block<T, TC, CB, NT, ILV>(Y, ld, ncols, J, atom_ptr[J], atom_ptr[J + 1],
+                                      blockIdx.y * CB, idx, chi, C, alpha);
+}
+
+// Work-list form for a batch of clusters (items: cluster, atom, first column).
+__global__ void __launch_bounds__(256, 2)
+k_batch_project(const BatchItem *__restrict__ items, int nitems, const BatchNonlocal *cs)
+{
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        const BatchNonlocal &P = cs[w.cluster];
+        project_block<float, float, kBatchCols, 256, true>(
+            P.Y, P.ld, P.ncols, w.a, P.atom_ptr[w.a], P.atom_ptr[w.a + 1], w.col, P.idx,
+            P.chi_f, P.C, P.alpha);
+    }
+}
+
+cudaError_t batch_project(const BatchItem *items, int nitems, const BatchNonlocal *cs, int grid,
+                          cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    k_batch_project<<<grid, 256, 0, st>>>(items, nitems, cs);
+    note_launch();
+    return cudaGetLastError();
 }
 
 template <typename T, typename TC, bool ILV>
@@ -290,16 +324,14 @@ __device__ __forceinline__ void scatter_node_f32(float *o, long ld, int c0, int 
         if (c < nc) oc[(long)c * ld] = x[c] + v[c];
 }
 
-__global__ void __launch_bounds__(kScatNodes)
-k_scatter_f32(float *out, long ld, int ncols, long nuniq, const int *__restrict__ uniq_node,
-              const int *__restrict__ uniq_ptr, const int *__restrict__ nl_atom,
-              const float4 *__restrict__ g4, const float4 *__restrict__ Cs4)
+// Covered node u (entries q0 .. q1-1), columns c0 .. c0+nc-1.
+__device__ __forceinline__ void scatter_f32_node(float *out, long ld, int ncols, long node, int q0,
+                                                 int q1, int c0, int nc,
+                                                 const int *__restrict__ nl_atom,
+                                                 const float4 *__restrict__ g4,
+                                                 const float4 *__restrict__ Cs4)
 {
-    const long u = (long)blockIdx.x * kScatNodes + threadIdx.x;
-    if (u >= nuniq) return;
-    const int c0 = blockIdx.y * kScatCols, nc = min(ncols - c0, kScatCols);
-    float *o = out + uniq_node[u];
-    const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
+    float *o = out + node;
     switch (q1 - q0) {
     case 1: scatter_node_f32<1>(o, ld, c0, nc, q0, ncols, nl_atom, g4, Cs4); return;
     case 2: scatter_node_f32<2>(o, ld, c0, nc, q0, ncols, nl_atom, g4, Cs4); return;
@@ -319,6 +351,45 @@ k_scatter_f32(float *out, long ld, int ncols, long nuniq, const int *__restrict_
         float *oc = o + (long)c * ld;
         *oc = *oc + v;
     }
+}
+
+__global__ void __launch_bounds__(kScatNodes)
+k_scatter_f32(float *out, long ld, int ncols, long nuniq, const int *__restrict__ uniq_node,
+              const int *__restrict__ uniq_ptr, const int *__restrict__ nl_atom,
+              const float4 *__restrict__ g4, const float4 *__restrict__ Cs4)
+{
+    const long u = (long)blockIdx.x * kScatNodes + threadIdx.x;
+    if (u >= nuniq) return;
+    const int c0 = blockIdx.y * kScatCols, nc = min(ncols - c0, kScatCols);
+    scatter_f32_node(out, ld, ncols, uniq_node[u], uniq_ptr[u], uniq_ptr[u + 1], c0, nc, nl_atom,
+                     g4, Cs4);
+}
+
+// Work-list form for a batch of clusters (items: cluster, node chunk, first column).
+__global__ void __launch_bounds__(kScatNodes)
+k_batch_scatter(const BatchItem *__restrict__ items, int nitems, const BatchNonlocal *cs)
+{
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        const BatchNonlocal &P = cs[w.cluster];
+        const long u = (long)w.a * kBatchNodes + threadIdx.x;
+        if (u < P.nuniq) {
+            const int nc = min(P.ncols - w.col, kScatCols);
+            scatter_f32_node(P.out, P.ld, P.ncols, P.uniq_node[u], P.uniq_ptr[u],
+                             P.uniq_ptr[u + 1], w.col, nc, P.nl_atom,
+                             reinterpret_cast<const float4 *>(P.nl_gf),
+                             reinterpret_cast<const float4 *>(P.C));
+        }
+    }
+}
+
+cudaError_t batch_scatter(const BatchItem *items, int nitems, const BatchNonlocal *cs, int grid,
+                          cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    k_batch_scatter<<<grid, kScatNodes, 0, st>>>(items, nitems, cs);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t scatter_f32(const DevHam &H, const float *Cs, float *out, int ncols, long ld,

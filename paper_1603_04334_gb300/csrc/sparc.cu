@@ -360,8 +360,7 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
     } else {
         // mixed-precision form: both contractions on the tensor cores (gram_tc.cu)
         TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, gram_tc_workspace(nd, ns, false, true)));
-        { PHASE(SPARC_PHASE_GRAM); CK((gram_tc<float, float>((const float *)Yf, ld, (const float *)Yf, ld, nd, ns, d.M, ctx->tcws, ctx->tcws_bytes, true, ctx->H.err, ctx->st))); }
-        { PHASE(SPARC_PHASE_GRAM); CK((gram_tc<float, double>((const float *)Yf, ld, HX, ld, nd, ns, d.Hs, ctx->tcws, ctx->tcws_bytes, true, ctx->H.err, ctx->st))); }
+        { PHASE(SPARC_PHASE_GRAM); CK((gram_tc_pair<float, double>((const float *)Yf, ld, HX, ld, nd, ns, d.M, d.Hs, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st))); }
     }
     { PHASE(SPARC_PHASE_DENSE); CK(dense_rr(d.M, d.Hs, ns, d.ritz, d.Cf, d.work, ctx->flags, ctx->st)); }
     CK(cudaMemcpyAsync(ctx->pin_i, ctx->flags, sizeof(int) * 16, cudaMemcpyDeviceToHost, ctx->st));
@@ -876,6 +875,20 @@ sparc_status sparc_launch_count(long long *count)
     *count = g_launches.load(std::memory_order_relaxed);
     return SPARC_OK;
 }
+
+}  // extern "C"
+
+namespace sparc {
+// accessors for the batch layer (batch.cu)
+const DevHam *ctx_ham(const sparc_ctx *ctx) { return &ctx->H; }
+cudaStream_t ctx_stream(const sparc_ctx *ctx) { return ctx->st; }
+float *ctx_coef_buffer(sparc_ctx *ctx, int ncols)
+{
+    return ensure_C(ctx, ncols) == SPARC_OK ? (float *)ctx->C : nullptr;
+}
+}  // namespace sparc
+
+extern "C" {
 
 sparc_status sparc_device_bytes(const sparc_ctx *ctx, size_t *peak_bytes)
 {

@@ -40,25 +40,22 @@ static StepCoef<TC> cast_coef(const StepCoef<double> &d)
     return c;
 }
 
+// One tile: nodes (i0 .. i0+BX-1, j0 .. j0+BY-1, k0 .. k1-1) of one column (Yc, Pc, Oc
+// point at the column). Ends with a CTA barrier, so the caller may reuse the shared
+// memory for its next tile.
 template <typename T, typename TO, typename TC, int BX, int BY>
-__global__ void __launch_bounds__(BX *BY)
-k_stencil(const T *__restrict__ Y, const TO *Yprev, TO *out, const TC *__restrict__ V,
-          int n0, int n1, int n2, long ld, int nzc, int zchunk, StepCoef<TC> cf)
+__device__ __forceinline__ void stencil_tile(const T *__restrict__ Yc, const TO *Pc, TO *Oc,
+                                             const TC *__restrict__ V, int n0, int n1, int n2,
+                                             int i0, int j0, int k0, int k1,
+                                             const StepCoef<TC> &cf)
 {
     constexpr int R = kRadius;
     // plane k is read from s[b] while plane k+1 is staged into s[b ^ 1] (one barrier per
     // plane; the global loads of plane k+1 are in flight during the compute of plane k)
     __shared__ TC s[2][BY + 2 * R][BX + 2 * R];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
     const int i = i0 + tx, j = j0 + ty;
-    const int col = blockIdx.z / nzc;
-    const int k0 = (blockIdx.z % nzc) * zchunk;
-    const int k1 = min(n2, k0 + zchunk);
     const long plane = (long)n0 * n1;
-    const T *Yc = Y + (long)col * ld;
-    const TO *Pc = Yprev ? Yprev + (long)col * ld : nullptr;
-    TO *Oc = out + (long)col * ld;
     const bool act = (i < n0) && (j < n1);
     const long pij = (long)i + (long)n0 * j;
     const bool hx = tx < R, hy = ty < R;
@@ -140,6 +137,36 @@ k_stencil(const T *__restrict__ Y, const TO *Yprev, TO *out, const TC *__restric
     }
 }
 
+template <typename T, typename TO, typename TC, int BX, int BY>
+__global__ void __launch_bounds__(BX *BY)
+k_stencil(const T *Y, const TO *Yprev, TO *out, const TC *__restrict__ V, int n0, int n1, int n2,
+          long ld, int nzc, int zchunk, StepCoef<TC> cf)
+{
+    const int col = blockIdx.z / nzc;
+    const int k0 = (blockIdx.z % nzc) * zchunk;
+    const int k1 = min(n2, k0 + zchunk);
+    stencil_tile<T, TO, TC, BX, BY>(Y + (long)col * ld, Yprev ? Yprev + (long)col * ld : nullptr,
+                                    out + (long)col * ld, V, n0, n1, n2, blockIdx.x * BX,
+                                    blockIdx.y * BY, k0, k1, cf);
+}
+
+// Work-list form for a batch of clusters: each CTA walks the items (cluster, column, tile,
+// z range) with a grid stride; a cluster's pointers, sizes and step coefficients come from
+// its BatchStencil entry.
+template <int BX, int BY>
+__global__ void __launch_bounds__(BX *BY)
+k_batch_stencil(const BatchItem *__restrict__ items, int nitems, const BatchStencil *cs)
+{
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        const BatchStencil &C = cs[w.cluster];
+        const long off = (long)w.col * C.ld;
+        stencil_tile<float, float, float, BX, BY>(C.Y + off, C.Yprev ? C.Yprev + off : nullptr,
+                                                  C.out + off, C.V, C.n0, C.n1, C.n2, w.a * BX,
+                                                  w.b * BY, w.k0, w.k1, C.cf);
+    }
+}
+
 // Picks the number of z-chunks so that small problems still fill the 152 SMs.
 void stencil_z_split(int n2, long tiles, int ncols, int &nzc, int &zchunk)
 {
@@ -167,6 +194,32 @@ static cudaError_t launch(const DevHam &H, const T *Y, const TO *Yprev, TO *out,
                                                          ld, nzc, zchunk, cast_coef<TC>(cd));
     note_launch();
     return cudaGetLastError();
+}
+
+int batch_stencil_shapes() { return 3; }
+void batch_stencil_tile(int shape, int &bx, int &by)
+{
+    bx = shape == 2 ? 64 : 32;
+    by = shape == 1 ? 16 : 8;
+}
+
+cudaError_t batch_stencil(int shape, const BatchItem *items, int nitems, const BatchStencil *cs,
+                          int grid, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    switch (shape) {
+    case 0: k_batch_stencil<32, 8><<<grid, dim3(32, 8), 0, st>>>(items, nitems, cs); break;
+    case 1: k_batch_stencil<32, 16><<<grid, dim3(32, 16), 0, st>>>(items, nitems, cs); break;
+    case 2: k_batch_stencil<64, 8><<<grid, dim3(64, 8), 0, st>>>(items, nitems, cs); break;
+    default: return cudaErrorInvalidValue;
+    }
+    note_launch();
+    return cudaGetLastError();
+}
+
+StepCoef<float> coef_f32(const DevHam &H, double alpha, double shift, double beta)
+{
+    return cast_coef<float>(make_coef(H, alpha, shift, beta));
 }
 
 cudaError_t stencil_f32(const DevHam &H, const float *Y, const float *Yprev, float *out,

@@ -186,6 +186,162 @@ k_stencil_f32_tma(const __grid_constant__ CUtensorMap tmY, const __grid_constant
     }
 }
 
+// Work-list form for a batch of clusters: a persistent CTA walks its items (cluster,
+// column, 32 x 16 tile, z range) in order, and its ring runs on across item boundaries: the
+// planes of all its items form one sequence (item i contributes (k1 - k0) + 12 planes),
+// thread 0 issues that sequence kStages planes ahead of the planes released, and the
+// consumers take the planes in the same order. Each cluster's tensor maps (Y_j with halo,
+// Y_{j-1} tile) live in device memory, its sizes, pointers and coefficients in its
+// BatchTma entry. Same per-point arithmetic as k_stencil_f32_tma.
+__global__ void __launch_bounds__(kTX *kTY)
+k_batch_stencil_tma(const BatchItem *__restrict__ items, int nitems, const BatchTma *cs, int *err)
+{
+    extern __shared__ __align__(128) float sm[];
+    __shared__ __align__(8) uint64_t full[kStages];
+    __shared__ int timed_out;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kTX + tx;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+        mbar_fence_init();
+        timed_out = 0;
+    }
+    __syncthreads();
+    // producer state (thread 0): next plane to hand to the TMA unit
+    int p_it = blockIdx.x, p_t = 0;
+    long issued = 0;
+    auto issue_upto = [&](long limit) {
+        while (issued < limit && p_it < nitems) {
+            const BatchItem w = items[p_it];
+            const BatchTma &C = cs[w.cluster];
+            const int T = (w.k1 - w.k0) + 2 * kR;
+            const int s = (int)(issued % kStages);
+            const bool p = C.mP != nullptr && p_t >= 2 * kR;
+            float *st = sm + (long)s * kStageFloats;
+            const int i0 = w.a * kBX, j0 = w.b * kTY;
+            mbar_arrive_expect_tx(&full[s], kPlaneBytes + (p ? kTileBytes : 0));
+            tma_load_4d(st, (const CUtensorMap *)C.mY, &full[s], i0 - 8, j0 - kR,
+                        w.k0 - kR + p_t, w.col);
+            if (p)
+                tma_load_4d(st + kH * kW, (const CUtensorMap *)C.mP, &full[s], i0, j0,
+                            w.k0 - 2 * kR + p_t, w.col);
+            ++issued;
+            if (++p_t == T) {
+                p_t = 0;
+                p_it += gridDim.x;
+            }
+        }
+    };
+    auto wait = [&](long g) -> bool {
+        return mbar_wait(&full[g % kStages], (unsigned)((g / kStages) & 1), kWaitLimit);
+    };
+    if (tid == 0) issue_upto(kStages);
+    long g0 = 0;  // sequence index of the current item's first plane
+    for (int it = blockIdx.x; it < nitems && !timed_out; it += gridDim.x) {
+        const BatchItem w = items[it];
+        const BatchTma &C = cs[w.cluster];
+        const int n0 = C.n0, n1 = C.n1;
+        const int T = (w.k1 - w.k0) + 2 * kR;
+        const int i0 = w.a * kBX, j0 = w.b * kTY;
+        const int i = i0 + 4 * tx, j = j0 + ty;
+        const bool act = (i < n0) && (j < n1);
+        const long plane = (long)n0 * n1;
+        const long pij = (long)i + (long)n0 * j;
+        float *Oc = C.out + (long)w.col * C.ld;
+        const float *V = C.V;
+        const StepCoef<float> cf = C.cf;
+        const bool hasP = C.mP != nullptr;
+        auto center = [&](long g) -> float4 {
+            return *reinterpret_cast<const float4 *>(sm + (long)(g % kStages) * kStageFloats +
+                                                     (kR + ty) * kW + 8 + 4 * tx);
+        };
+        bool ok = true;
+        float4 q[2 * kR + 1];
+        for (int t = 0; t < kR; ++t) {
+            ok = ok && wait(g0 + t);
+            q[t] = center(g0 + t);
+        }
+        if (!ok) timed_out = 1;
+        __syncthreads();
+        if (tid == 0 && !timed_out) issue_upto(g0 + kR + kStages);
+        for (int t = kR; t < 2 * kR; ++t) {
+            ok = ok && wait(g0 + t);
+            q[t] = center(g0 + t);
+        }
+        if (!ok) timed_out = 1;
+        __syncthreads();
+        float4 vv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act) vv = *reinterpret_cast<const float4 *>(V + pij + (long)w.k0 * plane);
+        for (int tc = kR; tc < T - kR && !timed_out; ++tc) {
+            const int k = w.k0 - kR + tc;
+            const long p = pij + (long)k * plane;
+            float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (act && k + 1 < w.k1) vn = *reinterpret_cast<const float4 *>(V + p + plane);
+            if (!wait(g0 + tc + kR)) timed_out = 1;
+            q[2 * kR] = center(g0 + tc + kR);
+            const float *pl = sm + (long)((g0 + tc) % kStages) * kStageFloats;
+            const float *row = pl + (kR + ty) * kW + 4 * tx;
+            float f[20];
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                const float4 v = *reinterpret_cast<const float4 *>(row + 4 * m);
+                f[4 * m] = v.x;
+                f[4 * m + 1] = v.y;
+                f[4 * m + 2] = v.z;
+                f[4 * m + 3] = v.w;
+            }
+            float acc[4];
+            const float *c4 = &q[kR].x;
+            const float *v4 = &vv.x;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = (cf.c0 + cf.alpha * v4[u]) * c4[u];
+#pragma unroll
+            for (int r = 1; r <= kR; ++r) {
+                const float4 yp = *reinterpret_cast<const float4 *>(row + r * kW + 8);
+                const float4 ym = *reinterpret_cast<const float4 *>(row - r * kW + 8);
+                const float *a = &yp.x, *b = &ym.x, *zp = &q[kR + r].x, *zm = &q[kR - r].x;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float t = (f[8 + u + r] + f[8 + u - r]) + (a[u] + b[u]) + (zp[u] + zm[u]);
+                    acc[u] += cf.w[r] * t;
+                }
+            }
+            if (act) {
+                float4 o = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                if (hasP) {
+                    const float4 pv = *reinterpret_cast<const float4 *>(
+                        sm + (long)((g0 + tc + kR) % kStages) * kStageFloats + kH * kW +
+                        ty * kBX + 4 * tx);
+                    o.x -= cf.beta * pv.x;
+                    o.y -= cf.beta * pv.y;
+                    o.z -= cf.beta * pv.z;
+                    o.w -= cf.beta * pv.w;
+                }
+                *reinterpret_cast<float4 *>(Oc + p) = o;
+            }
+            vv = vn;
+#pragma unroll
+            for (int t = 0; t < 2 * kR; ++t) q[t] = q[t + 1];
+            __syncthreads();  // plane tc's stage is free
+            if (tid == 0 && !timed_out) issue_upto(g0 + tc + 1 + kStages);
+        }
+        g0 += T;
+        __syncthreads();  // the item's last planes (z halo) are free
+        if (tid == 0 && !timed_out) issue_upto(g0 + kStages);
+    }
+    if (timed_out) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            for (int s = 0; s < kStages; ++s) {
+                long last = -1;
+                for (long g = s; g < issued; g += kStages) last = g;
+                if (last >= 0) mbar_wait(&full[s], (unsigned)((last / kStages) & 1), kWaitLimit);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 static cudaError_t get_encoder()
@@ -199,6 +355,53 @@ static cudaError_t get_encoder()
     if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     return cudaSuccess;
+}
+
+// The two tensor maps of a block: with the halo box (the Y_j loads) and with the tile box
+// (the Y_{j-1} loads); maps[0], maps[1].
+cudaError_t encode_f32_maps(const DevHam &H, const float *base, int ncols, long ld, void *maps)
+{
+    cudaError_t e = get_encoder();
+    if (e != cudaSuccess) return e;
+    CUtensorMap *m = reinterpret_cast<CUtensorMap *>(maps);
+    cuuint64_t dims[4] = {(cuuint64_t)H.n0, (cuuint64_t)H.n1, (cuuint64_t)H.n2, (cuuint64_t)ncols};
+    cuuint64_t strides[3] = {(cuuint64_t)H.n0 * 4, (cuuint64_t)H.n0 * H.n1 * 4,
+                             (cuuint64_t)ld * 4};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    cuuint32_t boxY[4] = {(cuuint32_t)kW, (cuuint32_t)kH, 1, 1};
+    cuuint32_t boxP[4] = {(cuuint32_t)kBX, (cuuint32_t)kTY, 1, 1};
+    if (g_encode(&m[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)base, dims, strides, boxY,
+                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        g_encode(&m[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)base, dims, strides, boxP,
+                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
+void batch_tma_tile(int &bx, int &by)
+{
+    bx = kBX;
+    by = kTY;
+}
+
+cudaError_t batch_stencil_tma(const BatchItem *items, int nitems, const BatchTma *cs, int grid,
+                              int *err, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    static bool attr_set = false;
+    const int smem = kStages * kStageFloats * 4;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_batch_stencil_tma,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_batch_stencil_tma<<<grid, dim3(kTX, kTY), smem, st>>>(items, nitems, cs, err);
+    note_launch();
+    return cudaGetLastError();
 }
 
 bool stencil_tma_ok(const DevHam &H, const void *Y, const void *Yprev, const void *out, long ld)

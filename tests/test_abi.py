@@ -11,7 +11,7 @@ import subprocess
 import pytest
 
 from paper_1603_04334_gb300 import build as pkg_build
-from paper_1603_04334_gb300 import serve, sparc
+from paper_1603_04334_gb300 import batching, serve, sparc
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
@@ -48,7 +48,7 @@ def test_library_exports_every_declared_symbol(lib_path):
 
 
 def test_binding_names_match_header():
-    assert sorted(sparc.EXPORTS + serve.EXPORTS) == header_symbols()
+    assert sorted(sparc.EXPORTS + serve.EXPORTS + batching.EXPORTS) == header_symbols()
 
 
 def test_library_is_built_for_sm103a(lib_path):
