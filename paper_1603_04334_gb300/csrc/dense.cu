@@ -28,12 +28,14 @@ constexpr int NT = 1024;
 constexpr int kMaxSweeps = 60;
 constexpr double kEps = 2.220446049250313e-16;
 
-struct Pairs {
+template <typename T>
+struct PairsT {
     int p[kMaxDense / 2];
     int q[kMaxDense / 2];
-    double c[kMaxDense / 2];
-    double s[kMaxDense / 2];
+    T c[kMaxDense / 2];
+    T s[kMaxDense / 2];
 };
+using Pairs = PairsT<double>;
 
 __device__ void pair_of(int r, int k, int m, int &p, int &q)
 {
@@ -65,37 +67,40 @@ __device__ double block_sum(double v, double *red)
     return s;
 }
 
-// Cyclic Jacobi on A (n x n, column-major, symmetric); V accumulates the rotations.
-// Returns (to all threads) the number of sweeps used, or -1 if it did not converge.
-__device__ int jacobi(double *A, double *V, int n, Pairs &P, int *sh_flag)
+// Cyclic Jacobi on A (n x n, column-major, symmetric) in the arithmetic of T; V
+// accumulates the rotations. Returns (to all threads) the number of sweeps used, or -1 if
+// it did not converge within max_sweeps.
+template <typename T>
+__device__ int jacobi(T *A, T *V, int n, PairsT<T> &P, int *sh_flag, double eps,
+                      int max_sweeps = kMaxSweeps)
 {
     __shared__ double red[NT / 32];
     const int tid = threadIdx.x;
     double f = 0.0;
     for (long t = tid; t < (long)n * n; t += NT) {
-        V[t] = ((t % n) == (t / n)) ? 1.0 : 0.0;
-        f += A[t] * A[t];
+        V[t] = ((t % n) == (t / n)) ? (T)1 : (T)0;
+        f += (double)A[t] * (double)A[t];
     }
-    const double thr = 4.0 * kEps * sqrt(block_sum(f, red));
+    const T thr = (T)(4.0 * eps * sqrt(block_sum(f, red)));
     __syncthreads();
     if (n == 1) return 0;
     const int m = (n % 2 == 0) ? n : n + 1;
     const int half = m / 2;
-    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (tid == 0) *sh_flag = 0;
         __syncthreads();
         for (int r = 0; r < m - 1; ++r) {
             for (int k = tid; k < half; k += NT) {
                 int p, q;
                 pair_of(r, k, m, p, q);
-                double c = 1.0, s = 0.0;
+                T c = (T)1, s = (T)0;
                 if (q < n) {
-                    const double apq = A[p + (long)q * n];
-                    const double app = A[p + (long)p * n], aqq = A[q + (long)q * n];
+                    const T apq = A[p + (long)q * n];
+                    const T app = A[p + (long)p * n], aqq = A[q + (long)q * n];
                     if (fabs(apq) > thr) {
-                        const double tau = (aqq - app) / (2.0 * apq);
-                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + t * t);
+                        const T tau = (aqq - app) / ((T)2 * apq);
+                        const T t = (tau >= (T)0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
+                        c = (T)1 / sqrt((T)1 + t * t);
                         s = t * c;
                         *sh_flag = 1;
                     }
@@ -109,11 +114,11 @@ __device__ int jacobi(double *A, double *V, int n, Pairs &P, int *sh_flag)
             // rows: A <- J^T A
             for (long t = tid; t < (long)half * n; t += NT) {
                 const int k = (int)(t / n), col = (int)(t % n);
-                const double s = P.s[k];
-                if (s == 0.0) continue;
-                const double c = P.c[k];
+                const T s = P.s[k];
+                if (s == (T)0) continue;
+                const T c = P.c[k];
                 const int p = P.p[k], q = P.q[k];
-                const double ap = A[p + (long)col * n], aq = A[q + (long)col * n];
+                const T ap = A[p + (long)col * n], aq = A[q + (long)col * n];
                 A[p + (long)col * n] = c * ap - s * aq;
                 A[q + (long)col * n] = s * ap + c * aq;
             }
@@ -121,14 +126,14 @@ __device__ int jacobi(double *A, double *V, int n, Pairs &P, int *sh_flag)
             // columns: A <- A J, V <- V J
             for (long t = tid; t < (long)half * n; t += NT) {
                 const int k = (int)(t / n), row = (int)(t % n);
-                const double s = P.s[k];
-                if (s == 0.0) continue;
-                const double c = P.c[k];
+                const T s = P.s[k];
+                if (s == (T)0) continue;
+                const T c = P.c[k];
                 const int p = P.p[k], q = P.q[k];
-                const double ap = A[row + (long)p * n], aq = A[row + (long)q * n];
+                const T ap = A[row + (long)p * n], aq = A[row + (long)q * n];
                 A[row + (long)p * n] = c * ap - s * aq;
                 A[row + (long)q * n] = s * ap + c * aq;
-                const double vp = V[row + (long)p * n], vq = V[row + (long)q * n];
+                const T vp = V[row + (long)p * n], vq = V[row + (long)q * n];
                 V[row + (long)p * n] = c * vp - s * vq;
                 V[row + (long)q * n] = s * vp + c * vq;
             }
@@ -176,7 +181,7 @@ __device__ void sort_and_sign(const double *dg, long ds, const double *V, int n,
 }
 }  // namespace
 
-long dense_work_elems(int ns) { return 5L * ns * ns + 8L * ns + 64; }
+long dense_work_elems(int ns) { return 11L * ns * ns + 8L * ns + 64; }
 
 // ---- multi-SM reduction of the generalized problem ----------------------------------
 // Cholesky M_s = L L^T on a cooperative grid (right-looking, one bounded grid barrier per
@@ -299,6 +304,40 @@ k_dense_sort(int n, const double *diag, const double *V, double *ritz, double *Q
     sort_and_sign(diag, 1, V, n, ritz, Q, rank);
 }
 
+// ---- mixed-precision eigensolve of A = U^T H_s U (Ns > kMixedFrom) ----------------------
+// Cyclic Jacobi in FP32 first (64x the FP64 rate on GB300), its eigenvectors P made
+// orthogonal to FP64 accuracy by two Newton-Schulz steps P <- P (3 I - P^T P) / 2, then the
+// FP64 Jacobi on A' = P^T A P, which is already diagonal to the FP32 level and converges in
+// a few sweeps (quadratically); the eigenvectors of A are P V'. The result is the FP64
+// eigendecomposition; the FP32 phase only shortens the FP64 phase.
+constexpr int kMixedFrom = 256;     // Ns above this: FP32 phase first
+constexpr int kMaxSweeps32 = 20;
+
+__global__ void k_f64_to_f32(const double *a, float *b, long n)
+{
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        b[t] = (float)a[t];
+}
+__global__ void k_f32_to_f64(const float *a, double *b, long n)
+{
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        b[t] = (double)a[t];
+}
+// A grid barrier of the FP32 phase that gave up makes the whole eigensolve report a
+// timeout (its eigenvectors would be partial); the FP64 phase resets the barrier.
+__global__ void k_keep_barrier_error(const GridBarrier *bar, int *status)
+{
+    if (threadIdx.x == 0 && bar->err && *status == 0) *status = 4;
+}
+
+// C <- 1.5 I - 0.5 C (the Newton-Schulz coefficient matrix from C = P^T P)
+__global__ void k_newton_schulz_coef(double *C, int n)
+{
+    const long nn = (long)n * n;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (long)gridDim.x * blockDim.x)
+        C[t] = ((t % n) == (t / n) ? 1.5 : 0.0) - 0.5 * C[t];
+}
+
 static int g_chol_blocks = 0;  // co-resident CTAs of k_chol_grid (queried once)
 
 cudaError_t dense_rr(double *M, double *Hs, int ns, double *ritz, double *Cf, double *work,
@@ -307,12 +346,18 @@ cudaError_t dense_rr(double *M, double *Hs, int ns, double *ritz, double *Cf, do
     if (ns <= 0 || ns > kMaxDense) return cudaErrorInvalidValue;
     const long nn = (long)ns * ns;
     double *R0 = work;            // L row-major, then H_s U, then Jacobi's second copy, then Q
-    double *A = work + nn;        // U^T H_s U, Jacobi's working copy
-    double *V = work + 2 * nn;    // Jacobi eigenvectors
+    double *A = work + nn;        // U^T H_s U, then A' = P^T A P (Jacobi's working copy)
+    double *V = work + 2 * nn;    // FP64 Jacobi eigenvectors of A'
     double *U = work + 3 * nn;    // L^-T
     double *part = work + 4 * nn; // Gram partials (one row slice for ns <= 2048 rows)
-    double *diag = work + 5 * nn, *dinv = diag + ns, *odiag = dinv + ns;
+    double *P = work + 5 * nn;    // FP32-phase eigenvectors, then orthogonalised
+    double *G = work + 6 * nn;    // P^T P / Newton-Schulz coefficients / A P / P V'
+    double *P2 = work + 7 * nn;   // Newton-Schulz ping-pong
+    float *A32 = (float *)(work + 8 * nn), *V32 = A32 + nn;
+    float *A32b = (float *)(work + 9 * nn), *D32 = A32b + nn;
+    double *diag = work + 10 * nn, *dinv = diag + ns, *odiag = dinv + ns;
     GridBarrier *bar = (GridBarrier *)(status + 8);
+    int *status32 = status + 13;  // FP32 phase: running out of sweeps only shortens its help
     cudaError_t e;
     if (g_chol_blocks == 0) {
         int dev = 0, sms = 0, per = 0;
@@ -326,13 +371,13 @@ cudaError_t dense_rr(double *M, double *Hs, int ns, double *ritz, double *Cf, do
     }
     long want = (nn / 2 + CT - 1) / CT;
     if (want < 1) want = 1;
-    int G = (int)(want < g_chol_blocks ? want : g_chol_blocks);
-    if (G > 152) G = 152;
+    int G0 = (int)(want < g_chol_blocks ? want : g_chol_blocks);
+    if (G0 > 152) G0 = 152;
     if ((e = cudaMemsetAsync(status, 0, sizeof(int), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return e;
     {
         void *args[] = {&M, &Hs, &ns, &R0, &dinv, &odiag, &bar, &status};
-        e = cudaLaunchCooperativeKernel((const void *)k_chol_grid, dim3(G), dim3(CT), args, 0, st);
+        e = cudaLaunchCooperativeKernel((const void *)k_chol_grid, dim3(G0), dim3(CT), args, 0, st);
         note_launch();
         if (e != cudaSuccess) return e;
     }
@@ -342,9 +387,49 @@ cudaError_t dense_rr(double *M, double *Hs, int ns, double *ritz, double *Cf, do
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = rotate_f64(Hs, ns, ns, ns, U, R0, ns, st)) != cudaSuccess) return e;  // H_s U
     if ((e = gram_f64(U, ns, R0, ns, ns, ns, A, part, st, true)) != cudaSuccess) return e;
+    if (ns <= kMixedFrom) {
+        // small Ns: the FP64 Jacobi alone is cheaper than the FP32 phase and the extra
+        // products (its rounds are bound by the grid barrier, not by arithmetic)
+        if ((e = jacobi_grid(A, R0, V, diag, ns, bar, status, status + 12, st)) != cudaSuccess)
+            return e;
+        k_dense_sort<<<1, NT, 0, st>>>(ns, diag, V, ritz, R0, status, bar);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        return rotate_f64(U, ns, ns, ns, R0, Cf, ns, st);  // Cf = U Q
+    }
+    // FP32 phase -> P
+    const int cg = (int)((nn + 255) / 256 < 152 * 4 ? (nn + 255) / 256 : 152 * 4);
+    {
+        k_f64_to_f32<<<cg, 256, 0, st>>>(A, A32, nn);
+        note_launch();
+        if ((e = cudaMemsetAsync(status32, 0, sizeof(int), st)) != cudaSuccess) return e;
+        if ((e = jacobi_grid_f32(A32, A32b, V32, D32, ns, bar, status32, status + 14 + 1,
+                                 kMaxSweeps32, st)) != cudaSuccess)
+            return e;
+        k_f32_to_f64<<<cg, 256, 0, st>>>(V32, P, nn);
+        note_launch();
+        k_keep_barrier_error<<<1, 32, 0, st>>>(bar, status);
+        note_launch();
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // two Newton-Schulz steps: P <- P (1.5 I - 0.5 P^T P)
+    double *Pc = P, *Pn = P2;
+    for (int it = 0; it < 2; ++it) {
+        if ((e = gram_f64(Pc, ns, Pc, ns, ns, ns, G, part, st, true)) != cudaSuccess) return e;
+        k_newton_schulz_coef<<<cg, 256, 0, st>>>(G, ns);
+        note_launch();
+        if ((e = rotate_f64(Pc, ns, ns, ns, G, Pn, ns, st)) != cudaSuccess) return e;
+        double *t = Pc;
+        Pc = Pn;
+        Pn = t;
+    }
+    // A' = P^T (A P), then the FP64 Jacobi on A'
+    if ((e = rotate_f64(A, ns, ns, ns, Pc, G, ns, st)) != cudaSuccess) return e;
+    if ((e = gram_f64(Pc, ns, G, ns, ns, ns, A, part, st, true)) != cudaSuccess) return e;
     if ((e = jacobi_grid(A, R0, V, diag, ns, bar, status, status + 12, st)) != cudaSuccess)
         return e;
-    k_dense_sort<<<1, NT, 0, st>>>(ns, diag, V, ritz, R0, status, bar);
+    if ((e = rotate_f64(Pc, ns, ns, ns, V, G, ns, st)) != cudaSuccess) return e;  // P V'
+    k_dense_sort<<<1, NT, 0, st>>>(ns, diag, G, ritz, R0, status, bar);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return rotate_f64(U, ns, ns, ns, R0, Cf, ns, st);  // Cf = U Q
@@ -363,7 +448,7 @@ k_dense_syev(double *A, int nmax, const int *n_dev, double *ev, double *Q, doubl
     __shared__ int flag;
     __shared__ int rank[kMaxDense];
     double *V = work;
-    const int sweeps = jacobi(A, V, n, P, &flag);
+    const int sweeps = jacobi<double>(A, V, n, P, &flag, kEps);
     if (sweeps < 0) {
         if (threadIdx.x == 0) *status = 3;
         return;

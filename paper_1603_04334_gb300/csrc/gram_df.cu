@@ -172,8 +172,9 @@ k_rotate_df(const double *__restrict__ A, long lda, long nd, int ns, const doubl
     __shared__ float2 As[GK][GT + 1];
     __shared__ float2 Qs[GK][GT + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const long r0 = (long)blockIdx.x * GT;
-    const int j0 = blockIdx.y * GT;
+    const int j0 = blockIdx.x * GT;  // column tiles of a row tile run side by side (L2 reuse)
+    for (long rt = blockIdx.y; rt * GT < nd; rt += gridDim.y) {
+    const long r0 = rt * GT;
     float sh[4][4], sl[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -223,15 +224,15 @@ k_rotate_df(const double *__restrict__ A, long lda, long nd, int ns, const doubl
             const int c = j0 + tx + 16 * y;
             if (row < nd && c < ns) out[row + (long)c * ldo] = (double)sh[x][y] + (double)sl[x][y];
         }
+    }
 }
 
 cudaError_t rotate_f64_df(const double *A, long lda, long nd, int ns, const double *Q, double *out,
                           long ldo, cudaStream_t st)
 {
     if (ns <= 0 || nd <= 0) return cudaSuccess;
-    const long gx = (nd + GT - 1) / GT;
-    if (gx > 2147483647L) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)gx, (ns + GT - 1) / GT);
+    const long gy = (nd + GT - 1) / GT;
+    dim3 grid((ns + GT - 1) / GT, (unsigned)(gy < 65535 ? gy : 65535));
     k_rotate_df<<<grid, 256, 0, st>>>(A, lda, nd, ns, Q, out, ldo);
     note_launch();
     return cudaGetLastError();

@@ -47,48 +47,51 @@ __device__ __forceinline__ void pair_of(int r, int k, int m, int &p, int &q)
 // Returns false (to every thread of the CTA) once any CTA has hit the spin limit.
 }  // namespace
 
+// T = double: the eigensolve; T = float: the FP32 pre-solve of the mixed-precision
+// eigensolve (dense.cu), with eps the unit roundoff of T.
+template <typename T>
 __global__ void __launch_bounds__(NT)
-k_jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrier *bar,
-              int *status, int *sweeps_out)
+k_jacobi_grid(T *A0, T *A1, T *V, T *diag, int n, GridBarrier *bar, int *status,
+              int *sweeps_out, double eps, int max_sweeps)
 {
     __shared__ int sp[kMaxDense / 2], sq[kMaxDense / 2];
-    __shared__ double sc[kMaxDense / 2], ss[kMaxDense / 2];
+    __shared__ T sc[kMaxDense / 2], ss[kMaxDense / 2];
     __shared__ double red[NT / 32];
     __shared__ int any_rot;
     if (*((volatile int *)status) != 0) return;  // the reduction step failed
     const unsigned nb = gridDim.x;
     const long nn = (long)n * n;
     const long gtid = (long)blockIdx.x * NT + threadIdx.x, gstride = (long)nb * NT;
-    for (long t = gtid; t < nn; t += gstride) V[t] = ((t % n) == (t / n)) ? 1.0 : 0.0;
+    for (long t = gtid; t < nn; t += gstride) V[t] = ((t % n) == (t / n)) ? (T)1 : (T)0;
     double f = 0.0;
-    for (long t = threadIdx.x; t < nn; t += NT) f += A0[t] * A0[t];
+    for (long t = threadIdx.x; t < nn; t += NT) f += (double)A0[t] * (double)A0[t];
     for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f;
     __syncthreads();
     double fro = 0.0;
     for (int w = 0; w < NT / 32; ++w) fro += red[w];
-    const double thr = 4.0 * kEps * sqrt(fro);
+    const T thr = (T)(4.0 * eps * sqrt(fro));
     if (!grid_barrier(bar, nb)) return;
 
-    double *cur = A0, *nxt = A1;
+    T *cur = A0, *nxt = A1;
     const int m = n + (n & 1), half = m / 2;
     int sweeps = -1;
-    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (threadIdx.x == 0) any_rot = 0;
         __syncthreads();
         for (int r = 0; r < m - 1; ++r) {
             for (int k = threadIdx.x; k < half; k += NT) {
                 int p, q;
                 pair_of(r, k, m, p, q);
-                double c = 1.0, s = 0.0;
+                T c = (T)1, s = (T)0;
                 if (q < n) {
-                    const double apq = __ldcg(cur + p + (long)q * n);
+                    const T apq = __ldcg(cur + p + (long)q * n);
                     if (fabs(apq) > thr) {
-                        const double app = __ldcg(cur + p + (long)p * n);
-                        const double aqq = __ldcg(cur + q + (long)q * n);
-                        const double tau = (aqq - app) / (2.0 * apq);
-                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + t * t);
+                        const T app = __ldcg(cur + p + (long)p * n);
+                        const T aqq = __ldcg(cur + q + (long)q * n);
+                        const T tau = (aqq - app) / ((T)2 * apq);
+                        const T t = (tau >= (T)0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
+                        c = (T)1 / sqrt((T)1 + t * t);
                         s = t * c;
                         any_rot = 1;
                     }
@@ -104,13 +107,13 @@ k_jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrie
                 const int k1 = (int)(b % half), k2 = (int)(b / half);
                 const int p1 = sp[k1], q1 = sq[k1], p2 = sp[k2], q2 = sq[k2];
                 const bool v1 = q1 < n, v2 = q2 < n;
-                const double c1 = sc[k1], s1 = ss[k1], c2 = sc[k2], s2 = ss[k2];
-                const double app = __ldcg(cur + p1 + (long)p2 * n);
-                const double apq = v2 ? __ldcg(cur + p1 + (long)q2 * n) : 0.0;
-                const double aqp = v1 ? __ldcg(cur + q1 + (long)p2 * n) : 0.0;
-                const double aqq = (v1 && v2) ? __ldcg(cur + q1 + (long)q2 * n) : 0.0;
-                const double bpp = c1 * app - s1 * aqp, bpq = c1 * apq - s1 * aqq;
-                const double bqp = s1 * app + c1 * aqp, bqq = s1 * apq + c1 * aqq;
+                const T c1 = sc[k1], s1 = ss[k1], c2 = sc[k2], s2 = ss[k2];
+                const T app = __ldcg(cur + p1 + (long)p2 * n);
+                const T apq = v2 ? __ldcg(cur + p1 + (long)q2 * n) : (T)0;
+                const T aqp = v1 ? __ldcg(cur + q1 + (long)p2 * n) : (T)0;
+                const T aqq = (v1 && v2) ? __ldcg(cur + q1 + (long)q2 * n) : (T)0;
+                const T bpp = c1 * app - s1 * aqp, bpq = c1 * apq - s1 * aqq;
+                const T bqp = s1 * app + c1 * aqp, bqq = s1 * apq + c1 * aqq;
                 nxt[p1 + (long)p2 * n] = c2 * bpp - s2 * bpq;
                 if (v2) nxt[p1 + (long)q2 * n] = s2 * bpp + c2 * bpq;
                 if (v1) nxt[q1 + (long)p2 * n] = c2 * bqp - s2 * bqq;
@@ -119,16 +122,16 @@ k_jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrie
             // V <- V J, columns p, q of each rotated pair
             for (long t = gtid; t < (long)half * n; t += gstride) {
                 const int k = (int)(t / n), row = (int)(t % n);
-                const double s = ss[k];
-                if (s == 0.0) continue;
-                const double c = sc[k];
+                const T s = ss[k];
+                if (s == (T)0) continue;
+                const T c = sc[k];
                 const int p = sp[k], q = sq[k];
-                const double vp = __ldcg(V + row + (long)p * n), vq = __ldcg(V + row + (long)q * n);
+                const T vp = __ldcg(V + row + (long)p * n), vq = __ldcg(V + row + (long)q * n);
                 V[row + (long)p * n] = c * vp - s * vq;
                 V[row + (long)q * n] = s * vp + c * vq;
             }
             if (!grid_barrier(bar, nb)) return;
-            double *t = cur;
+            T *t = cur;
             cur = nxt;
             nxt = t;
         }
@@ -146,33 +149,49 @@ k_jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrie
     }
 }
 
-static int g_coop_blocks = 0;  // co-resident CTAs of k_jacobi_grid (queried once)
-
-cudaError_t jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrier *bar,
-                        int *status, int *sweeps_out, cudaStream_t st)
+template <typename T>
+static cudaError_t jacobi_grid_t(T *A0, T *A1, T *V, T *diag, int n, GridBarrier *bar,
+                                 int *status, int *sweeps_out, double eps, int max_sweeps,
+                                 cudaStream_t st)
 {
+    static int coop_blocks = 0;  // co-resident CTAs of this instance (queried once)
     if (n <= 0 || n > kMaxDense) return cudaErrorInvalidValue;
-    if (g_coop_blocks == 0) {
+    if (coop_blocks == 0) {
         int dev = 0, sms = 0, per = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_jacobi_grid, NT, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_jacobi_grid<T>, NT, 0);
         if (e != cudaSuccess) return e;
-        g_coop_blocks = sms * (per > 0 ? per : 1);
+        coop_blocks = sms * (per > 0 ? per : 1);
     }
     const long half = (n + 1) / 2;
     long want = (half * half + NT - 1) / NT;  // one 2 x 2 block of A per thread
     if (want < 1) want = 1;
-    int G = (int)(want < g_coop_blocks ? want : g_coop_blocks);
+    int G = (int)(want < coop_blocks ? want : coop_blocks);
     if (G > 152) G = 152;
     cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;
-    void *args[] = {&A0, &A1, &V, &diag, &n, &bar, &status, &sweeps_out};
-    e = cudaLaunchCooperativeKernel((const void *)k_jacobi_grid, dim3(G), dim3(NT), args, 0, st);
+    void *args[] = {&A0, &A1, &V, &diag, &n, &bar, &status, &sweeps_out, &eps, &max_sweeps};
+    e = cudaLaunchCooperativeKernel((const void *)k_jacobi_grid<T>, dim3(G), dim3(NT), args, 0,
+                                    st);
     note_launch();
     return e;
+}
+
+cudaError_t jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrier *bar,
+                        int *status, int *sweeps_out, cudaStream_t st)
+{
+    return jacobi_grid_t<double>(A0, A1, V, diag, n, bar, status, sweeps_out, kEps, kMaxSweeps,
+                                 st);
+}
+
+cudaError_t jacobi_grid_f32(float *A0, float *A1, float *V, float *diag, int n, GridBarrier *bar,
+                            int *status, int *sweeps_out, int max_sweeps, cudaStream_t st)
+{
+    return jacobi_grid_t<float>(A0, A1, V, diag, n, bar, status, sweeps_out,
+                                1.1920928955078125e-07, max_sweeps, st);
 }
 
 // Failure-detection self-test: every CTA of a cooperative grid waits at a barrier that

@@ -215,6 +215,10 @@ k_batch_stencil_tma(const BatchItem *__restrict__ items, int nitems, const Batch
             const BatchItem w = items[p_it];
             const BatchTma &C = cs[w.cluster];
             const int T = (w.k1 - w.k0) + 2 * kR;
+            if (p_t == 0) {  // a new item: bring its descriptors close before its loads
+                tma_prefetch_desc((const CUtensorMap *)C.mY);
+                if (C.mP) tma_prefetch_desc((const CUtensorMap *)C.mP);
+            }
             const int s = (int)(issued % kStages);
             const bool p = C.mP != nullptr && p_t >= 2 * kR;
             float *st = sm + (long)s * kStageFloats;

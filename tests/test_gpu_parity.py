@@ -334,6 +334,24 @@ def test_orth_rr_f64_many_columns(c24, ns):
     assert np.max(np.abs(Xg @ Xg.T - np.eye(ns))) <= 1e-12
 
 
+def test_orth_rr_f32_many_columns(c24):
+    # the mixed-precision form at 300 columns: tensor-core Gram, mixed-precision eigensolve,
+    # register-blocked FP32 rotation; Ritz values within the 1e-5 Ha contract of the FP64
+    # oracle on the same (FP32-rounded) block, rotated block orthonormal to FP32 level
+    w, cl, H, ctx = c24
+    X0 = synth.initial_block(10, w.nd, 300)
+    Yf = H.cheb_filter(X0, 2, 7.6, 40.1, -3.3)
+    Yd = to_dev(Yf, torch.float32)
+    Y64 = Yd.double().cpu().numpy()
+    Xo, HXo, lam, res, _ = oracle.orth_rr(Y64, H.apply(Y64))
+    ritz, resid = ctx.orth_rr(Yd)
+    assert np.max(np.abs(ritz - lam)) <= 1e-5
+    assert np.all(np.diff(ritz) >= 0)
+    Xg = Yd.double().cpu().numpy()
+    assert np.max(np.abs(Xg @ Xg.T - np.eye(300))) <= 1e-5
+    assert np.max(np.abs(resid - res)) <= 1e-4
+
+
 def test_orth_rr_not_spd_leaves_block(c24):
     w, cl, H, ctx = c24
     X = synth.initial_block(6, w.nd, 3)
