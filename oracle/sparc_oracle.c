@@ -87,6 +87,8 @@ void orc_laplacian(int n0, int n1, int n2, double h, int no,
 void orc_veff(int n0, int n1, int n2, double h, int natoms, const double *R,
               const double *Z, double rc, double *V)
 {
+    /* every node is computed on its own (same sum order at any thread count) */
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < n2; ++k)
         for (int j = 0; j < n1; ++j)
             for (int i = 0; i < n0; ++i) {

@@ -19,11 +19,13 @@ using namespace sparc;
 
 namespace {
 constexpr int kZSplits[3] = {1, 2, 4};
-// stencil forms: shared-memory tiles 32 x 8, 32 x 16, 64 x 8, and the TMA-fed 32 x 16
-// (form 3, for blocks the TMA path accepts); each with 1, 2 or 4 z ranges per column
-constexpr int kForms = 4, kTmaForm = 3;
+// stencil forms: shared-memory tiles 32 x 8, 32 x 16, 64 x 8; the TMA-fed 32 x 16 on a
+// persistent grid (form 3: one ring per CTA across its items) or with one CTA per item
+// (form 4: the scheduling of the single-cluster launches); forms 3 and 4 for blocks the TMA
+// path accepts. Each with 1, 2 or 4 z ranges per column.
+constexpr int kForms = 5, kTmaForm = 3, kTmaItemForm = 4;
 constexpr int kVariants = kForms * 3;
-constexpr int kDefaultVariant = kTmaForm * 3;  // TMA, whole z range
+constexpr int kDefaultVariant = kTmaItemForm * 3;  // TMA, one CTA per item, whole z range
 
 // Persistent grids: enough resident CTAs to fill the 152 SMs several times.
 constexpr int kGridStencil = 152 * 8;
@@ -98,7 +100,7 @@ void free_tables(sparc_batch *b)
 sparc_status build_items(sparc_batch *b, const int *ncols)
 {
     int bx, by;
-    if (b->form == kTmaForm)
+    if (b->form >= kTmaForm)
         batch_tma_tile(bx, by);
     else
         batch_stencil_tile(b->form, bx, by);
@@ -264,8 +266,9 @@ cudaError_t enqueue_steps(sparc_batch *b, float *const *X, float *const *W, cons
         const BatchNonlocal *P = b->d_nl + (size_t)j * n;
         if (b->any_atoms && (e = batch_project(pr_items, b->n_pr, P, kGridProject, b->st)))
             return e;
-        if (b->form == kTmaForm) {
-            e = batch_stencil_tma(st_items, b->n_st, b->d_tm + (size_t)j * n, kGridTma,
+        if (b->form >= kTmaForm) {
+            const int grid = b->form == kTmaItemForm ? b->n_st : kGridTma;
+            e = batch_stencil_tma(st_items, b->n_st, b->d_tm + (size_t)j * n, grid,
                                   ctx_ham(b->ctx[0])->err, b->st);
         } else {
             e = batch_stencil(b->form, st_items, b->n_st, S, kGridStencil, b->st);
@@ -316,8 +319,8 @@ sparc_status run_filter(sparc_batch *b, float *const *X, float *const *W, const 
             ok = ok && stencil_tma_ok(*ctx_ham(b->ctx[c]), X[c], W[c], W[c], ld[c]) &&
                  stencil_tma_ok(*ctx_ham(b->ctx[c]), W[c], X[c], X[c], ld[c]);
         b->form = b->variant / 3;
-        if (b->form == kTmaForm && !ok) b->form = 1;
-        b->tma = b->form == kTmaForm;
+        if (b->form >= kTmaForm && !ok) b->form = 1;
+        b->tma = b->form >= kTmaForm;
         if (b->tma) {
             const size_t mb = tensor_map_bytes(), need = 4 * mb * n;
             if (need > b->maps_cap) {
