@@ -323,10 +323,12 @@ def run_ours(args, rank, world, local_rank):
         roof["traffic_launch"] = tr["launch"]
         roof["traffic_algorithmic_bytes"] = tr["algorithmic_bytes"]
     if dtype == "f64":
-        # The FP64 step runs in FP32-pair arithmetic on the FP32 pipe; its FP64-equivalent
-        # flop rate is compared with the FP64 pipe's issue limit as context.
+        # The FP64 step runs on the integer and FP32 pipes (exact integer neighbour sums,
+        # FP32-pair scaling); its FP64-equivalent flop rate is compared with the FP64
+        # pipe's issue limit as context.
         fl = alg["flops"] / (alg["ms"] / 1e3) / 1e12 if alg["ms"] > 0 else None
-        roof["kernel"] = "k_stencil_df (fused stencil + V_eff + recurrence, FP32-pair)"
+        roof["kernel"] = ("k_stencil_df (fused stencil + V_eff + recurrence; exact integer "
+                          "neighbour sums, FP32-pair scaling)")
         roof["fp64_equiv_tflops"] = fl
         roof["fp64_pipe_peak_tflops"] = fp64_alu_peak_tflops(sm_max)
     else:

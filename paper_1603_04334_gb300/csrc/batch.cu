@@ -133,6 +133,14 @@ sparc_status build_items(sparc_batch *b, const int *ncols)
     }
     const size_t tot = st.size() + pr.size() + sc.size();
     if (tot > 0x7fffffff) return SPARC_ERR_ARG;
+    if (b->form == kTmaForm) {
+        // the persistent TMA kernel numbers the planes of each CTA's items in 32 bits
+        std::vector<long long> planes(kGridTma, 0);
+        for (size_t i = 0; i < st.size(); ++i)
+            planes[i % kGridTma] += (st[i].k1 - st[i].k0) + 2 * kRadius;
+        for (long long v : planes)
+            if (v >= (1LL << 31)) return SPARC_ERR_ARG;
+    }
     if (tot > b->items_cap) {
         if (b->items) cudaFree(b->items);
         b->items = nullptr;

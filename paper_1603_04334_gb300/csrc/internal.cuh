@@ -21,6 +21,10 @@ struct DevHam {
     int radius = 6;
     double kscale = 1.0;
     double w[kRadius + 1] = {0};  // Laplacian weights w_p (1/h^2 included), zero beyond radius
+    // the same weights as exact integers over one denominator D: 6 h^2 w_0 = wint[0] / D,
+    // h^2 w_p = wint[p] / D (p >= 1); wunit = 1 / (D h^2)
+    int wint[kRadius + 1] = {0};
+    double wunit = 0;
     int *err = nullptr;           // device word set by a kernel whose bounded wait ran out
 
     const double *V = nullptr;   // V_eff, Nd
@@ -66,12 +70,25 @@ StepCoef<double> make_coef(const DevHam &H, double alpha, double shift, double b
 // Yprev may be null (beta ignored) and may alias out (in-place recurrence). Cs: the
 // projection coefficients alpha * chi^T Y (FP32 pairs for FP64 blocks, FP32 for FP32
 // blocks), or null when the Hamiltonian has no atoms.
+// FP64 blocks (stencil_df.cu): the neighbour sums are exact integer sums of the values
+// scaled by a power of two per column, so each column needs a bound of its magnitude:
+// bY[c] (and bP[c] for Yprev) = the largest high word (bits 32..62) of |y| over the
+// column, as written by colmax_f64 or by the launch that produced the block. bOut, if not
+// null, is raised (atomicMax) to the bound of the output's columns.
 cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, double *out,
                         int ncols, long ld, double alpha, double shift, double beta,
+                        const unsigned *bY, const unsigned *bP, unsigned *bOut,
                         cudaStream_t st);
-// out += V_nl part from Cs = alpha chi^T Y (pairs), for FP64 blocks (stencil_df.cu)
+// out += V_nl part from Cs = alpha chi^T Y (pairs), for FP64 blocks (stencil_df.cu); bOut
+// as for stencil_f64 (raised to the bound of the updated values)
 cudaError_t scatter_f64_df(const DevHam &H, const float2 *Cs, double *out, int ncols, long ld,
-                           cudaStream_t st);
+                           unsigned *bOut, cudaStream_t st);
+// b[c] = max(b[c], largest high word of |Y| over column c) for FP64 or FP32 blocks (an FP32
+// value counts as its FP64 widening); b must be zeroed first to get the bound alone.
+cudaError_t colmax_f64(const double *Y, int ncols, long ld, long nd, unsigned *b,
+                       cudaStream_t st);
+cudaError_t colmax_f32(const float *Y, int ncols, long ld, long nd, unsigned *b,
+                       cudaStream_t st);
 // out += V_nl part from Cs = alpha chi^T Y, FP32 blocks (nonlocal.cu)
 cudaError_t scatter_f32(const DevHam &H, const float *Cs, float *out, int ncols, long ld,
                         cudaStream_t st);
@@ -147,7 +164,7 @@ cudaError_t stencil_f32_tma(const DevHam &H, const float *Y, const float *Yprev,
                             cudaStream_t st);
 // FP64 arithmetic on an FP32 block (H applied to FP32 Ritz blocks in FP64).
 cudaError_t stencil_f32in_f64(const DevHam &H, const float *Y, double *out, int ncols,
-                              long ld, cudaStream_t st);
+                              long ld, const unsigned *bY, cudaStream_t st);
 
 // ---- nonlocal.cu ------------------------------------------------------------------
 // C[(J*4+lm)*ncols + c] = alpha * sum_{s in supp(J)} chi_Jlm(s) Y[idx(s) + c*ld]

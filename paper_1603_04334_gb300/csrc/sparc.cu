@@ -9,6 +9,7 @@
 #include "internal.cuh"
 
 #include <atomic>
+#include <cstdint>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -16,6 +17,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 using namespace sparc;
@@ -62,6 +64,8 @@ struct sparc_ctx {
     size_t dev_bytes = 0, dev_peak = 0;  // device bytes allocated (see dmalloc)
     void *dm = nullptr;      size_t dm_bytes = 0;    // M, Hs, Cf, ritz, resid, dense work
     void *lz = nullptr;      size_t lz_bytes = 0;    // Lanczos vectors and scalars
+    void *bnd = nullptr;     size_t bnd_bytes = 0;   // column bounds of the FP64 filter's blocks
+    void *bsc = nullptr;     size_t bsc_bytes = 0;   // column bounds of other FP64 H applications
     int *flags = nullptr;                            // device status words
     double *pin = nullptr;                           // pinned host staging (2*1024+16)
     int *pin_i = nullptr;
@@ -209,18 +213,43 @@ sparc_status ensure_C(sparc_ctx *ctx, int ncols)
     return ensure(ctx, ctx->C, ctx->C_bytes, b);
 }
 
+// Column bounds of an FP64 or FP32 block into the scratch bound buffer (zeroed, then
+// raised by one pass over the block); returns the buffer.
+template <typename T>
+sparc_status scratch_bounds(sparc_ctx *ctx, const T *Y, int ncols, long ld, unsigned **b)
+{
+    TRY(ensure(ctx, ctx->bsc, ctx->bsc_bytes, sizeof(unsigned) * (size_t)ncols));
+    *b = (unsigned *)ctx->bsc;
+    CK(cudaMemsetAsync(*b, 0, sizeof(unsigned) * (size_t)ncols, ctx->st));
+    if (std::is_same<T, double>::value)
+        CK(colmax_f64((const double *)Y, ncols, ld, ctx->H.nd, *b, ctx->st));
+    else
+        CK(colmax_f32((const float *)Y, ncols, ld, ctx->H.nd, *b, ctx->st));
+    return SPARC_OK;
+}
+
 // out = alpha ((H - shift) Y) - beta Yprev  (Yprev may alias out, may be null):
-// projection alpha chi^T Y, stencil step, nonlocal scatter-add.
+// projection alpha chi^T Y, stencil step, nonlocal scatter-add. bY, bP: column bounds of Y
+// and Yprev (bY null: taken here by a pass over Y, Yprev must then be null); bOut: raised
+// to the bounds of out when not null.
 sparc_status step_f64(sparc_ctx *ctx, const double *Y, const double *Yprev, double *out, int ncols,
-                      long ld, double alpha, double shift, double beta)
+                      long ld, double alpha, double shift, double beta,
+                      const unsigned *bY = nullptr, const unsigned *bP = nullptr,
+                      unsigned *bOut = nullptr)
 {
     const DevHam &H = ctx->H;
+    if (!bY) {
+        if (Yprev) return fail(ctx, SPARC_ERR_ARG, "internal: step without column bounds");
+        unsigned *b = nullptr;
+        TRY(scratch_bounds(ctx, Y, ncols, ld, &b));
+        bY = b;
+    }
     if (H.natoms > 0) {
         TRY(ensure_C(ctx, ncols));
         { PHASE(SPARC_PHASE_PROJECT); CK(project_f64_df(H, Y, ncols, ld, alpha, (float2 *)ctx->C, ctx->st)); }
     }
-    { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f64(H, Y, Yprev, out, ncols, ld, alpha, shift, beta, ctx->st)); }
-    if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f64_df(H, (const float2 *)ctx->C, out, ncols, ld, ctx->st)); }
+    { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f64(H, Y, Yprev, out, ncols, ld, alpha, shift, beta, bY, bP, bOut, ctx->st)); }
+    if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f64_df(H, (const float2 *)ctx->C, out, ncols, ld, bOut, ctx->st)); }
     return SPARC_OK;
 }
 
@@ -245,23 +274,32 @@ sparc_status apply_f32in_f64(sparc_ctx *ctx, const float *Y, double *out, int nc
         TRY(ensure_C(ctx, ncols));
         { PHASE(SPARC_PHASE_PROJECT); CK(project_f32in_f64(H, Y, ncols, ld, (double *)ctx->C, ctx->st)); }
     }
-    { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f32in_f64(H, Y, out, ncols, ld, ctx->st)); }
+    unsigned *bY = nullptr;
+    TRY(scratch_bounds(ctx, Y, ncols, ld, &bY));
+    { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f32in_f64(H, Y, out, ncols, ld, bY, ctx->st)); }
     if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f64(H, (const double *)ctx->C, out, ncols, ld, 1.0, ctx->st)); }
     return SPARC_OK;
 }
 
+// Step t of a filter (Y = Y_t, Yp = Y_{t-1}, out = Y_{t+1}). FP64 blocks: bnd holds one
+// row of column bounds per Y_t (row 0 filled before the first step); step t reads rows t
+// and t-1 and raises row t+1.
 template <typename T>
 sparc_status step_t(sparc_ctx *ctx, const T *Y, const T *Yp, T *out, int ncols, long ld,
-                    double alpha, double shift, double beta);
+                    double alpha, double shift, double beta, unsigned *bnd, int t);
 template <>
 sparc_status step_t<double>(sparc_ctx *ctx, const double *Y, const double *Yp, double *out,
-                            int ncols, long ld, double alpha, double shift, double beta)
+                            int ncols, long ld, double alpha, double shift, double beta,
+                            unsigned *bnd, int t)
 {
-    return step_f64(ctx, Y, Yp, out, ncols, ld, alpha, shift, beta);
+    const size_t n = (size_t)ncols;
+    return step_f64(ctx, Y, Yp, out, ncols, ld, alpha, shift, beta, bnd + t * n,
+                    t > 0 ? bnd + (t - 1) * n : nullptr, bnd + (t + 1) * n);
 }
 template <>
 sparc_status step_t<float>(sparc_ctx *ctx, const float *Y, const float *Yp, float *out,
-                           int ncols, long ld, double alpha, double shift, double beta)
+                           int ncols, long ld, double alpha, double shift, double beta,
+                           unsigned *, int)
 {
     return step_f32(ctx, Y, Yp, out, ncols, ld, alpha, shift, beta);
 }
@@ -285,12 +323,20 @@ sparc_status filter_impl(sparc_ctx *ctx, T *X, T *W, int ncols, long ld, int m, 
 {
     const double e = (b - a) / 2.0, c = (b + a) / 2.0;
     const double sigma1 = e / (a0 - c);
-    TRY(step_t<T>(ctx, X, nullptr, W, ncols, ld, sigma1 / e, c, 0.0));
+    unsigned *bnd = nullptr;
+    if (std::is_same<T, double>::value) {
+        const size_t nb = sizeof(unsigned) * (size_t)(m + 1) * ncols;
+        TRY(ensure(ctx, ctx->bnd, ctx->bnd_bytes, nb));
+        bnd = (unsigned *)ctx->bnd;
+        CK(cudaMemsetAsync(bnd, 0, nb, ctx->st));
+        CK(colmax_f64((const double *)X, ncols, ld, ctx->H.nd, bnd, ctx->st));
+    }
+    TRY(step_t<T>(ctx, X, nullptr, W, ncols, ld, sigma1 / e, c, 0.0, bnd, 0));
     T *cur = W, *prev = X;
     double sigma = sigma1;
     for (int j = 2; j <= m; ++j) {
         const double sn = 1.0 / (2.0 / sigma1 - sigma);
-        TRY(step_t<T>(ctx, cur, prev, prev, ncols, ld, 2.0 * sn / e, c, sigma * sn));
+        TRY(step_t<T>(ctx, cur, prev, prev, ncols, ld, 2.0 * sn / e, c, sigma * sn, bnd, j - 1));
         T *t = cur;
         cur = prev;
         prev = t;
@@ -425,12 +471,70 @@ void lap_weights(int no, double h, double *w)
     }
 }
 
+// Eq. (weightsLap) as exact fractions: h^2 w_p = 2 (-1)^(p+1) / p^2 * prod_{q<=p}
+// (no-q+1)/(no+q) and the three-dimensional centre 6 h^2 w_0 = -6 sum_{q<=no} 1/q^2, all
+// brought to their least common denominator D (831600 for no = 6). The FP64 stencil sums
+// 6 neighbours of |value| < 2^27 per radius in int32 and accumulates the weighted sums of
+// two such digit planes in int64, so |wint[0]| + 6 sum_p |wint[p]| must stay below 2^25.
+bool lap_weights_int(int no, double h, int *wint, double &wunit)
+{
+    if (no < 1 || no > kRadius) return false;
+    auto gcd = [](long long a, long long b) {
+        if (a < 0) a = -a;
+        while (b) {
+            const long long t = a % b;
+            a = b;
+            b = t;
+        }
+        return a;
+    };
+    long long num[kRadius + 1], den[kRadius + 1];
+    long long cn = 0, cd = 1;  // sum_q 1/q^2
+    for (int q = 1; q <= no; ++q) {
+        cn = cn * q * q + cd;
+        cd *= (long long)q * q;
+        const long long g = gcd(cn, cd);
+        cn /= g;
+        cd /= g;
+    }
+    num[0] = -6 * cn;
+    den[0] = cd;
+    for (int p = 1; p <= no; ++p) {
+        long long n = 2, d = (long long)p * p;
+        for (int q = 1; q <= p; ++q) {
+            n *= no - q + 1;
+            d *= no + q;
+            const long long g = gcd(n, d);
+            n /= g;
+            d /= g;
+        }
+        num[p] = (p % 2) ? n : -n;
+        den[p] = d;
+    }
+    long long D = 1;
+    for (int p = 0; p <= no; ++p) {
+        const long long g = gcd(D, den[p]);
+        D = D / g * den[p];
+        if (D > (1LL << 40)) return false;
+    }
+    long long tot = 0;
+    for (int p = 0; p <= kRadius; ++p) {
+        const long long W = p <= no ? num[p] * (D / den[p]) : 0;
+        if (W > INT32_MAX || W < INT32_MIN) return false;
+        wint[p] = (int)W;
+        tot += (p ? 6 : 1) * (W < 0 ? -W : W);
+    }
+    if (tot >= (1LL << 25)) return false;
+    wunit = 1.0 / ((double)D * h * h);
+    return true;
+}
+
 void free_ctx(sparc_ctx *c)
 {
     if (!c) return;
     void *ps[] = {c->V, c->Vf, c->Vdf, c->atom_ptr, c->idx, c->ent_atom, c->chi, c->gchi, c->chi_f,
                   c->gchi_f, c->chi_df, c->uniq_node, c->uniq_ptr, c->ent_list, c->nl_atom, c->nl_gf, c->nl_gdf, c->C, c->hx, c->rotx, c->roth, c->part,
-                  c->tcws, c->dm, c->lz, c->flags};
+                  c->tcws, c->dm, c->lz, c->bnd, c->bsc, c->flags};
     for (void *p : ps) dfree(p);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->prof.used) cudaEventDestroy(e);
@@ -561,6 +665,10 @@ sparc_status sparc_create(const sparc_grid *grid, const double *veff_host,
     H.radius = grid->radius;
     H.kscale = 1.0;
     lap_weights(grid->radius, grid->h, H.w);
+    if (!lap_weights_int(grid->radius, grid->h, H.wint, H.wunit)) {
+        delete ctx;
+        return SPARC_ERR_ARG;
+    }
 
     sparc_status s = SPARC_OK;
     auto run = [&]() -> sparc_status {

@@ -207,40 +207,44 @@ k_batch_stencil_tma(const BatchItem *__restrict__ items, int nitems, const Batch
         timed_out = 0;
     }
     __syncthreads();
-    // producer state (thread 0): next plane to hand to the TMA unit
-    int p_it = blockIdx.x, p_t = 0;
-    long issued = 0;
-    auto issue_upto = [&](long limit) {
+    // producer state (thread 0): next plane to hand to the TMA unit; the item being issued
+    // is held in registers (read from global memory once per item, not once per plane)
+    int p_it = blockIdx.x, p_t = 0, p_T = 0, p_x = 0, p_y = 0, p_z = 0, p_col = 0;
+    const CUtensorMap *p_mY = nullptr, *p_mP = nullptr;
+    unsigned issued = 0;  // planes handed to the TMA unit (fewer than 2^31 per CTA: host check)
+    auto issue_upto = [&](unsigned limit) {
         while (issued < limit && p_it < nitems) {
-            const BatchItem w = items[p_it];
-            const BatchTma &C = cs[w.cluster];
-            const int T = (w.k1 - w.k0) + 2 * kR;
-            if (p_t == 0) {  // a new item: bring its descriptors close before its loads
-                tma_prefetch_desc((const CUtensorMap *)C.mY);
-                if (C.mP) tma_prefetch_desc((const CUtensorMap *)C.mP);
+            if (p_t == 0) {  // a new item: read it and bring its descriptors close
+                const BatchItem w = items[p_it];
+                const BatchTma &C = cs[w.cluster];
+                p_mY = (const CUtensorMap *)C.mY;
+                p_mP = (const CUtensorMap *)C.mP;
+                p_T = (w.k1 - w.k0) + 2 * kR;
+                p_x = w.a * kBX;
+                p_y = w.b * kTY;
+                p_z = w.k0 - kR;
+                p_col = w.col;
+                tma_prefetch_desc(p_mY);
+                if (p_mP) tma_prefetch_desc(p_mP);
             }
-            const int s = (int)(issued % kStages);
-            const bool p = C.mP != nullptr && p_t >= 2 * kR;
+            const unsigned s = issued % kStages;
+            const bool p = p_mP != nullptr && p_t >= 2 * kR;
             float *st = sm + (long)s * kStageFloats;
-            const int i0 = w.a * kBX, j0 = w.b * kTY;
             mbar_arrive_expect_tx(&full[s], kPlaneBytes + (p ? kTileBytes : 0));
-            tma_load_4d(st, (const CUtensorMap *)C.mY, &full[s], i0 - 8, j0 - kR,
-                        w.k0 - kR + p_t, w.col);
-            if (p)
-                tma_load_4d(st + kH * kW, (const CUtensorMap *)C.mP, &full[s], i0, j0,
-                            w.k0 - 2 * kR + p_t, w.col);
+            tma_load_4d(st, p_mY, &full[s], p_x - 8, p_y - kR, p_z + p_t, p_col);
+            if (p) tma_load_4d(st + kH * kW, p_mP, &full[s], p_x, p_y, p_z - kR + p_t, p_col);
             ++issued;
-            if (++p_t == T) {
+            if (++p_t == p_T) {
                 p_t = 0;
                 p_it += gridDim.x;
             }
         }
     };
-    auto wait = [&](long g) -> bool {
-        return mbar_wait(&full[g % kStages], (unsigned)((g / kStages) & 1), kWaitLimit);
+    auto wait = [&](unsigned g) -> bool {
+        return mbar_wait(&full[g % kStages], (g / kStages) & 1u, kWaitLimit);
     };
     if (tid == 0) issue_upto(kStages);
-    long g0 = 0;  // sequence index of the current item's first plane
+    unsigned g0 = 0;  // sequence index of the current item's first plane
     for (int it = blockIdx.x; it < nitems && !timed_out; it += gridDim.x) {
         const BatchItem w = items[it];
         const BatchTma &C = cs[w.cluster];
@@ -255,8 +259,8 @@ k_batch_stencil_tma(const BatchItem *__restrict__ items, int nitems, const Batch
         const float *V = C.V;
         const StepCoef<float> cf = C.cf;
         const bool hasP = C.mP != nullptr;
-        auto center = [&](long g) -> float4 {
-            return *reinterpret_cast<const float4 *>(sm + (long)(g % kStages) * kStageFloats +
+        auto center = [&](unsigned g) -> float4 {
+            return *reinterpret_cast<const float4 *>(sm + (g % kStages) * kStageFloats +
                                                      (kR + ty) * kW + 8 + 4 * tx);
         };
         bool ok = true;
@@ -283,7 +287,7 @@ k_batch_stencil_tma(const BatchItem *__restrict__ items, int nitems, const Batch
             if (act && k + 1 < w.k1) vn = *reinterpret_cast<const float4 *>(V + p + plane);
             if (!wait(g0 + tc + kR)) timed_out = 1;
             q[2 * kR] = center(g0 + tc + kR);
-            const float *pl = sm + (long)((g0 + tc) % kStages) * kStageFloats;
+            const float *pl = sm + ((g0 + tc) % kStages) * kStageFloats;
             const float *row = pl + (kR + ty) * kW + 4 * tx;
             float f[20];
 #pragma unroll
@@ -314,8 +318,8 @@ k_batch_stencil_tma(const BatchItem *__restrict__ items, int nitems, const Batch
                 float4 o = make_float4(acc[0], acc[1], acc[2], acc[3]);
                 if (hasP) {
                     const float4 pv = *reinterpret_cast<const float4 *>(
-                        sm + (long)((g0 + tc + kR) % kStages) * kStageFloats + kH * kW +
-                        ty * kBX + 4 * tx);
+                        sm + ((g0 + tc + kR) % kStages) * kStageFloats + kH * kW + ty * kBX +
+                        4 * tx);
                     o.x -= cf.beta * pv.x;
                     o.y -= cf.beta * pv.y;
                     o.z -= cf.beta * pv.z;
@@ -336,10 +340,10 @@ k_batch_stencil_tma(const BatchItem *__restrict__ items, int nitems, const Batch
     if (timed_out) {
         if (tid == 0) {
             atomicExch(err, 1);
-            for (int s = 0; s < kStages; ++s) {
-                long last = -1;
-                for (long g = s; g < issued; g += kStages) last = g;
-                if (last >= 0) mbar_wait(&full[s], (unsigned)((last / kStages) & 1), kWaitLimit);
+            for (unsigned s = 0; s < kStages; ++s) {
+                if (s >= issued) continue;
+                const unsigned last = s + (issued - 1 - s) / kStages * kStages;  // latest in s
+                mbar_wait(&full[s], (last / kStages) & 1u, kWaitLimit);
             }
         }
         __syncthreads();

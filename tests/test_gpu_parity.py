@@ -214,6 +214,38 @@ def test_cheb_filter_f64(c24, degree):
     assert nrm_err(Xd.cpu().numpy(), ref) <= degree * 1e-12
 
 
+def test_f64_column_scales_zero_and_nonfinite(c24):
+    # The FP64 stencil puts each column on a fixed-point grid scaled by a power of two from
+    # the column's magnitude bound, and the filter hands the bound of Y_{j+1} from step to
+    # step: columns of very different sizes, a zero column and a column holding a NaN
+    # (which turns that column, and only it, into NaN). The sizes stay where the FP32-pair
+    # projection and scatter keep their precision (|y| >= 2^-74: the low part of a pair
+    # must stay a normal FP32 number).
+    w, cl, H, ctx = c24
+    X = synth.initial_block(4, w.nd, 5)
+    sc = np.array([1e-15, 1.0, 3e25, 0.0, 1.0])
+    X = X * sc[:, None]
+    X[4, 1234] = np.nan
+    Xd = to_dev(X)
+    HXd = torch.empty_like(Xd)
+    ctx.apply_H(Xd, HXd)
+    got = HXd.cpu().numpy()
+    for c in (0, 1, 2):
+        ref = H.apply(X[c:c + 1] / sc[c]) * sc[c]
+        assert nrm_err(got[c:c + 1], ref) <= 1e-12
+    assert np.all(got[3] == 0.0)
+    assert np.all(np.isnan(got[4]))
+    a0, a, b = -3.3, 7.6, 40.1
+    Wd = torch.empty_like(Xd)
+    ctx.cheb_filter(Xd, Wd, 10, a, b, a0)
+    got = Xd.cpu().numpy()
+    for c in (0, 1, 2):
+        ref = H.cheb_filter(X[c:c + 1] / sc[c], 10, a, b, a0) * sc[c]
+        assert nrm_err(got[c:c + 1], ref) <= 10 * 1e-12
+    assert np.all(got[3] == 0.0)
+    assert np.all(np.isnan(got[4]))
+
+
 def test_cheb_filter_f32(c24):
     w, cl, H, ctx = c24
     X = synth.initial_block(3, w.nd, 6)
