@@ -72,13 +72,14 @@ StepCoef<double> make_coef(const DevHam &H, double alpha, double shift, double b
 // blocks), or null when the Hamiltonian has no atoms.
 // FP64 blocks (stencil_df.cu): the neighbour sums are exact integer sums of the values
 // scaled by a power of two per column, so each column needs a bound of its magnitude:
-// bY[c] (and bP[c] for Yprev) = the largest high word (bits 32..62) of |y| over the
-// column, as written by colmax_f64 or by the launch that produced the block. bOut, if not
-// null, is raised (atomicMax) to the bound of the output's columns.
+// bY[c] = the largest high word (bits 32..62) of |y| over the column, as written by
+// colmax_f64 or by the launch that produced the block. bOut, if not null, is raised
+// (atomicMax) to the bound of the output's columns. Vc: V_eff - shift as FP32 pairs
+// (H.Vdf for shift 0, else from vshift_pairs).
 cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, double *out,
-                        int ncols, long ld, double alpha, double shift, double beta,
-                        const unsigned *bY, const unsigned *bP, unsigned *bOut,
-                        cudaStream_t st);
+                        int ncols, long ld, double alpha, const float2 *Vc, double beta,
+                        const unsigned *bY, unsigned *bOut, cudaStream_t st);
+cudaError_t vshift_pairs(const double *V, double shift, float2 *out, long n, cudaStream_t st);
 // out += V_nl part from Cs = alpha chi^T Y (pairs), for FP64 blocks (stencil_df.cu); bOut
 // as for stencil_f64 (raised to the bound of the updated values)
 cudaError_t scatter_f64_df(const DevHam &H, const float2 *Cs, double *out, int ncols, long ld,

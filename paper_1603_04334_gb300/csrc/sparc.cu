@@ -66,6 +66,8 @@ struct sparc_ctx {
     void *lz = nullptr;      size_t lz_bytes = 0;    // Lanczos vectors and scalars
     void *bnd = nullptr;     size_t bnd_bytes = 0;   // column bounds of the FP64 filter's blocks
     void *bsc = nullptr;     size_t bsc_bytes = 0;   // column bounds of other FP64 H applications
+    void *vc = nullptr;      size_t vc_bytes = 0;    // V_eff - vc_shift as FP32 pairs
+    double vc_shift = 0.0;   bool vc_valid = false;
     int *flags = nullptr;                            // device status words
     double *pin = nullptr;                           // pinned host staging (2*1024+16)
     int *pin_i = nullptr;
@@ -228,27 +230,43 @@ sparc_status scratch_bounds(sparc_ctx *ctx, const T *Y, int ncols, long ld, unsi
     return SPARC_OK;
 }
 
+// V_eff - shift as FP32 pairs for the FP64 stencil (kept until the shift changes).
+sparc_status shifted_v(sparc_ctx *ctx, double shift, const float2 **Vc)
+{
+    if (shift == 0.0) {
+        *Vc = ctx->H.Vdf;
+        return SPARC_OK;
+    }
+    if (!ctx->vc_valid || ctx->vc_shift != shift) {
+        TRY(ensure(ctx, ctx->vc, ctx->vc_bytes, sizeof(float2) * (size_t)ctx->H.nd));
+        CK(vshift_pairs(ctx->H.V, shift, (float2 *)ctx->vc, ctx->H.nd, ctx->st));
+        ctx->vc_shift = shift;
+        ctx->vc_valid = true;
+    }
+    *Vc = (const float2 *)ctx->vc;
+    return SPARC_OK;
+}
+
 // out = alpha ((H - shift) Y) - beta Yprev  (Yprev may alias out, may be null):
-// projection alpha chi^T Y, stencil step, nonlocal scatter-add. bY, bP: column bounds of Y
-// and Yprev (bY null: taken here by a pass over Y, Yprev must then be null); bOut: raised
-// to the bounds of out when not null.
+// projection alpha chi^T Y, stencil step, nonlocal scatter-add. bY: column bounds of Y
+// (null: taken here by a pass over Y); bOut: raised to the bounds of out when not null.
 sparc_status step_f64(sparc_ctx *ctx, const double *Y, const double *Yprev, double *out, int ncols,
                       long ld, double alpha, double shift, double beta,
-                      const unsigned *bY = nullptr, const unsigned *bP = nullptr,
-                      unsigned *bOut = nullptr)
+                      const unsigned *bY = nullptr, unsigned *bOut = nullptr)
 {
     const DevHam &H = ctx->H;
     if (!bY) {
-        if (Yprev) return fail(ctx, SPARC_ERR_ARG, "internal: step without column bounds");
         unsigned *b = nullptr;
         TRY(scratch_bounds(ctx, Y, ncols, ld, &b));
         bY = b;
     }
+    const float2 *Vc = nullptr;
+    TRY(shifted_v(ctx, shift, &Vc));
     if (H.natoms > 0) {
         TRY(ensure_C(ctx, ncols));
         { PHASE(SPARC_PHASE_PROJECT); CK(project_f64_df(H, Y, ncols, ld, alpha, (float2 *)ctx->C, ctx->st)); }
     }
-    { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f64(H, Y, Yprev, out, ncols, ld, alpha, shift, beta, bY, bP, bOut, ctx->st)); }
+    { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f64(H, Y, Yprev, out, ncols, ld, alpha, Vc, beta, bY, bOut, ctx->st)); }
     if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f64_df(H, (const float2 *)ctx->C, out, ncols, ld, bOut, ctx->st)); }
     return SPARC_OK;
 }
@@ -282,8 +300,8 @@ sparc_status apply_f32in_f64(sparc_ctx *ctx, const float *Y, double *out, int nc
 }
 
 // Step t of a filter (Y = Y_t, Yp = Y_{t-1}, out = Y_{t+1}). FP64 blocks: bnd holds one
-// row of column bounds per Y_t (row 0 filled before the first step); step t reads rows t
-// and t-1 and raises row t+1.
+// row of column bounds per Y_t (row 0 filled before the first step); step t reads row t
+// and raises row t+1.
 template <typename T>
 sparc_status step_t(sparc_ctx *ctx, const T *Y, const T *Yp, T *out, int ncols, long ld,
                     double alpha, double shift, double beta, unsigned *bnd, int t);
@@ -294,7 +312,7 @@ sparc_status step_t<double>(sparc_ctx *ctx, const double *Y, const double *Yp, d
 {
     const size_t n = (size_t)ncols;
     return step_f64(ctx, Y, Yp, out, ncols, ld, alpha, shift, beta, bnd + t * n,
-                    t > 0 ? bnd + (t - 1) * n : nullptr, bnd + (t + 1) * n);
+                    bnd + (t + 1) * n);
 }
 template <>
 sparc_status step_t<float>(sparc_ctx *ctx, const float *Y, const float *Yp, float *out,
@@ -534,7 +552,7 @@ void free_ctx(sparc_ctx *c)
     if (!c) return;
     void *ps[] = {c->V, c->Vf, c->Vdf, c->atom_ptr, c->idx, c->ent_atom, c->chi, c->gchi, c->chi_f,
                   c->gchi_f, c->chi_df, c->uniq_node, c->uniq_ptr, c->ent_list, c->nl_atom, c->nl_gf, c->nl_gdf, c->C, c->hx, c->rotx, c->roth, c->part,
-                  c->tcws, c->dm, c->lz, c->bnd, c->bsc, c->flags};
+                  c->tcws, c->dm, c->lz, c->bnd, c->bsc, c->vc, c->flags};
     for (void *p : ps) dfree(p);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->prof.used) cudaEventDestroy(e);

@@ -1,43 +1,45 @@
-// stencil_df.cu -- the FP64 fused stencil step on the FP32 and integer pipes.
+// stencil_df.cu -- the FP64 fused stencil step on the integer and FP32 pipes.
 //
 // Same operation and blocking as k_stencil in stencil.cu (Eq. FD:Laplacian with the
 // weights of Eq. weightsLap, zero-Dirichlet boundaries, V_eff and the Chebyshev
 // three-term recurrence of Algorithm ChebychevFilter, Sec. 3.4), for FP64 blocks. GB300
 // issues FP64 at 1/64 of its FP32 rate, so a native FP64 stencil is bound by the FP64
-// pipe at a few per cent of HBM bandwidth. This kernel does no FP64 arithmetic but one
-// add per point:
+// pipe at a few per cent of HBM bandwidth. This kernel does one FP64 add per point:
 //   * The Laplacian weights of radius n_o are rationals with one small common
 //     denominator D (h^2 w_p = W_p / D, W_p integers, D = 831600 for n_o = 6), so
 //     h^2 D L_h y = sum_p W_p S_p is an integer combination of the neighbour sums S_p.
-//   * Every value of a column is brought to a fixed-point grid: with |y| < 2^E over the
-//     column (E from a per-column bound), Q = y 2^(54-E) truncated to an integer
-//     (|Q| < 2^54; the dropped part is below 2^(E-54), i.e. 2^-53 of the column's
-//     largest value), stored as two int32 digits Q = d1 2^27 + d0 with 0 <= d0 < 2^27.
-//   * Each radius sums its six neighbours digit by digit in int32 (exact: |sum| < 2^30)
-//     and the weights are applied with 32 x 32 -> 64-bit integer multiply-adds into two
-//     int64 accumulators (exact: |acc| < 2^52 because |W_0| + 6 sum |W_p| < 2^25).
-//   * The exact integer result is turned into an FP32 pair and scaled by
-//     alpha (-1/2) ks / (D h^2); the centre term (c0 + alpha V_p) y_p and the recurrence
-//     term -beta Y_{j-1} are formed in pair arithmetic (TwoSum / TwoProduct, df.cuh), all
-//     in units of 2^(E_ref - 54) with E_ref the larger of the column bounds of Y_j and
-//     Y_{j-1}, so that no FP32 exponent can overflow; the pair is widened to FP64 with
-//     that exponent offset (one FP64 add).
-// The error is the truncation above (absolute, relative to the column's largest value)
-// plus about 2^-47 of the largest term in the pair arithmetic. A column whose bound is
-// not finite (Inf or NaN anywhere in Y_j or Y_{j-1}) gives NaN in every output value.
-// Each launch can raise the output's column bounds (atomicMax), which is how the filter
-// hands the bound of Y_{j+1} to the next step without another pass over the block.
+//   * Every value of a column is put on a fixed-point grid: with |y| < 2^E over the
+//     column (E from a per-column bound), y 2^(28-E) = d + r with d an integer truncated
+//     toward zero (|d| < 2^28) and r the rest (|r| < 1, same sign, kept to 23 bits as
+//     FP32).
+//   * Each radius sums its six neighbours' d in int32 (exact: |sum| < 6 * 2^28 < 2^31)
+//     and applies W_p with one 32 x 32 -> 64-bit integer multiply-add (exact: the int64
+//     accumulator stays below 2^53); the r parts are summed and weighted in FP32. The r
+//     parts carry only the bits below 2^(E-28), so FP32 rounding there costs about 2^-51
+//     of the largest term.
+//   * The integer sum becomes an FP32 pair and the r sum is added; in pair arithmetic
+//     (TwoSum / TwoProduct, df.cuh) and in units of 2^(E-28) the kernel forms
+//     (-1/2) ks / (D h^2) T + (V_p - shift) y_p and multiplies it by alpha. The pair is
+//     widened to FP64 by integer operations on its exponent (no FP64 instruction), then
+//     two FP64 operations finish the point: the pair's add and the recurrence term
+//     -beta Y_{j-1} as one fused multiply-add.
+// Error: the truncation of r (2^-51 of the column's largest value) plus about 2^-47 of the
+// largest term in the pair and FP32 arithmetic. A column whose bound is not finite (Inf or
+// NaN anywhere in Y_j) gives NaN in every output value of the column, and so does a point
+// whose pair overflows FP32 (|alpha (V_p - shift)| or the Laplacian scale near 2^100 and
+// beyond). Each launch can raise the output's column bounds (atomicMax), which is how the
+// filter hands the bound of Y_{j+1} to the next step without another pass over the block.
 #include "df.cuh"
 #include "internal.cuh"
 
 namespace sparc {
 
 struct FxCoef {
-    int W[kRadius + 1];  // integer weights: W[0] three-dimensional centre, W[p] radius p
-    float gh, gl;        // alpha (-1/2) ks / (D h^2) as a pair
-    float c0h, c0l;      // -alpha * shift as a pair
-    float ah, al;        // alpha as a pair
-    float bh, bl;        // -beta as a pair
+    int W[kRadius + 1];    // integer weights: W[0] three-dimensional centre, W[p] radius p
+    float Wf[kRadius + 1]; // the same as FP32 (exact: |W| < 2^24)
+    float gh, gl;          // (-1/2) ks / (D h^2) as a pair
+    float ah, al;          // alpha as a pair
+    double mbeta;          // -beta
 };
 
 // (sh, sl) += (vh, vl) * (wh, wl), with sh updated by TwoSum and all error terms in sl.
@@ -80,56 +82,57 @@ __device__ __forceinline__ float2 int_to_pair(long long A)
 // Column bound (largest high word of |y|) -> E with |y| < 2^E for every y of the column.
 __device__ __forceinline__ int bound_exponent(unsigned b) { return (int)((b >> 20) & 0x7ffu) - 1022; }
 
-// y 2^(54-E) truncated toward zero, as digits (d1, d0): d1 2^27 + d0, 0 <= d0 < 2^27.
-// Requires |y| < 2^E; zero and subnormal y give 0.
-__device__ __forceinline__ int2 to_digits(double y, int E)
+// A value on the column's grid: .x = d, .y = the bits of r (y 2^(28-E) = d + r).
+// From the significand M (53 bits) of y = M 2^(e-1075): d = M >> s and r = the next 23
+// bits of M below d, with s = 1047 + E - e >= 25 (|y| < 2^E); zero and subnormal y give 0.
+__device__ __forceinline__ int2 to_fx(double y, int E)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(y);
-    const unsigned hw = (unsigned)(b >> 32);
+    const unsigned hw = (unsigned)(b >> 32), ml = (unsigned)b;
     const int e = (int)((hw >> 20) & 0x7ffu);
-    const unsigned long long M = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
-    const int rsh = 1021 + E - e;  // y = M 2^(e-1075): Q = M 2^-rsh, rsh >= -1
-    unsigned long long Q = rsh < 0 ? (M << 1) : (rsh < 64 ? (M >> rsh) : 0ull);
-    if (e == 0) Q = 0ull;
-    const long long S = (hw >> 31) ? -(long long)Q : (long long)Q;
-    return make_int2((int)(S >> 27), (int)(S & 0x7ffffffll));
+    const unsigned mh = (hw & 0xfffffu) | 0x100000u;
+    const int s = 1047 + E - e, s2 = s - 23;
+    const unsigned d = s < 32 ? __funnelshift_r(ml, mh, s) : (mh >> min(s - 32, 31));
+    const unsigned r23 =
+        (s2 < 32 ? __funnelshift_r(ml, mh, s2) : (mh >> min(s2 - 32, 31))) & 0x7fffffu;
+    float r = __uint_as_float(0x3F800000u | r23) - 1.0f;  // r23 2^-23, exact
+    int di = (int)d;
+    if (hw >> 31) {
+        di = -di;
+        r = -r;
+    }
+    return e == 0 ? make_int2(0, 0) : make_int2(di, __float_as_int(r));
 }
 
-__device__ __forceinline__ int2 to_digits(float y, int E)
+// FP32 input: y = m 2^(e-150) (24-bit m); with M = m 2^27 (< 2^51),
+// y 2^(28-E) = M 2^-s, s = 149 + E - e >= 23 (|y| < 2^E), so d = M >> s < 2^28.
+__device__ __forceinline__ int2 to_fx(float y, int E)
 {
     const unsigned u = __float_as_uint(y);
     const int e = (int)((u >> 23) & 0xffu);
-    const unsigned long long M = (unsigned long long)((u & 0x7fffffu) | 0x800000u);
-    const int lsh = e - 96 - E;  // y = M 2^(e-150): Q = M 2^lsh, lsh <= 30
-    unsigned long long Q = lsh >= 0 ? (M << lsh) : (-lsh < 64 ? (M >> -lsh) : 0ull);
-    if (e == 0) Q = 0ull;
-    const long long S = (u >> 31) ? -(long long)Q : (long long)Q;
-    return make_int2((int)(S >> 27), (int)(S & 0x7ffffffll));
+    const unsigned long long M = (unsigned long long)((u & 0x7fffffu) | 0x800000u) << 27;
+    const int s = 149 + E - e;
+    const unsigned d = s < 64 ? (unsigned)(M >> s) : 0u;
+    const int s2 = s - 23;
+    const unsigned r23 = (s2 < 64 ? (unsigned)(M >> s2) : 0u) & 0x7fffffu;
+    float r = __uint_as_float(0x3F800000u | r23) - 1.0f;
+    int di = (int)d;
+    if (u >> 31) {
+        di = -di;
+        r = -r;
+    }
+    return e == 0 ? make_int2(0, 0) : make_int2(di, __float_as_int(r));
 }
 
-// The digits' value d1 2^27 + d0 (in units of 2^(E-54)) as an FP32 pair.
-__device__ __forceinline__ float2 digits_to_pair(int2 d)
+// d + r as an FP32 pair: d = dh 2^16 + dl with exactly representable pieces, Fast2Sum
+// (|dh 2^16| >= 2^16 > dl unless dh = 0), then r joins the low part.
+__device__ __forceinline__ float2 fx_to_pair(int2 v)
 {
-    return int_to_pair((long long)d.x * 134217728ll + d.y);
-}
-
-// FP32 pair (hi, lo) of y 2^k for finite y, from the bit pattern (as split_double in
-// df.cuh, with the exponent moved by k): zero for y = 0, subnormal y or |y 2^k| < 2^-126.
-__device__ __forceinline__ float2 split_scaled(double y, int k)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(y);
-    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
-    const int e = (int)((hw >> 20) & 0x7ffu);
-    const int ek = e + k;
-    const unsigned sg = hw & 0x80000000u;
-    const unsigned hb = sg | ((unsigned)(ek - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29);
-    const bool zero = e == 0 || ek < 897;
-    const unsigned hbits = zero ? 0u : (ek > 1150 ? (sg | 0x7f800000u) : hb);
-    const int es = ek - 948;
-    const float sc = __uint_as_float((unsigned)max(es, 1) << 23);
-    float lo = __uint2float_rn(lw & 0x1fffffffu) * sc;
-    lo = __uint_as_float(__float_as_uint(lo) ^ sg);
-    return make_float2(__uint_as_float(hbits), (!zero && es >= 1 && ek <= 1150) ? lo : 0.0f);
+    const float fh = small_int_to_float(v.x >> 16) * 65536.0f;
+    const float fl = small_int_to_float(v.x & 0xffff);
+    const float s = fh + fl;
+    const float e = fl - (s - fh);
+    return make_float2(s, e + __int_as_float(v.y));
 }
 
 // f 2^k as FP64 from the bit pattern: FP32 zero and subnormals, and results below the
@@ -147,164 +150,192 @@ __device__ __forceinline__ double widen_scaled(float f, int k)
     return __hiloint2double((int)hi, (int)lo);
 }
 
+// f 2^k as FP64 for FP32 values the scaled pair arithmetic produces, with
+// koff = (896 + k) << 20 and -896 <= k <= 896 (so every normal FP32 exponent lands in the
+// FP64 normal range): the exponent field is moved by an integer add; zero and FP32
+// subnormals give a signed zero. Inf and NaN are not handled (the caller checks).
+__device__ __forceinline__ double widen_fast(float f, unsigned koff)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned sg = u & 0x80000000u;
+    const bool z = (u & 0x7f800000u) == 0u;
+    const unsigned hi = z ? sg : (sg | (((u >> 3) & 0x0fffffffu) + koff));
+    return __hiloint2double((int)hi, z ? 0 : (int)(u << 29));
+}
+
 __device__ __forceinline__ unsigned abs_hi_word(double x)
 {
     return (unsigned)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7fffffffu;
 }
 
+// *b = max(*b, m). Bounds only grow, so a value read here that is already >= m makes the
+// atomic unnecessary (most warps of a launch find the bound raised by earlier warps).
+__device__ __forceinline__ void raise_bound(unsigned *b, unsigned m)
+{
+    if (m > *(volatile unsigned *)b) atomicMax(b, m);
+}
+
 // TI is the input block's type: FP64, or FP32 (the mixed-precision Rayleigh-Ritz step
 // applies H in FP64 to the FP32 filtered block). One thread per (x, y) node of a BX x BY
 // tile walks the tile's z range of one column; the 13 planes around it stay in registers
-// as digits, the current plane's tile with its x and y halos in shared memory.
+// on the column's grid, the current plane's tile with its x and y halos in shared memory.
+// The halo strips (2 R (BX + BY) nodes) are loaded and converted by all threads together,
+// at most two nodes each, so no warp runs them as a divergent side branch.
 template <typename TI, int BX, int BY>
 __global__ void __launch_bounds__(BX *BY, 2)
 k_stencil_df(const TI *__restrict__ Y, const double *Yprev, double *out,
-             const float2 *__restrict__ Vdf, int n0, int n1, int n2, long ld, int nzc, int zchunk,
-             FxCoef cf, const unsigned *__restrict__ bY, const unsigned *__restrict__ bP,
-             unsigned *bOut)
+             const float2 *__restrict__ Vc, int n0, int n1, int n2, long ld, int nzc, int zchunk,
+             FxCoef cf, const unsigned *__restrict__ bY, unsigned *bOut)
 {
-    constexpr int R = kRadius;
-    // plane k is read from s[b] while plane k+1 is staged into s[b ^ 1]: one barrier per
-    // plane, and the global loads of plane k+1 are in flight while plane k is computed
-    __shared__ int2 s[2][BY + 2 * R][BX + 2 * R];
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    constexpr int R = kRadius, SX = BX + 2 * R, SY = BY + 2 * R, NT = BX * BY;
+    constexpr int NH = 2 * R * (BX + BY);  // halo nodes of a plane
+    static_assert(NH <= 2 * NT, "at most two halo nodes per thread");
+    // plane k is read from buffer b while plane k+1 is staged into buffer b ^ 1: one barrier
+    // per plane, and the global loads of plane k+1 are in flight while plane k is computed
+    __shared__ int2 s[2 * SY * SX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
     const int i = i0 + tx, j = j0 + ty;
     const int col = blockIdx.z / nzc;
     const int k0 = (blockIdx.z % nzc) * zchunk;
     const int k1 = min(n2, k0 + zchunk);
-    const long plane = (long)n0 * n1;
+    const unsigned plane = (unsigned)n0 * (unsigned)n1;  // offsets in a column fit 32 bits
     const TI *Yc = Y + (long)col * ld;
     const double *Pc = Yprev ? Yprev + (long)col * ld : nullptr;
     double *Oc = out + (long)col * ld;
     const bool act = (i < n0) && (j < n1);
-    const long pij = (long)i + (long)n0 * j;
+    const unsigned pij = act ? (unsigned)i + (unsigned)n0 * (unsigned)j : 0u;
     const int2 zero = make_int2(0, 0);
-    // the column's scales: digits in units of 2^(EY-54), results in units of 2^(Eref-54)
-    const unsigned uy = bY[col], up = Pc ? bP[col] : 0u;
-    const bool nonfinite = ((uy >> 20) & 0x7ffu) == 0x7ffu || ((up >> 20) & 0x7ffu) == 0x7ffu;
+    // the column's scale: grid values and the pair arithmetic in units of 2^(EY-28)
+    const unsigned uy = bY[col];
+    const bool nonfinite = ((uy >> 20) & 0x7ffu) == 0x7ffu;
     const int EY = bound_exponent(uy);
-    const int Eref = Pc ? max(EY, bound_exponent(up)) : EY;
-    const int dsc = EY - Eref;  // <= 0
-    const float p2 = dsc < -126 ? 0.0f : __uint_as_float((unsigned)(dsc + 127) << 23);
-    const float sgh = cf.gh * p2, sgl = cf.gl * p2;
-    const float c0h = cf.c0h * p2, c0l = cf.c0l * p2, ah_ = cf.ah * p2, al_ = cf.al * p2;
-    const int kout = Eref - 54;
-    // halo duties of this thread: x halos (tx < R) and y halos (ty < R)
-    const bool hx = tx < R, hy = ty < R;
-    const int il = i0 - R + tx, ir = i0 + BX + tx, jt = j0 - R + ty, jb = j0 + BY + ty;
-    const bool okl = hx && j < n1 && il >= 0, okr = hx && j < n1 && ir < n0;
-    const bool okt = hy && i < n0 && jt >= 0, okb = hy && i < n0 && jb < n1;
-    const long offl = il + (long)n0 * j, offr = ir + (long)n0 * j;
-    const long offt = i + (long)n0 * jt, offb = i + (long)n0 * jb;
+    const int kout = EY - 28;
+    const bool fastw = kout >= -896 && kout <= 896;  // uniform over the CTA
+    const unsigned koff = (unsigned)(896 + kout) << 20;
+    // halo duties: nodes tid and tid + NT of the strips (left, right: R x BY each; top,
+    // bottom: BX x R each); hs = shared-memory index (-1: none), hg = offset in the plane
+    int hs[2];
+    unsigned hg[2];
+    bool hv[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int h = tid + u * NT;
+        int sx, sy;
+        if (h < 2 * R * BY) {
+            const int side = h / (R * BY), rr = h % (R * BY);
+            sy = R + rr / R;
+            sx = side ? BX + R + rr % R : rr % R;
+        } else {
+            const int v = h - 2 * R * BY;
+            const int side = v / (R * BX), rr = v % (R * BX);
+            sx = R + rr % BX;
+            sy = side ? BY + R + rr / BX : rr / BX;
+        }
+        const int gx = i0 - R + sx, gy = j0 - R + sy;
+        hs[u] = h < NH ? sy * SX + sx : -1;
+        hv[u] = h < NH && gx >= 0 && gx < n0 && gy >= 0 && gy < n1;
+        hg[u] = hv[u] ? (unsigned)gx + (unsigned)n0 * (unsigned)gy : 0u;
+    }
+    const int me = (ty + R) * SX + tx + R;  // this thread's node in a plane buffer
 
     int2 q[2 * R + 1];
 #pragma unroll
     for (int t = 0; t < 2 * R + 1; ++t) {
         const int kk = k0 - R + t;
-        q[t] = (act && kk >= 0 && kk < n2) ? to_digits(Yc[pij + (long)kk * plane], EY) : zero;
+        q[t] = (act && kk >= 0 && kk < n2) ? to_fx(Yc[pij + (unsigned)kk * plane], EY) : zero;
     }
     {
-        const long pk = (long)k0 * plane;
-        s[0][ty + R][tx + R] = q[R];
-        if (hx) {
-            s[0][ty + R][tx] = okl ? to_digits(Yc[pk + offl], EY) : zero;
-            s[0][ty + R][tx + BX + R] = okr ? to_digits(Yc[pk + offr], EY) : zero;
-        }
-        if (hy) {
-            s[0][ty][tx + R] = okt ? to_digits(Yc[pk + offt], EY) : zero;
-            s[0][ty + BY + R][tx + R] = okb ? to_digits(Yc[pk + offb], EY) : zero;
-        }
+        const unsigned pk = (unsigned)k0 * plane;
+        s[me] = q[R];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (hs[u] >= 0) s[hs[u]] = hv[u] ? to_fx(Yc[hg[u] + pk], EY) : zero;
     }
-    float2 vcur = act ? Vdf[pij + (long)k0 * plane] : make_float2(0.0f, 0.0f);
-    double pcur = (act && Pc) ? Pc[pij + (long)k0 * plane] : 0.0;
+    float2 vcur = act ? Vc[pij + (unsigned)k0 * plane] : make_float2(0.0f, 0.0f);
+    double pcur = (act && Pc) ? Pc[pij + (unsigned)k0 * plane] : 0.0;
     unsigned omax = 0u;
     __syncthreads();
     for (int k = k0; k < k1; ++k) {
         const int b = (k - k0) & 1;
-        const long pk = (long)k * plane;
+        const unsigned pk = (unsigned)k * plane;
         // loads for plane k+1 (and the queue entry k+R+1), consumed after the compute
         const bool more = k + 1 < k1;
-        const long pk1 = pk + plane;
-        TI gl = 0, gr = 0, gt = 0, gb = 0, gq = 0;
+        const unsigned pk1 = pk + plane;
+        TI g[2] = {0, 0}, gq = 0;
         double pnext = 0.0;
         float2 vnext = make_float2(0.0f, 0.0f);
         if (more) {
-            if (okl) gl = Yc[pk1 + offl];
-            if (okr) gr = Yc[pk1 + offr];
-            if (okt) gt = Yc[pk1 + offt];
-            if (okb) gb = Yc[pk1 + offb];
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (hv[u]) g[u] = Yc[hg[u] + pk1];
             if (act) {
-                vnext = Vdf[pij + pk1];
+                vnext = Vc[pij + pk1];
                 if (Pc) pnext = Pc[pij + pk1];
             }
         }
         const int kn = k + R + 1;
-        if (act && kn < n2) gq = Yc[pij + (long)kn * plane];
+        if (act && kn < n2) gq = Yc[pij + (unsigned)kn * plane];
         if (act) {
-            // h^2 D L_h y in units of 2^(EY-54): two digit planes, exact integer sums
+            // h^2 D L_h y in units of 2^(EY-28): exact integer sums of d, FP32 sums of r
             const int2 c = q[R];
-            long long A1 = (long long)cf.W[0] * c.x, A0 = (long long)cf.W[0] * c.y;
+            const int2 *row = s + b * (SY * SX) + me;
+            long long A = (long long)cf.W[0] * c.x;
+            float Rs = cf.Wf[0] * __int_as_float(c.y);
 #pragma unroll
             for (int r = 1; r <= R; ++r) {
-                const int2 xa = s[b][ty + R][tx + R + r], xb = s[b][ty + R][tx + R - r];
-                const int2 ya = s[b][ty + R + r][tx + R], yb = s[b][ty + R - r][tx + R];
-                const int s1 = (xa.x + xb.x + ya.x) + (yb.x + q[R + r].x + q[R - r].x);
-                const int s0 = (xa.y + xb.y + ya.y) + (yb.y + q[R + r].y + q[R - r].y);
-                A1 += (long long)cf.W[r] * s1;
-                A0 += (long long)cf.W[r] * s0;
+                const int2 xa = row[r], xb = row[-r], ya = row[r * SX], yb = row[-r * SX];
+                const int2 za = q[R + r], zb = q[R - r];
+                const int sd = (xa.x + xb.x + ya.x) + (yb.x + za.x + zb.x);
+                const float sr = ((__int_as_float(xa.y) + __int_as_float(xb.y)) +
+                                  (__int_as_float(ya.y) + __int_as_float(yb.y))) +
+                                 (__int_as_float(za.y) + __int_as_float(zb.y));
+                A += (long long)cf.W[r] * sd;
+                Rs = fmaf(cf.Wf[r], sr, Rs);
             }
-            // N = A1 2^27 + A0 as a pair, times g = alpha (-1/2) ks / (D h^2) 2^(EY-Eref)
-            const float2 n1p = int_to_pair(A1), n0p = int_to_pair(A0);
-            float nh, nl;
-            two_sum(n1p.x * 134217728.0f, n0p.x, nh, nl);
-            nl += n1p.y * 134217728.0f + n0p.y;
-            float ah = sgh * nh;
-            float al = fmaf(sgh, nh, -ah);
-            al = fmaf(sgh, nl, al);
-            al = fmaf(sgl, nh, al);
-            // centre: (c0 + alpha V_p) y_p
-            const float2 v = vcur;
-            float ch = 0.0f, cl = 0.0f;
-            acc_mul(v.x, v.y, ah_, al_, ch, cl);
-            {
-                float t, e;
-                two_sum(ch, c0h, t, e);
-                ch = t;
-                cl += e + c0l;
-            }
-            const float2 y = digits_to_pair(c);
-            acc_mul(y.x, y.y, ch, cl, ah, al);
-            if (Pc) {
-                const float2 pv = split_scaled(pcur, -kout);
-                acc_mul(pv.x, pv.y, cf.bh, cf.bl, ah, al);
-            }
-            double o = widen_scaled(ah, kout) + widen_scaled(al, kout);
-            if (nonfinite) o = __longlong_as_double(0x7ff8000000000000ll);
+            // T = A + Rs as a pair; (-1/2) ks / (D h^2) T + (V_p - shift) y_p; times alpha
+            const float2 tp = int_to_pair(A);
+            float th, tl;
+            two_sum(tp.x, Rs, th, tl);
+            tl += tp.y;
+            float ih = cf.gh * th;
+            float il = fmaf(cf.gh, th, -ih);
+            il = fmaf(cf.gh, tl, il);
+            il = fmaf(cf.gl, th, il);
+            const float2 y = fx_to_pair(c);
+            acc_mul(y.x, y.y, vcur.x, vcur.y, ih, il);
+            const float ah = cf.ah * ih;
+            float al = fmaf(cf.ah, ih, -ah);
+            al = fmaf(cf.ah, il, al);
+            al = fmaf(cf.al, ih, al);
+            double o;
+            if (fastw)
+                o = widen_fast(ah, koff) + widen_fast(al, koff);
+            else
+                o = widen_scaled(ah, kout) + widen_scaled(al, kout);
+            if (Pc) o = fma(cf.mbeta, pcur, o);
+            if (nonfinite || (__float_as_uint(ah) & 0x7f800000u) == 0x7f800000u)
+                o = __longlong_as_double(0x7ff8000000000000ll);
             omax = max(omax, abs_hi_word(o));
             Oc[pij + pk] = o;
         }
 #pragma unroll
         for (int t = 0; t < 2 * R; ++t) q[t] = q[t + 1];
-        q[2 * R] = (act && kn < n2) ? to_digits(gq, EY) : zero;
+        q[2 * R] = (act && kn < n2) ? to_fx(gq, EY) : zero;
         vcur = vnext;
         pcur = pnext;
         if (more) {
-            s[b ^ 1][ty + R][tx + R] = q[R];
-            if (hx) {
-                s[b ^ 1][ty + R][tx] = okl ? to_digits(gl, EY) : zero;
-                s[b ^ 1][ty + R][tx + BX + R] = okr ? to_digits(gr, EY) : zero;
-            }
-            if (hy) {
-                s[b ^ 1][ty][tx + R] = okt ? to_digits(gt, EY) : zero;
-                s[b ^ 1][ty + BY + R][tx + R] = okb ? to_digits(gb, EY) : zero;
-            }
+            int2 *nb = s + (b ^ 1) * (SY * SX);
+            nb[me] = q[R];
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (hs[u] >= 0) nb[hs[u]] = hv[u] ? to_fx(g[u], EY) : zero;
         }
         __syncthreads();
     }
     if (bOut) {
         omax = __reduce_max_sync(0xffffffffu, omax);
-        if (((ty * BX + tx) & 31) == 0 && omax) atomicMax(bOut + col, omax);
+        if ((tid & 31) == 0 && omax) raise_bound(bOut + col, omax);
     }
 }
 
@@ -370,7 +401,7 @@ k_scatter_df(double *out, long ld, int ncols, long nuniq, const int *__restrict_
 #pragma unroll
         for (int k = 0; k < kScatCols; ++k) {
             const unsigned m = __reduce_max_sync(0xffffffffu, abs_hi_word(o[k]));
-            if ((threadIdx.x & 31) == 0 && m && c0 + k < c1) atomicMax(bOut + c0 + k, m);
+            if ((threadIdx.x & 31) == 0 && m && c0 + k < c1) raise_bound(bOut + c0 + k, m);
         }
     }
 }
@@ -417,7 +448,7 @@ k_colmax(const T *__restrict__ Y, long ld, long nd, unsigned *b)
         if (p < nd) m = max(m, abs_hi_word(Yc[p]));
     }
     m = __reduce_max_sync(0xffffffffu, m);
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(b + blockIdx.y, m);
+    if ((threadIdx.x & 31) == 0 && m) raise_bound(b + blockIdx.y, m);
 }
 
 template <typename T>
@@ -447,43 +478,59 @@ cudaError_t colmax_f32(const float *Y, int ncols, long ld, long nd, unsigned *b,
 
 template <typename TI>
 static cudaError_t stencil_df_launch(const DevHam &H, const TI *Y, const double *Yprev,
-                                     double *out, int ncols, long ld, double alpha, double shift,
-                                     double beta, const unsigned *bY, const unsigned *bP,
+                                     double *out, int ncols, long ld, double alpha,
+                                     const float2 *Vc, double beta, const unsigned *bY,
                                      unsigned *bOut, cudaStream_t st)
 {
     constexpr int BX = 32, BY = 16;
     if (ncols <= 0) return cudaSuccess;
-    if (ncols > 65535 || !bY || (Yprev && !bP)) return cudaErrorInvalidValue;
+    if (ncols > 65535 || !bY || !Vc) return cudaErrorInvalidValue;
     FxCoef cf;
-    for (int r = 0; r <= kRadius; ++r) cf.W[r] = H.wint[r];
-    split_host(alpha * (-0.5 * H.kscale) * H.wunit, cf.gh, cf.gl);
-    split_host(-alpha * shift, cf.c0h, cf.c0l);
+    for (int r = 0; r <= kRadius; ++r) {
+        cf.W[r] = H.wint[r];
+        cf.Wf[r] = (float)H.wint[r];
+    }
+    split_host(-0.5 * H.kscale * H.wunit, cf.gh, cf.gl);
     split_host(alpha, cf.ah, cf.al);
-    split_host(-beta, cf.bh, cf.bl);
+    cf.mbeta = -beta;
     const int gx = (H.n0 + BX - 1) / BX, gy = (H.n1 + BY - 1) / BY;
     int nzc, zchunk;
     stencil_z_split(H.n2, (long)gx * gy, ncols, nzc, zchunk);
     dim3 grid(gx, gy, ncols * nzc), block(BX, BY);
-    k_stencil_df<TI, BX, BY><<<grid, block, 0, st>>>(Y, Yprev, out, H.Vdf, H.n0, H.n1, H.n2, ld,
-                                                     nzc, zchunk, cf, bY, bP, bOut);
+    k_stencil_df<TI, BX, BY><<<grid, block, 0, st>>>(Y, Yprev, out, Vc, H.n0, H.n1, H.n2, ld,
+                                                     nzc, zchunk, cf, bY, bOut);
     note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, double *out,
-                        int ncols, long ld, double alpha, double shift, double beta,
-                        const unsigned *bY, const unsigned *bP, unsigned *bOut,
-                        cudaStream_t st)
+                        int ncols, long ld, double alpha, const float2 *Vc, double beta,
+                        const unsigned *bY, unsigned *bOut, cudaStream_t st)
 {
-    return stencil_df_launch<double>(H, Y, Yprev, out, ncols, ld, alpha, shift, beta, bY, bP,
-                                     bOut, st);
+    return stencil_df_launch<double>(H, Y, Yprev, out, ncols, ld, alpha, Vc, beta, bY, bOut,
+                                     st);
 }
 
 cudaError_t stencil_f32in_f64(const DevHam &H, const float *Y, double *out, int ncols, long ld,
                               const unsigned *bY, cudaStream_t st)
 {
-    return stencil_df_launch<float>(H, Y, nullptr, out, ncols, ld, 1.0, 0.0, 0.0, bY, nullptr,
-                                    nullptr, st);
+    return stencil_df_launch<float>(H, Y, nullptr, out, ncols, ld, 1.0, H.Vdf, 0.0, bY, nullptr,
+                                    st);
+}
+
+// (V_eff - shift) as FP32 pairs: the FP64 difference, then split.
+__global__ void k_vshift(const double *__restrict__ V, double shift, float2 *out, long n)
+{
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (long)gridDim.x * blockDim.x)
+        out[q] = split_double(V[q] - shift);
+}
+
+cudaError_t vshift_pairs(const double *V, double shift, float2 *out, long n, cudaStream_t st)
+{
+    k_vshift<<<152 * 4, 256, 0, st>>>(V, shift, out, n);
+    note_launch();
+    return cudaGetLastError();
 }
 
 __global__ void k_to_float_pair(const double *in, float2 *out, long n)
