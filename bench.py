@@ -43,7 +43,7 @@ UNIT = "point-orbitals/s"
 ORACLE_COLS = 16      # column slice of the block the oracle timing runs on
 SM_COUNT = 152
 # kernel sources whose DRAM traffic the committed ncu summary was taken on, per dtype
-STENCIL_SOURCES = {"f64": ("stencil_df.cu", "df.cuh"),
+STENCIL_SOURCES = {"f64": ("stencil_df.cu", "df.cuh", "fx.cuh"),
                    "f32": ("stencil_tma.cu",)}
 
 

@@ -1,0 +1,97 @@
+// bounds.cu -- helpers of the FP64 path that run once per block or per context:
+// per-column magnitude bounds (the FP64 stencil's fixed-point grid), V_eff - shift as FP32
+// pairs, and FP64 arrays as FP32 pairs.
+#include "df.cuh"
+#include "fx.cuh"
+#include "internal.cuh"
+
+namespace sparc {
+
+// Column bounds: b[c] = max(b[c], largest high word of |y| over column c). kColmaxCtas
+// CTAs per column stride over it (loads 8 x 256 apart in flight per thread), reduce in
+// the CTA and raise the bound once: a few atomics per column, not one per warp.
+namespace {
+constexpr int kColmaxThreads = 256, kColmaxPer = 8, kColmaxCtas = 8;
+}  // namespace
+
+template <typename T>
+__global__ void __launch_bounds__(kColmaxThreads)
+k_colmax(const T *__restrict__ Y, long ld, long nd, unsigned *b)
+{
+    __shared__ unsigned red[kColmaxThreads / 32];
+    const T *Yc = Y + (long)blockIdx.y * ld;
+    constexpr long span = (long)kColmaxThreads * kColmaxPer;
+    unsigned m = 0u;
+    for (long base = (long)blockIdx.x * span + threadIdx.x; base < nd;
+         base += (long)gridDim.x * span) {
+#pragma unroll
+        for (int t = 0; t < kColmaxPer; ++t) {
+            const long p = base + (long)t * kColmaxThreads;
+            if (p < nd) m = max(m, abs_hi_word(Yc[p]));
+        }
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kColmaxThreads / 32; ++w) m = max(m, red[w]);
+        if (m) raise_bound(b + blockIdx.y, m);
+    }
+}
+
+template <typename T>
+static cudaError_t colmax_launch(const T *Y, int ncols, long ld, long nd, unsigned *b,
+                                 cudaStream_t st)
+{
+    if (ncols <= 0 || nd <= 0) return cudaSuccess;
+    if (ncols > 65535) return cudaErrorInvalidValue;
+    const long per = (long)kColmaxThreads * kColmaxPer;
+    const long chunks = (nd + per - 1) / per;
+    dim3 grid((unsigned)(chunks < kColmaxCtas ? chunks : kColmaxCtas), (unsigned)ncols);
+    k_colmax<T><<<grid, kColmaxThreads, 0, st>>>(Y, ld, nd, b);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t colmax_f64(const double *Y, int ncols, long ld, long nd, unsigned *b,
+                       cudaStream_t st)
+{
+    return colmax_launch<double>(Y, ncols, ld, nd, b, st);
+}
+
+cudaError_t colmax_f32(const float *Y, int ncols, long ld, long nd, unsigned *b,
+                       cudaStream_t st)
+{
+    return colmax_launch<float>(Y, ncols, ld, nd, b, st);
+}
+
+// (V_eff - shift) as FP32 pairs: the FP64 difference, then split.
+__global__ void k_vshift(const double *__restrict__ V, double shift, float2 *out, long n)
+{
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (long)gridDim.x * blockDim.x)
+        out[q] = split_double(V[q] - shift);
+}
+
+cudaError_t vshift_pairs(const double *V, double shift, float2 *out, long n, cudaStream_t st)
+{
+    k_vshift<<<152 * 4, 256, 0, st>>>(V, shift, out, n);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void k_to_float_pair(const double *in, float2 *out, long n)
+{
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (long)gridDim.x * blockDim.x)
+        out[q] = split_double(in[q]);
+}
+
+cudaError_t to_float_pair(const double *in, float2 *out, long n, cudaStream_t st)
+{
+    k_to_float_pair<<<152 * 8, 256, 0, st>>>(in, out, n);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace sparc

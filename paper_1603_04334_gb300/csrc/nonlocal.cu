@@ -4,9 +4,11 @@
 //   project: C_Jlm,c = sum_{s in supp(J)} chi_Jlm(s) Y(s, c)       (gather + 4 x nsup x ncols)
 //   scatter: out(p, c) += alpha sum_{e at p} sum_lm gchi(e, lm) C_atom(e)lm,c
 // with gchi = h^3 gamma chi precomputed at setup. The scatter walks the node -> entries
-// inverse map (entries of a node in ascending order), so no atomics are used and the
-// result does not depend on scheduling.
+// inverse map (entries of a node in ascending order), so the values need no atomics and
+// do not depend on scheduling (the FP64 pair scatter also raises per-column magnitude
+// bounds with atomicMax, whose result does not depend on order either).
 #include "df.cuh"
+#include "fx.cuh"
 #include "internal.cuh"
 
 namespace sparc {
@@ -163,7 +165,7 @@ cudaError_t project_f32in_f64(const DevHam &H, const float *Y, int ncols, long l
 // support are combined across the CTA with pair additions (TwoSum). The result is written
 // as FP32 pairs, scaled by `alpha` (the filter step's factor), for the pair scatter.
 template <int CB, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 4)
 k_project_df(const double *__restrict__ Y, long ld, int ncols, const int *__restrict__ atom_ptr,
              const int *__restrict__ idx, const float2 *__restrict__ chi, float2 *__restrict__ C,
              float alh, float all)
@@ -177,6 +179,7 @@ k_project_df(const double *__restrict__ Y, long ld, int ncols, const int *__rest
     for (int l = 0; l < 4; ++l)
 #pragma unroll
         for (int cb = 0; cb < CB; ++cb) sh[l][cb] = sl[l][cb] = 0.0f;
+#pragma unroll 2
     for (int s = b + threadIdx.x; s < e; s += NT) {
         const long p = idx[s];
         float2 x[4];
@@ -233,7 +236,7 @@ cudaError_t project_f64_df(const DevHam &H, const double *Y, int ncols, long ld,
                            float2 *C, cudaStream_t st)
 {
     if (H.natoms == 0 || ncols <= 0) return cudaSuccess;
-    constexpr int CB = 8, NT = 256;
+    constexpr int CB = 4, NT = 256;
     dim3 grid(H.natoms, (ncols + CB - 1) / CB);
     if (grid.y > 65535) return cudaErrorInvalidValue;
     const float alh = (float)alpha, all = (float)(alpha - (double)alh);
@@ -416,6 +419,80 @@ cudaError_t scatter_f64(const DevHam &H, const double *C, double *out, int ncols
     k_scatter_f64<<<grid, kScatNodes, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node,
                                                H.uniq_ptr, H.ent_list, H.ent_atom, H.gchi, C,
                                                alpha);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Nonlocal scatter for FP64 blocks in pair arithmetic: out(p, c) += sum_{q at p} sum_l
+// g(q, l) Cs(atom(q), l, c), Cs = alpha chi^T Y as pairs (k_project_df). A thread owns one
+// covered node and a group of kScatDfCols columns; the grid's x dimension (dispatched first)
+// runs over the covered nodes, so the CTAs resident at one time sweep consecutive nodes of
+// the same columns (coalesced, DRAM-page-local read-modify-write of the output; the node's
+// entries stay in L1). The pair sum is added to the FP64 output with one FP64 add. With
+// bOut, the column bounds of the output are raised to cover the updated values.
+namespace {
+constexpr int kScatDfNodes = 256;
+constexpr int kScatDfCols = 8;
+}  // namespace
+
+__global__ void __launch_bounds__(kScatDfNodes)
+k_scatter_df(double *out, long ld, int ncols, long nuniq, const int *__restrict__ uniq_node,
+             const int *__restrict__ uniq_ptr, const int *__restrict__ nl_atom,
+             const float2 *__restrict__ g, const float2 *__restrict__ Cs, unsigned *bOut)
+{
+    const long u = (long)blockIdx.x * kScatDfNodes + threadIdx.x;
+    const bool live = u < nuniq;  // no early return: the warp reduces the bounds below
+    const int c0 = blockIdx.y * kScatDfCols, c1 = min(ncols, c0 + kScatDfCols);
+    double o[kScatDfCols];
+    if (live) {
+        const long node = uniq_node[u];
+        const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
+        // all column sums first (coefficients from L1 / L2), then every output read is
+        // issued before any store: kScatDfCols independent DRAM reads in flight per thread
+        double v[kScatDfCols];
+#pragma unroll
+        for (int k = 0; k < kScatDfCols; ++k) {
+            const int c = c0 + k;
+            float vh = 0.0f, vl = 0.0f;
+            if (c < c1) {
+                for (int q = q0; q < q1; ++q) {
+                    const float2 *cs = Cs + (long)nl_atom[q] * 4 * ncols + c;
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) mac(g[4L * q + l], cs[(long)l * ncols], vh, vl);
+                }
+            }
+            v[k] = pair_to_double(vh, vl);
+        }
+        double *op = out + node + (long)c0 * ld;
+#pragma unroll
+        for (int k = 0; k < kScatDfCols; ++k) o[k] = c0 + k < c1 ? op[(long)k * ld] : 0.0;
+#pragma unroll
+        for (int k = 0; k < kScatDfCols; ++k) {
+            o[k] += v[k];
+            if (c0 + k < c1) op[(long)k * ld] = o[k];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScatDfCols; ++k) o[k] = 0.0;
+    }
+    if (bOut) {
+#pragma unroll
+        for (int k = 0; k < kScatDfCols; ++k) {
+            const unsigned m = __reduce_max_sync(0xffffffffu, abs_hi_word(o[k]));
+            if ((threadIdx.x & 31) == 0 && m && c0 + k < c1) raise_bound(bOut + c0 + k, m);
+        }
+    }
+}
+
+cudaError_t scatter_f64_df(const DevHam &H, const float2 *Cs, double *out, int ncols, long ld,
+                           unsigned *bOut, cudaStream_t st)
+{
+    if (H.natoms == 0 || H.nuniq == 0 || ncols <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((H.nuniq + kScatDfNodes - 1) / kScatDfNodes),
+              (unsigned)((ncols + kScatDfCols - 1) / kScatDfCols));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    k_scatter_df<<<grid, kScatDfNodes, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node, H.uniq_ptr,
+                                              H.nl_atom, H.nl_gdf, Cs, bOut);
     note_launch();
     return cudaGetLastError();
 }

@@ -30,6 +30,7 @@
 // beyond). Each launch can raise the output's column bounds (atomicMax), which is how the
 // filter hands the bound of Y_{j+1} to the next step without another pass over the block.
 #include "df.cuh"
+#include "fx.cuh"
 #include "internal.cuh"
 
 namespace sparc {
@@ -161,18 +162,6 @@ __device__ __forceinline__ double widen_fast(float f, unsigned koff)
     const bool z = (u & 0x7f800000u) == 0u;
     const unsigned hi = z ? sg : (sg | (((u >> 3) & 0x0fffffffu) + koff));
     return __hiloint2double((int)hi, z ? 0 : (int)(u << 29));
-}
-
-__device__ __forceinline__ unsigned abs_hi_word(double x)
-{
-    return (unsigned)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7fffffffu;
-}
-
-// *b = max(*b, m). Bounds only grow, so a value read here that is already >= m makes the
-// atomic unnecessary (most warps of a launch find the bound raised by earlier warps).
-__device__ __forceinline__ void raise_bound(unsigned *b, unsigned m)
-{
-    if (m > *(volatile unsigned *)b) atomicMax(b, m);
 }
 
 // TI is the input block's type: FP64, or FP32 (the mixed-precision Rayleigh-Ritz step
@@ -345,137 +334,6 @@ static void split_host(double x, float &h, float &l)
     l = (float)(x - (double)h);
 }
 
-// Nonlocal scatter for FP64 blocks in pair arithmetic: out(p, c) += sum_{q at p} sum_l
-// g(q, l) Cs(atom(q), l, c), Cs = alpha chi^T Y as pairs (k_project_df). A thread owns one
-// covered node and a group of kScatCols columns; the grid's x dimension (dispatched first)
-// runs over the covered nodes, so the CTAs resident at one time sweep consecutive nodes of
-// the same columns (coalesced, DRAM-page-local read-modify-write of the output; the node's
-// entries stay in L1). The pair sum is added to the FP64 output with one FP64 add. With
-// bOut, the column bounds of the output are raised to cover the updated values.
-namespace {
-constexpr int kScatNodes = 256;
-constexpr int kScatCols = 8;
-}  // namespace
-
-__global__ void __launch_bounds__(kScatNodes)
-k_scatter_df(double *out, long ld, int ncols, long nuniq, const int *__restrict__ uniq_node,
-             const int *__restrict__ uniq_ptr, const int *__restrict__ nl_atom,
-             const float2 *__restrict__ g, const float2 *__restrict__ Cs, unsigned *bOut)
-{
-    const long u = (long)blockIdx.x * kScatNodes + threadIdx.x;
-    const bool live = u < nuniq;  // no early return: the warp reduces the bounds below
-    const int c0 = blockIdx.y * kScatCols, c1 = min(ncols, c0 + kScatCols);
-    double o[kScatCols];
-    if (live) {
-        const long node = uniq_node[u];
-        const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
-        // all column sums first (coefficients from L1 / L2), then every output read is
-        // issued before any store: kScatCols independent DRAM reads in flight per thread
-        double v[kScatCols];
-#pragma unroll
-        for (int k = 0; k < kScatCols; ++k) {
-            const int c = c0 + k;
-            float vh = 0.0f, vl = 0.0f;
-            if (c < c1) {
-                for (int q = q0; q < q1; ++q) {
-                    const float2 *cs = Cs + (long)nl_atom[q] * 4 * ncols + c;
-#pragma unroll
-                    for (int l = 0; l < 4; ++l) mac(g[4L * q + l], cs[(long)l * ncols], vh, vl);
-                }
-            }
-            v[k] = pair_to_double(vh, vl);
-        }
-        double *op = out + node + (long)c0 * ld;
-#pragma unroll
-        for (int k = 0; k < kScatCols; ++k) o[k] = c0 + k < c1 ? op[(long)k * ld] : 0.0;
-#pragma unroll
-        for (int k = 0; k < kScatCols; ++k) {
-            o[k] += v[k];
-            if (c0 + k < c1) op[(long)k * ld] = o[k];
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < kScatCols; ++k) o[k] = 0.0;
-    }
-    if (bOut) {
-#pragma unroll
-        for (int k = 0; k < kScatCols; ++k) {
-            const unsigned m = __reduce_max_sync(0xffffffffu, abs_hi_word(o[k]));
-            if ((threadIdx.x & 31) == 0 && m && c0 + k < c1) raise_bound(bOut + c0 + k, m);
-        }
-    }
-}
-
-cudaError_t scatter_f64_df(const DevHam &H, const float2 *Cs, double *out, int ncols, long ld,
-                           unsigned *bOut, cudaStream_t st)
-{
-    if (H.natoms == 0 || H.nuniq == 0 || ncols <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((H.nuniq + kScatNodes - 1) / kScatNodes),
-              (unsigned)((ncols + kScatCols - 1) / kScatCols));
-    if (grid.y > 65535) return cudaErrorInvalidValue;
-    k_scatter_df<<<grid, kScatNodes, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node, H.uniq_ptr,
-                                              H.nl_atom, H.nl_gdf, Cs, bOut);
-    note_launch();
-    return cudaGetLastError();
-}
-
-// Column bounds: b[c] = max(b[c], largest high word of |y| over column c). A CTA reads
-// kColmaxPer consecutive elements per thread of one column; one atomic per warp.
-namespace {
-constexpr int kColmaxThreads = 256, kColmaxPer = 8;
-}  // namespace
-
-__device__ __forceinline__ unsigned abs_hi_word(float x)
-{
-    // high word of the FP64 widening of |x| (exponent rebiased; subnormals count as 0)
-    const unsigned u = __float_as_uint(x) & 0x7fffffffu;
-    const unsigned e = u >> 23;
-    if (e == 0u) return 0u;
-    if (e == 0xffu) return 0x7ff00000u | ((u & 0x7fffffu) ? 0x80000u : 0u);
-    return ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kColmaxThreads)
-k_colmax(const T *__restrict__ Y, long ld, long nd, unsigned *b)
-{
-    const T *Yc = Y + (long)blockIdx.y * ld;
-    const long base = (long)blockIdx.x * kColmaxThreads * kColmaxPer + threadIdx.x;
-    unsigned m = 0u;
-#pragma unroll
-    for (int t = 0; t < kColmaxPer; ++t) {
-        const long p = base + (long)t * kColmaxThreads;
-        if (p < nd) m = max(m, abs_hi_word(Yc[p]));
-    }
-    m = __reduce_max_sync(0xffffffffu, m);
-    if ((threadIdx.x & 31) == 0 && m) raise_bound(b + blockIdx.y, m);
-}
-
-template <typename T>
-static cudaError_t colmax_launch(const T *Y, int ncols, long ld, long nd, unsigned *b,
-                                 cudaStream_t st)
-{
-    if (ncols <= 0 || nd <= 0) return cudaSuccess;
-    if (ncols > 65535) return cudaErrorInvalidValue;
-    const long per = (long)kColmaxThreads * kColmaxPer;
-    dim3 grid((unsigned)((nd + per - 1) / per), (unsigned)ncols);
-    k_colmax<T><<<grid, kColmaxThreads, 0, st>>>(Y, ld, nd, b);
-    note_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t colmax_f64(const double *Y, int ncols, long ld, long nd, unsigned *b,
-                       cudaStream_t st)
-{
-    return colmax_launch<double>(Y, ncols, ld, nd, b, st);
-}
-
-cudaError_t colmax_f32(const float *Y, int ncols, long ld, long nd, unsigned *b,
-                       cudaStream_t st)
-{
-    return colmax_launch<float>(Y, ncols, ld, nd, b, st);
-}
-
 template <typename TI>
 static cudaError_t stencil_df_launch(const DevHam &H, const TI *Y, const double *Yprev,
                                      double *out, int ncols, long ld, double alpha,
@@ -516,35 +374,6 @@ cudaError_t stencil_f32in_f64(const DevHam &H, const float *Y, double *out, int 
 {
     return stencil_df_launch<float>(H, Y, nullptr, out, ncols, ld, 1.0, H.Vdf, 0.0, bY, nullptr,
                                     st);
-}
-
-// (V_eff - shift) as FP32 pairs: the FP64 difference, then split.
-__global__ void k_vshift(const double *__restrict__ V, double shift, float2 *out, long n)
-{
-    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (long)gridDim.x * blockDim.x)
-        out[q] = split_double(V[q] - shift);
-}
-
-cudaError_t vshift_pairs(const double *V, double shift, float2 *out, long n, cudaStream_t st)
-{
-    k_vshift<<<152 * 4, 256, 0, st>>>(V, shift, out, n);
-    note_launch();
-    return cudaGetLastError();
-}
-
-__global__ void k_to_float_pair(const double *in, float2 *out, long n)
-{
-    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (long)gridDim.x * blockDim.x)
-        out[q] = split_double(in[q]);
-}
-
-cudaError_t to_float_pair(const double *in, float2 *out, long n, cudaStream_t st)
-{
-    k_to_float_pair<<<152 * 8, 256, 0, st>>>(in, out, n);
-    note_launch();
-    return cudaGetLastError();
 }
 
 }  // namespace sparc
