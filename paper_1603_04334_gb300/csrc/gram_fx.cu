@@ -1,0 +1,220 @@
+// gram_fx.cu -- the FP64 subspace contractions M_s = Y^T Y and H_s = Y^T (H Y) (Sec. 3.4)
+// on the integer and FP32 pipes, from the per-column fixed-point grids of the FP64 stencil.
+//
+// Column j of an operand has a bound 2^E_j > max_k |x_kj| (fx.cuh). On that grid
+// x 2^(28 - E_j) = d + r with d an int32 (|d| < 2^28) and r the next 23 bits as FP32, so
+//   a b 2^(56 - E_i - E_j) = da db + (da rb + ra db) + ra rb.
+// da db is exact in a 32 x 32 -> 64-bit integer multiply-add; the cross terms (below
+// 2^29 each) are summed in FP32 with float(d) (its rounding is 2^-24 of a term that is
+// itself 2^-28 of da db); ra rb < 1 is dropped (2^-56 of the leading term). Every kChunk
+// rows the FP32 cross sum is rounded to an integer and joins the chunk's int64 sum
+// (|sum| < 2^62 + 2^36), which is added, shifted right by `sh` bits with rounding, to the
+// slice's int64 sum: the host picks sh so that no slice sum can overflow, and the dropped
+// bits are below 2^(sh - 63) of the largest possible chunk sum. The slice sum times
+// 2^(sh + E_i + E_j - 56) is the slice's partial; partials are summed in FP64 in a fixed
+// order. Error per chunk about 2^-47 of sum |a b| (the FP32 cross sums): the accuracy of
+// an FP64 dot product, at three integer / FP32 instructions per multiply-add where the
+// FP32-pair Gram (gram_df.cu) takes twelve.
+//
+// A CTA owns a 64 x 64 tile of G over a slice of rows (split-K); 256 threads hold 4 x 4
+// entries each: the chunk sums in registers, the slice sums in shared memory (each
+// thread owns its 16 words, no atomics). Operand rows are staged 8 at a time, converted
+// to (d, float(d), r) once per staged element, double-buffered. Symmetric mode computes
+// the tiles with i0 <= j0 only and the reduction mirrors them. A column whose bound is not
+// finite gives NaN in its row and column of G.
+#include "fx.cuh"
+#include "internal.cuh"
+
+namespace sparc {
+
+namespace {
+constexpr int FT = 64;          // tile of G
+constexpr int FK = 8;           // rows per stage
+constexpr int kChunk = 64;      // rows per exact int64 chunk sum (64 * 2^56 < 2^63)
+constexpr int kThreads = 256;
+struct __align__(16) FxEl {
+    int d;
+    float fd, r, pad;
+};
+constexpr unsigned kStageBytes = 2u * FK * FT * sizeof(FxEl);       // A and B, one buffer
+constexpr unsigned kSliceBytes = 16u * kThreads * sizeof(long long);  // [entry][thread]
+constexpr unsigned kSmemBytes = 2u * kStageBytes + kSliceBytes;       // 64 KB
+}  // namespace
+
+__device__ __forceinline__ FxEl fx_el(double x, int E)
+{
+    const int2 v = to_fx(x, E);
+    FxEl e;
+    e.d = v.x;
+    e.fd = (float)v.x;
+    e.r = __int_as_float(v.y);
+    e.pad = 0.0f;
+    return e;
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+k_gram_fx(const double *__restrict__ A, long lda, const unsigned *__restrict__ bA,
+          const double *__restrict__ B, long ldb, const unsigned *__restrict__ bB, long nd,
+          int ns, long rows_per, int sh, int sym, double *__restrict__ part)
+{
+    if (sym && blockIdx.x > blockIdx.y) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    FxEl *stage = reinterpret_cast<FxEl *>(smem);  // [buf][operand][FK][FT]
+    long long *slice = reinterpret_cast<long long *>(smem + 2 * kStageBytes);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int i0 = blockIdx.x * FT, j0 = blockIdx.y * FT;
+    const long r0 = (long)blockIdx.z * rows_per;
+    const long r1 = min(nd, r0 + rows_per);
+    // staging duty: row lr of a stage, columns lc + 32 u of each operand
+    const int lr = tid & 7, lc = tid >> 3;
+    int EA[2], EB[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int ca = i0 + lc + 32 * u, cb = j0 + lc + 32 * u;
+        EA[u] = ca < ns ? bound_exponent(bA[ca]) : 0;
+        EB[u] = cb < ns ? bound_exponent(bB[cb]) : 0;
+    }
+    long long acc[4][4];
+    float cr[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            acc[x][y] = 0;
+            cr[x][y] = 0.0f;
+            slice[(x * 4 + y) * kThreads + tid] = 0;
+        }
+    double ra[2], rb[2];
+    auto load = [&](long r) {
+        const long row = r + lr;
+        const bool okr = row < r1;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int c = lc + 32 * u;
+            ra[u] = (okr && i0 + c < ns) ? A[row + (long)(i0 + c) * lda] : 0.0;
+            rb[u] = (okr && j0 + c < ns) ? B[row + (long)(j0 + c) * ldb] : 0.0;
+        }
+    };
+    auto put = [&](int buf) {
+        FxEl *sa = stage + (buf * 2) * FK * FT, *sb = sa + FK * FT;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            sa[lr * FT + lc + 32 * u] = fx_el(ra[u], EA[u]);
+            sb[lr * FT + lc + 32 * u] = fx_el(rb[u], EB[u]);
+        }
+    };
+    const long long half = sh > 0 ? (1LL << (sh - 1)) : 0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+                const long long t = acc[x][y] + __float2ll_rn(cr[x][y]);
+                slice[(x * 4 + y) * kThreads + tid] += (t + half) >> sh;
+                acc[x][y] = 0;
+                cr[x][y] = 0.0f;
+            }
+    };
+    if (r0 < r1) {
+        load(r0);
+        put(0);
+    }
+    __syncthreads();
+    int steps = 0, buf = 0;
+    for (long r = r0; r < r1; r += FK) {
+        const bool more = r + FK < r1;
+        if (more) load(r + FK);
+        const FxEl *sa = stage + (buf * 2) * FK * FT, *sb = sa + FK * FT;
+#pragma unroll 2
+        for (int kk = 0; kk < FK; ++kk) {
+            FxEl a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = sa[kk * FT + ty + 16 * u];
+                b[u] = sb[kk * FT + tx + 16 * u];
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    acc[x][y] += (long long)a[x].d * b[y].d;
+                    cr[x][y] = fmaf(a[x].fd, b[y].r, cr[x][y]);
+                    cr[x][y] = fmaf(a[x].r, b[y].fd, cr[x][y]);
+                }
+        }
+        if (++steps == kChunk / FK) {
+            steps = 0;
+            flush();
+        }
+        if (more) put(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+    }
+    flush();
+    double *P = part + (long)blockIdx.z * ns * ns;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int gi = i0 + ty + 16 * x, gj = j0 + tx + 16 * y;
+            if (gi < ns && gj < ns) {
+                const unsigned ui = bA[gi], uj = bB[gj];
+                double v;
+                if (((ui >> 20) & 0x7ffu) == 0x7ffu || ((uj >> 20) & 0x7ffu) == 0x7ffu)
+                    v = __longlong_as_double(0x7ff8000000000000ll);
+                else
+                    v = ldexp((double)slice[(x * 4 + y) * kThreads + tid],
+                              sh + bound_exponent(ui) + bound_exponent(uj) - 56);
+                P[gi + (long)gj * ns] = v;
+            }
+        }
+}
+
+// G(i, j) = sum over slices in a fixed order; in symmetric mode entries of tiles below the
+// diagonal are read from the mirrored (j, i) position.
+__global__ void k_gram_fx_reduce(const double *__restrict__ part, int nsplit, int ns, int sym,
+                                 double *G)
+{
+    const long nn = (long)ns * ns;
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nn;
+         q += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % ns), j = (int)(q / ns);
+        const long src = (sym && (i / FT) > (j / FT)) ? (long)j + (long)i * ns : q;
+        double s = 0.0;
+        for (int t = 0; t < nsplit; ++t) s += part[(long)t * nn + src];
+        G[q] = s;
+    }
+}
+
+cudaError_t gram_f64_fx(const double *A, long lda, const unsigned *bA, const double *B,
+                        long ldb, const unsigned *bB, long nd, int ns, double *G, double *part,
+                        cudaStream_t st, bool sym)
+{
+    if (ns <= 0) return cudaSuccess;
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            k_gram_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int nsplit = gram_default_splits(ns, nd);
+    long rows_per = (nd + nsplit - 1) / nsplit;
+    rows_per = (rows_per + FK - 1) / FK * FK;
+    // slice sums stay below 2^63: chunks per slice <= 2^sh, each chunk sum < 2^62 + 2^36
+    const long chunks = (rows_per + kChunk - 1) / kChunk;
+    int sh = 0;
+    while ((1L << sh) < chunks + 1) ++sh;
+    dim3 grid((ns + FT - 1) / FT, (ns + FT - 1) / FT, nsplit);
+    k_gram_fx<<<grid, kThreads, kSmemBytes, st>>>(A, lda, bA, B, ldb, bB, nd, ns, rows_per, sh,
+                                                  sym ? 1 : 0, part);
+    note_launch();
+    const long nn = (long)ns * ns;
+    int rb = (int)((nn + 255) / 256);
+    if (rb > 152 * 16) rb = 152 * 16;
+    k_gram_fx_reduce<<<rb, 256, 0, st>>>(part, nsplit, ns, sym ? 1 : 0, G);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace sparc

@@ -225,6 +225,11 @@ cudaError_t rotate_f64_df(const double *A, long lda, long nd, int ns, const doub
                           long ldo, cudaStream_t st);
 // FP64 Gram with a caller-chosen number of row slices (part: nsplit * ns * ns doubles).
 int gram_default_splits(int ns, long nd);
+// G = A^T B for FP64 blocks on the column grids of bA, bB (bounds as for stencil_f64),
+// integer and FP32 arithmetic (gram_fx.cu); part: gram_part_elems(ns, nd) doubles.
+cudaError_t gram_f64_fx(const double *A, long lda, const unsigned *bA, const double *B,
+                        long ldb, const unsigned *bB, long nd, int ns, double *G, double *part,
+                        cudaStream_t st, bool sym);
 // Tensor-core Gram of the mixed-precision form (gram_tc.cu): G = A^T B (ns x ns FP64,
 // column-major) from operands rounded to 23 bits of each 256-row chunk's largest entry,
 // accumulated exactly on the tensor cores; sym computes the tiles on and above the

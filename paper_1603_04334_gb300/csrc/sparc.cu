@@ -408,19 +408,27 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
         TRY(ensure(ctx, ctx->hx, ctx->hx_bytes, sizeof(double) * (size_t)ns * ld));
         HX = (double *)ctx->hx;
     }
-    // H Yf in FP64
-    if (sizeof(T) == 8)
-        TRY(step_f64(ctx, (const double *)Yf, nullptr, HX, ns, ld, 1.0, 0.0, 0.0));
-    else
+    // H Yf in FP64. FP64 blocks: column bounds of Yf (one pass) and of H Yf (raised by its
+    // application) for the integer-arithmetic Gram
+    unsigned *bY = nullptr, *bH = nullptr;
+    if (sizeof(T) == 8) {
+        TRY(ensure(ctx, ctx->bsc, ctx->bsc_bytes, sizeof(unsigned) * 2 * (size_t)ns));
+        bY = (unsigned *)ctx->bsc;
+        bH = bY + ns;
+        CK(cudaMemsetAsync(bY, 0, sizeof(unsigned) * 2 * (size_t)ns, ctx->st));
+        CK(colmax_f64((const double *)Yf, ns, ld, nd, bY, ctx->st));
+        TRY(step_f64(ctx, (const double *)Yf, nullptr, HX, ns, ld, 1.0, 0.0, 0.0, bY, bH));
+    } else {
         TRY(apply_f32in_f64(ctx, (const float *)Yf, HX, ns, ld));
+    }
     // M_s = Yf^T Yf, H_s = Yf^T (H Yf)
     DenseBufs d;
     TRY(dense_bufs(ctx, ns, d));
     TRY(ensure(ctx, ctx->part, ctx->part_bytes, sizeof(double) * (size_t)gram_part_elems(ns, nd)));
     double *part = (double *)ctx->part;
     if (sizeof(T) == 8) {
-        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64((const double *)Yf, ld, (const double *)Yf, ld, nd, ns, d.M, part, ctx->st, true)); }
-        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64((const double *)Yf, ld, HX, ld, nd, ns, d.Hs, part, ctx->st, true)); }
+        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64_fx((const double *)Yf, ld, bY, (const double *)Yf, ld, bY, nd, ns, d.M, part, ctx->st, true)); }
+        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64_fx((const double *)Yf, ld, bY, HX, ld, bH, nd, ns, d.Hs, part, ctx->st, true)); }
     } else {
         // mixed-precision form: both contractions on the tensor cores (gram_tc.cu)
         TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, gram_tc_workspace(nd, ns, false, true)));
