@@ -1,5 +1,6 @@
-// gram_fx.cu -- the FP64 subspace contractions M_s = Y^T Y and H_s = Y^T (H Y) (Sec. 3.4)
-// on the integer and FP32 pipes, from the per-column fixed-point grids of the FP64 stencil.
+// gram_fx.cu -- the FP64 subspace contractions M_s = Y^T Y, H_s = Y^T (H Y) and the
+// rotation Y C of the Rayleigh-Ritz step (Sec. 3.4) on the integer and FP32 pipes, from the
+// per-column fixed-point grids of the FP64 stencil.
 //
 // Column j of an operand has a bound 2^E_j > max_k |x_kj| (fx.cuh). On that grid
 // x 2^(28 - E_j) = d + r with d an int32 (|d| < 2^28) and r the next 23 bits as FP32, so
@@ -22,6 +23,13 @@
 // to (d, float(d), r) once per staged element, double-buffered. Symmetric mode computes
 // the tiles with i0 <= j0 only and the reduction mirrors them. A column whose bound is not
 // finite gives NaN in its row and column of G.
+//
+// The rotation X = Y C (Eq. OrbitalTransformation, C the Ns x Ns matrix of the Rayleigh-
+// Ritz step) uses the same arithmetic: the rows of C are first scaled by 2^(E_k - E_max)
+// (E_k the bound exponent of column k of Y, E_max the largest), which puts every product
+// Y_ik C_kj on the common scale 2^(E_max - 28); each column j of the scaled C is put on its
+// own grid 2^F_j. An output's int64 sum becomes an FP32 pair with integer operations and is
+// widened to FP64 with the exponent offset (one FP64 add per output).
 #include "fx.cuh"
 #include "internal.cuh"
 
@@ -137,7 +145,8 @@ k_gram_fx(const double *__restrict__ A, long lda, const unsigned *__restrict__ b
             for (int x = 0; x < 4; ++x)
 #pragma unroll
                 for (int y = 0; y < 4; ++y) {
-                    acc[x][y] += (long long)a[x].d * b[y].d;
+                    // one 32 x 32 -> 64-bit multiply-add into the chunk sum
+                    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc[x][y]) : "r"(a[x].d), "r"(b[y].d));
                     cr[x][y] = fmaf(a[x].fd, b[y].r, cr[x][y]);
                     cr[x][y] = fmaf(a[x].r, b[y].fd, cr[x][y]);
                 }
@@ -198,7 +207,14 @@ cudaError_t gram_f64_fx(const double *A, long lda, const unsigned *bA, const dou
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int nsplit = gram_default_splits(ns, nd);
+    // one wave of CTAs: two resident per SM, the active tiles times the slices
+    const int nt = (ns + FT - 1) / FT;
+    const int tiles = sym ? nt * (nt + 1) / 2 : nt * nt;
+    int nsplit = 2 * 152 / tiles;
+    const int cap = gram_default_splits(ns, nd);  // the partial buffer holds this many
+    if (nsplit > cap) nsplit = cap;
+    if ((long)nsplit * kChunk > nd) nsplit = (int)((nd + kChunk - 1) / kChunk);
+    if (nsplit < 1) nsplit = 1;
     long rows_per = (nd + nsplit - 1) / nsplit;
     rows_per = (rows_per + FK - 1) / FK * FK;
     // slice sums stay below 2^63: chunks per slice <= 2^sh, each chunk sum < 2^62 + 2^36
@@ -213,6 +229,218 @@ cudaError_t gram_f64_fx(const double *A, long lda, const unsigned *bA, const dou
     int rb = (int)((nn + 255) / 256);
     if (rb > 152 * 16) rb = 152 * 16;
     k_gram_fx_reduce<<<rb, 256, 0, st>>>(part, nsplit, ns, sym ? 1 : 0, G);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---- rotation ---------------------------------------------------------------------
+// One CTA: E_max over the bounds of Y's columns, then per column j of C (one warp per
+// column) the scaled entries C_kj 2^(E_k - E_max), their bound F_j and their grid values,
+// stored row-major ([k][j]) for coalesced staging. meta = {E_max, any bound not finite}.
+__global__ void __launch_bounds__(1024)
+k_rot_prep(const double *__restrict__ C, int ns, const unsigned *__restrict__ bA, FxEl *Cd,
+           unsigned *bC, int *meta)
+{
+    __shared__ int red[32];
+    __shared__ int emax_s, bad_s;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int em = -2000, bad = 0;
+    for (int k = tid; k < ns; k += blockDim.x) {
+        const unsigned b = bA[k];
+        bad |= ((b >> 20) & 0x7ffu) == 0x7ffu;
+        em = max(em, bound_exponent(b));
+    }
+    em = __reduce_max_sync(0xffffffffu, em);
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (lane == 0) red[w] = em;
+    if (tid == 0) bad_s = 0;
+    __syncthreads();
+    if (lane == 0 && bad) atomicOr(&bad_s, 1);
+    if (tid == 0) {
+        int m = red[0];
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) m = max(m, red[q]);
+        emax_s = m;
+    }
+    __syncthreads();
+    const int Emax = emax_s;
+    for (int j = w; j < ns; j += blockDim.x >> 5) {
+        unsigned m = 0u;
+        for (int k = lane; k < ns; k += 32) {
+            const double v = ldexp(C[k + (long)j * ns], bound_exponent(bA[k]) - Emax);
+            m = max(m, abs_hi_word(v));
+        }
+        m = __reduce_max_sync(0xffffffffu, m);
+        const int F = bound_exponent(m);
+        for (int k = lane; k < ns; k += 32) {
+            const double v = ldexp(C[k + (long)j * ns], bound_exponent(bA[k]) - Emax);
+            Cd[(long)k * ns + j] = fx_el(v, F);
+        }
+        if (lane == 0) bC[j] = m;
+    }
+    if (tid == 0) {
+        meta[0] = Emax;
+        meta[1] = bad_s;
+    }
+}
+
+// x (|x| < 2^63) as an FP32 pair: three 21-bit pieces, each exact, Fast2Sum of the upper
+// two (the top piece is zero or larger in magnitude), the last joins the low part.
+__device__ __forceinline__ float2 int63_to_pair(long long x)
+{
+    const int p2 = (int)(x >> 42);
+    const int p1 = (int)((x >> 21) & 0x1fffff);
+    const int p0 = (int)(x & 0x1fffff);
+    const float f2 = (__int_as_float(0x4B400000 + p2) - 12582912.0f) * 4398046511104.0f;  // 2^42
+    const float f1 = (__int_as_float(0x4B400000 + p1) - 12582912.0f) * 2097152.0f;        // 2^21
+    const float f0 = __int_as_float(0x4B400000 + p0) - 12582912.0f;
+    const float s = f2 + f1;
+    const float e = f1 - (s - f2);
+    return make_float2(s, e + f0);
+}
+
+// f 2^k as FP64 from the bit pattern (zero / FP32 subnormal / FP64 underflow -> signed zero,
+// overflow -> Inf).
+__device__ __forceinline__ double widen_k(float f, int k)
+{
+    const unsigned u = __float_as_uint(f);
+    const int e = (int)((u >> 23) & 0xffu);
+    const unsigned m = u & 0x7fffffu, sg = u & 0x80000000u;
+    const int E = e + 896 + k;
+    unsigned hi = sg | ((unsigned)E << 20) | (m >> 3), lo = m << 29;
+    if (e == 0 || E <= 0) hi = sg, lo = 0u;
+    if (e != 0 && E >= 2047) hi = sg | 0x7ff00000u, lo = 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// out = A C: a CTA walks 64-row tiles of A for one 64-column tile of C (column tiles of a
+// row tile run side by side, so A stays in L2), K = ns staged 16 at a time.
+__global__ void __launch_bounds__(kThreads, 2)
+k_rotate_fx(const double *__restrict__ A, long lda, const unsigned *__restrict__ bA, long nd,
+            int ns, const FxEl *__restrict__ Cd, const unsigned *__restrict__ bC,
+            const int *__restrict__ meta, int sh, double *__restrict__ out, long ldo)
+{
+    constexpr int RK = 16;
+    extern __shared__ __align__(16) unsigned char smem[];
+    FxEl *As = reinterpret_cast<FxEl *>(smem);   // [RK][FT]
+    FxEl *Cs = As + RK * FT;                     // [RK][FT]
+    long long *slice = reinterpret_cast<long long *>(smem + 2 * RK * FT * sizeof(FxEl));
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int j0 = blockIdx.x * FT;
+    const int Emax = meta[0];
+    const bool bad = meta[1] != 0;
+    const long long half = sh > 0 ? (1LL << (sh - 1)) : 0;
+    for (long rt = blockIdx.y; rt * FT < nd; rt += gridDim.y) {
+        const long r0 = rt * FT;
+        long long acc[4][4];
+        float cr[4][4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+                acc[x][y] = 0;
+                cr[x][y] = 0.0f;
+                slice[(x * 4 + y) * kThreads + tid] = 0;
+            }
+        int nk = 0;
+        for (int k0 = 0; k0 < ns; k0 += RK) {
+            {   // A tile: rows r0 .. r0+63, columns k0 .. k0+15, each on its column's grid
+                const int rr = tid & 63, kc = tid >> 6;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = kc + 4 * u;
+                    const long row = r0 + rr;
+                    const bool ok = row < nd && k0 + k < ns;
+                    As[k * FT + rr] = ok ? fx_el(A[row + (long)(k0 + k) * lda],
+                                                 bound_exponent(bA[k0 + k]))
+                                         : fx_el(0.0, 0);
+                }
+            }
+            {   // C tile: rows k0 .. k0+15 of the grid form, columns j0 .. j0+63
+                const int c = tid & 63, kr = tid >> 6;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = kr + 4 * u;
+                    Cs[k * FT + c] = (k0 + k < ns && j0 + c < ns) ? Cd[(long)(k0 + k) * ns + j0 + c]
+                                                                  : fx_el(0.0, 0);
+                }
+            }
+            __syncthreads();
+#pragma unroll 2
+            for (int kk = 0; kk < RK; ++kk) {
+                FxEl a[4], c[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    a[u] = As[kk * FT + ty + 16 * u];
+                    c[u] = Cs[kk * FT + tx + 16 * u];
+                }
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) {
+                        asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc[x][y]) : "r"(a[x].d), "r"(c[y].d));
+                        cr[x][y] = fmaf(a[x].fd, c[y].r, cr[x][y]);
+                        cr[x][y] = fmaf(a[x].r, c[y].fd, cr[x][y]);
+                    }
+            }
+            nk += RK;
+            if (nk == kChunk || k0 + RK >= ns) {  // flush the chunk into the slice sums
+                nk = 0;
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) {
+                        const long long t = acc[x][y] + __float2ll_rn(cr[x][y]);
+                        slice[(x * 4 + y) * kThreads + tid] += (t + half) >> sh;
+                        acc[x][y] = 0;
+                        cr[x][y] = 0.0f;
+                    }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int c = j0 + tx + 16 * y;
+            if (c >= ns) continue;
+            const int kf = sh + Emax - 28 + bound_exponent(bC[c]) - 28;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const long row = r0 + ty + 16 * x;
+                if (row >= nd) continue;
+                const float2 p = int63_to_pair(slice[(x * 4 + y) * kThreads + tid]);
+                double v = widen_k(p.x, kf) + widen_k(p.y, kf);
+                if (bad) v = __longlong_as_double(0x7ff8000000000000ll);
+                out[row + (long)c * ldo] = v;
+            }
+        }
+    }
+}
+
+size_t rotate_fx_workspace(int ns) { return sizeof(FxEl) * (size_t)ns * ns + 16 * (size_t)ns + 64; }
+
+cudaError_t rotate_f64_fx(const double *A, long lda, const unsigned *bA, long nd, int ns,
+                          const double *C, double *out, long ldo, void *ws, cudaStream_t st)
+{
+    if (ns <= 0 || nd <= 0) return cudaSuccess;
+    constexpr unsigned kRotSmem = 2u * 16 * FT * sizeof(FxEl) + kSliceBytes;  // 64 KB
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            k_rotate_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRotSmem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    FxEl *Cd = reinterpret_cast<FxEl *>(ws);
+    unsigned *bC = reinterpret_cast<unsigned *>(Cd + (size_t)ns * ns);
+    int *meta = reinterpret_cast<int *>(bC + ns);
+    k_rot_prep<<<1, 1024, 0, st>>>(C, ns, bA, Cd, bC, meta);
+    note_launch();
+    const int chunks = (ns + kChunk - 1) / kChunk;
+    int sh = 0;
+    while ((1 << sh) < chunks + 1) ++sh;
+    const long gy = (nd + FT - 1) / FT;
+    dim3 grid((ns + FT - 1) / FT, (unsigned)(gy < 65535 ? gy : 65535));
+    k_rotate_fx<<<grid, kThreads, kRotSmem, st>>>(A, lda, bA, nd, ns, Cd, bC, meta, sh, out,
+                                                   ldo);
     note_launch();
     return cudaGetLastError();
 }

@@ -230,6 +230,11 @@ int gram_default_splits(int ns, long nd);
 cudaError_t gram_f64_fx(const double *A, long lda, const unsigned *bA, const double *B,
                         long ldb, const unsigned *bB, long nd, int ns, double *G, double *part,
                         cudaStream_t st, bool sym);
+// out = A C (C: ns x ns FP64, column-major) for an FP64 block A with column bounds bA, in
+// the same arithmetic; ws: rotate_fx_workspace(ns) bytes of device memory.
+size_t rotate_fx_workspace(int ns);
+cudaError_t rotate_f64_fx(const double *A, long lda, const unsigned *bA, long nd, int ns,
+                          const double *C, double *out, long ldo, void *ws, cudaStream_t st);
 // Tensor-core Gram of the mixed-precision form (gram_tc.cu): G = A^T B (ns x ns FP64,
 // column-major) from operands rounded to 23 bits of each 256-row chunk's largest entry,
 // accumulated exactly on the tensor cores; sym computes the tiles on and above the

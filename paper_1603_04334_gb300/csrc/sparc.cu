@@ -67,6 +67,7 @@ struct sparc_ctx {
     void *bnd = nullptr;     size_t bnd_bytes = 0;   // column bounds of the FP64 filter's blocks
     void *bsc = nullptr;     size_t bsc_bytes = 0;   // column bounds of other FP64 H applications
     void *vc = nullptr;      size_t vc_bytes = 0;    // V_eff - vc_shift as FP32 pairs
+    void *rws = nullptr;     size_t rws_bytes = 0;   // grid form of the rotation matrix
     double vc_shift = 0.0;   bool vc_valid = false;
     int *flags = nullptr;                            // device status words
     double *pin = nullptr;                           // pinned host staging (2*1024+16)
@@ -454,9 +455,10 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
         TRY(ensure(ctx, ctx->rotx, ctx->rotx_bytes, sizeof(T) * (size_t)ns * ld));
         xout = (T *)ctx->rotx;
     }
-    if (sizeof(T) == 8)
-        { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64((const double *)Yf, ld, nd, ns, d.Cf, (double *)xout, ld, ctx->st)); }
-    else
+    if (sizeof(T) == 8) {
+        TRY(ensure(ctx, ctx->rws, ctx->rws_bytes, rotate_fx_workspace(ns)));
+        { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64_fx((const double *)Yf, ld, bY, nd, ns, d.Cf, (double *)xout, ld, ctx->rws, ctx->st)); }
+    } else
         { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f32((const float *)Yf, ld, nd, ns, d.Cf, (float *)xout, ld, ctx->st)); }
     if (resid_host) {
         // H X = (H Y_f) (L^-T Q); residuals against the rotated block. The FP32 form rotates
@@ -464,7 +466,7 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
         TRY(ensure(ctx, ctx->roth, ctx->roth_bytes, sizeof(T) * (size_t)ns * ld));
         if (sizeof(T) == 8) {
             double *hxr = (double *)ctx->roth;
-            { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64(HX, ld, nd, ns, d.Cf, hxr, ld, ctx->st)); }
+            { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64_fx(HX, ld, bH, nd, ns, d.Cf, hxr, ld, ctx->rws, ctx->st)); }
             { PHASE(SPARC_PHASE_OTHER); CK(resid_f64((const double *)xout, hxr, ld, nd, ns, d.ritz, d.resid, ctx->st)); }
         } else {
             float *hxr = (float *)ctx->roth;
@@ -560,7 +562,7 @@ void free_ctx(sparc_ctx *c)
     if (!c) return;
     void *ps[] = {c->V, c->Vf, c->Vdf, c->atom_ptr, c->idx, c->ent_atom, c->chi, c->gchi, c->chi_f,
                   c->gchi_f, c->chi_df, c->uniq_node, c->uniq_ptr, c->ent_list, c->nl_atom, c->nl_gf, c->nl_gdf, c->C, c->hx, c->rotx, c->roth, c->part,
-                  c->tcws, c->dm, c->lz, c->bnd, c->bsc, c->vc, c->flags};
+                  c->tcws, c->dm, c->lz, c->bnd, c->bsc, c->vc, c->rws, c->flags};
     for (void *p : ps) dfree(p);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->prof.used) cudaEventDestroy(e);
