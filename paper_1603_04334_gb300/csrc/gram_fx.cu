@@ -19,8 +19,9 @@
 //
 // A CTA owns a 64 x 64 tile of G over a slice of rows (split-K); 256 threads hold 4 x 4
 // entries each: the chunk sums in registers, the slice sums in shared memory (each
-// thread owns its 16 words, no atomics). Operand rows are staged 8 at a time, converted
-// to (d, float(d), r) once per staged element, double-buffered. Symmetric mode computes
+// thread owns its 16 words, no atomics). Operand rows are staged 16 at a time: the raw
+// FP64 tiles of stage s+1 are copied asynchronously (cp.async, two-slot rings) while stage
+// s is converted to (d, float(d), r) and multiplied. Symmetric mode computes
 // the tiles with i0 <= j0 only and the reduction mirrors them. A column whose bound is not
 // finite gives NaN in its row and column of G.
 //
@@ -37,16 +38,18 @@ namespace sparc {
 
 namespace {
 constexpr int FT = 64;          // tile of G
-constexpr int FK = 8;           // rows per stage
+constexpr int FK = 16;          // rows per stage
 constexpr int kChunk = 64;      // rows per exact int64 chunk sum (64 * 2^56 < 2^63)
 constexpr int kThreads = 256;
 struct __align__(16) FxEl {
     int d;
     float fd, r, pad;
 };
-constexpr unsigned kStageBytes = 2u * FK * FT * sizeof(FxEl);       // A and B, one buffer
 constexpr unsigned kSliceBytes = 16u * kThreads * sizeof(long long);  // [entry][thread]
-constexpr unsigned kSmemBytes = 2u * kStageBytes + kSliceBytes;       // 64 KB
+constexpr int kRawCol = FK + 1;  // padded column of a raw tile (doubles)
+constexpr unsigned kSmemBytes = 4u * FT * kRawCol * sizeof(double)  // raw A, B rings
+                                + 2u * FK * FT * sizeof(FxEl)       // converted A, B
+                                + kSliceBytes;                      // 98 KB
 }  // namespace
 
 __device__ __forceinline__ FxEl fx_el(double x, int E)
@@ -60,6 +63,23 @@ __device__ __forceinline__ FxEl fx_el(double x, int E)
     return e;
 }
 
+// Asynchronous copies global -> shared (cp.async), zero-filled when `ok` is false (the
+// source address is then never read; a valid one is passed anyway).
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool ok)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+                 "r"(ok ? 8 : 0));
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool ok)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+                 "r"(ok ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
 __global__ void __launch_bounds__(kThreads, 2)
 k_gram_fx(const double *__restrict__ A, long lda, const unsigned *__restrict__ bA,
           const double *__restrict__ B, long ldb, const unsigned *__restrict__ bB, long nd,
@@ -67,21 +87,21 @@ k_gram_fx(const double *__restrict__ A, long lda, const unsigned *__restrict__ b
 {
     if (sym && blockIdx.x > blockIdx.y) return;
     extern __shared__ __align__(16) unsigned char smem[];
-    FxEl *stage = reinterpret_cast<FxEl *>(smem);  // [buf][operand][FK][FT]
-    long long *slice = reinterpret_cast<long long *>(smem + 2 * kStageBytes);
+    // raw tiles column-major with a padded column ([2][FT][FK + 1]): the copies (rows
+    // along threads) and the conversion reads (columns along threads) are conflict-free
+    double *Araw = reinterpret_cast<double *>(smem);
+    double *Braw = Araw + 2 * FT * kRawCol;
+    FxEl *As = reinterpret_cast<FxEl *>(Braw + 2 * FT * kRawCol);  // [FK][FT]
+    FxEl *Bs = As + FK * FT;                                       // [FK][FT]
+    long long *slice = reinterpret_cast<long long *>(Bs + FK * FT);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int i0 = blockIdx.x * FT, j0 = blockIdx.y * FT;
     const long r0 = (long)blockIdx.z * rows_per;
     const long r1 = min(nd, r0 + rows_per);
-    // staging duty: row lr of a stage, columns lc + 32 u of each operand
-    const int lr = tid & 7, lc = tid >> 3;
-    int EA[2], EB[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int ca = i0 + lc + 32 * u, cb = j0 + lc + 32 * u;
-        EA[u] = ca < ns ? bound_exponent(bA[ca]) : 0;
-        EB[u] = cb < ns ? bound_exponent(bB[cb]) : 0;
-    }
+    // conversion duty: column tid % 64, rows tid / 64 + 4 u of a stage
+    const int cc = tid & 63;
+    const int EA = i0 + cc < ns ? bound_exponent(bA[i0 + cc]) : 0;
+    const int EB = j0 + cc < ns ? bound_exponent(bB[j0 + cc]) : 0;
     long long acc[4][4];
     float cr[4][4];
 #pragma unroll
@@ -92,24 +112,20 @@ k_gram_fx(const double *__restrict__ A, long lda, const unsigned *__restrict__ b
             cr[x][y] = 0.0f;
             slice[(x * 4 + y) * kThreads + tid] = 0;
         }
-    double ra[2], rb[2];
-    auto load = [&](long r) {
-        const long row = r + lr;
-        const bool okr = row < r1;
+    const long nst = (r1 > r0) ? (r1 - r0 + FK - 1) / FK : 0;
+    auto issue = [&](long st) {
+        const int b = (int)(st & 1);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int c = lc + 32 * u;
-            ra[u] = (okr && i0 + c < ns) ? A[row + (long)(i0 + c) * lda] : 0.0;
-            rb[u] = (okr && j0 + c < ns) ? B[row + (long)(j0 + c) * ldb] : 0.0;
+        for (int u = 0; u < 4; ++u) {  // copy duty: element e = tid + 256 u is row e % 16,
+            const int e = tid + kThreads * u, q = e & 15, c = e >> 4;  // column e / 16
+            const long row = r0 + st * FK + q;
+            const bool oka = row < r1 && i0 + c < ns, okb = row < r1 && j0 + c < ns;
+            cp_async8(Araw + (b * FT + c) * kRawCol + q, oka ? A + row + (long)(i0 + c) * lda : A,
+                      oka);
+            cp_async8(Braw + (b * FT + c) * kRawCol + q, okb ? B + row + (long)(j0 + c) * ldb : B,
+                      okb);
         }
-    };
-    auto put = [&](int buf) {
-        FxEl *sa = stage + (buf * 2) * FK * FT, *sb = sa + FK * FT;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            sa[lr * FT + lc + 32 * u] = fx_el(ra[u], EA[u]);
-            sb[lr * FT + lc + 32 * u] = fx_el(rb[u], EB[u]);
-        }
+        cp_async_commit();
     };
     const long long half = sh > 0 ? (1LL << (sh - 1)) : 0;
     auto flush = [&]() {
@@ -123,23 +139,32 @@ k_gram_fx(const double *__restrict__ A, long lda, const unsigned *__restrict__ b
                 cr[x][y] = 0.0f;
             }
     };
-    if (r0 < r1) {
-        load(r0);
-        put(0);
-    }
-    __syncthreads();
-    int steps = 0, buf = 0;
-    for (long r = r0; r < r1; r += FK) {
-        const bool more = r + FK < r1;
-        if (more) load(r + FK);
-        const FxEl *sa = stage + (buf * 2) * FK * FT, *sb = sa + FK * FT;
+    if (nst > 0) issue(0);
+    int steps = 0;
+    for (long st = 0; st < nst; ++st) {
+        if (st + 1 < nst)
+            issue(st + 1);
+        else
+            cp_async_commit();  // an empty group keeps the wait count uniform
+        cp_async_wait1();
+        __syncthreads();
+        {   // this stage's elements onto their columns' grids
+            const int b = (int)(st & 1);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = (tid >> 6) + 4 * u;
+                As[q * FT + cc] = fx_el(Araw[(b * FT + cc) * kRawCol + q], EA);
+                Bs[q * FT + cc] = fx_el(Braw[(b * FT + cc) * kRawCol + q], EB);
+            }
+        }
+        __syncthreads();
 #pragma unroll 2
         for (int kk = 0; kk < FK; ++kk) {
             FxEl a[4], b[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                a[u] = sa[kk * FT + ty + 16 * u];
-                b[u] = sb[kk * FT + tx + 16 * u];
+                a[u] = As[kk * FT + ty + 16 * u];
+                b[u] = Bs[kk * FT + tx + 16 * u];
             }
 #pragma unroll
             for (int x = 0; x < 4; ++x)
@@ -155,9 +180,7 @@ k_gram_fx(const double *__restrict__ A, long lda, const unsigned *__restrict__ b
             steps = 0;
             flush();
         }
-        if (more) put(buf ^ 1);
-        __syncthreads();
-        buf ^= 1;
+        __syncthreads();  // ring slot st & 1 and the converted tiles are free again
     }
     flush();
     double *P = part + (long)blockIdx.z * ns * ns;
@@ -313,24 +336,52 @@ __device__ __forceinline__ double widen_k(float f, int k)
 }
 
 // out = A C: a CTA walks 64-row tiles of A for one 64-column tile of C (column tiles of a
-// row tile run side by side, so A stays in L2), K = ns staged 16 at a time.
+// row tile run side by side, so A stays in L2), K = ns staged RK at a time. The raw FP64
+// tile of A and the grid-form tile of C of stage s+1 are copied asynchronously while
+// stage s is converted and multiplied (two-slot rings, no registers held for them).
+namespace {
+constexpr int RK = 16;
+constexpr unsigned kRotSmem = 2u * RK * FT * sizeof(double)     // raw A ring
+                              + 2u * RK * FT * sizeof(FxEl)     // C ring
+                              + RK * FT * sizeof(FxEl)          // converted A
+                              + kSliceBytes;                    // 96 KB
+}  // namespace
+
 __global__ void __launch_bounds__(kThreads, 2)
 k_rotate_fx(const double *__restrict__ A, long lda, const unsigned *__restrict__ bA, long nd,
             int ns, const FxEl *__restrict__ Cd, const unsigned *__restrict__ bC,
             const int *__restrict__ meta, int sh, double *__restrict__ out, long ldo)
 {
-    constexpr int RK = 16;
     extern __shared__ __align__(16) unsigned char smem[];
-    FxEl *As = reinterpret_cast<FxEl *>(smem);   // [RK][FT]
-    FxEl *Cs = As + RK * FT;                     // [RK][FT]
-    long long *slice = reinterpret_cast<long long *>(smem + 2 * RK * FT * sizeof(FxEl));
+    double *Araw = reinterpret_cast<double *>(smem);               // [2][RK][FT]
+    FxEl *Cs = reinterpret_cast<FxEl *>(Araw + 2 * RK * FT);        // [2][RK][FT]
+    FxEl *As = Cs + 2 * RK * FT;                                    // [RK][FT]
+    long long *slice = reinterpret_cast<long long *>(As + RK * FT);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int j0 = blockIdx.x * FT;
     const int Emax = meta[0];
     const bool bad = meta[1] != 0;
     const long long half = sh > 0 ? (1LL << (sh - 1)) : 0;
+    const int nst = (ns + RK - 1) / RK;
     for (long rt = blockIdx.y; rt * FT < nd; rt += gridDim.y) {
         const long r0 = rt * FT;
+        // stage s into slot s & 1: element e = tid + 256 u is (k = e / 64, row / column
+        // e % 64) of the RK x 64 tiles
+        auto issue = [&](int st) {
+            const int k0 = st * RK, b = st & 1;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = tid + kThreads * u, k = e >> 6, q = e & 63;
+                const long row = r0 + q;
+                const bool oka = row < nd && k0 + k < ns;
+                cp_async8(Araw + (b * RK + k) * FT + q, oka ? A + row + (long)(k0 + k) * lda : A,
+                          oka);
+                const bool okc = k0 + k < ns && j0 + q < ns;
+                cp_async16(Cs + (b * RK + k) * FT + q,
+                           okc ? Cd + (long)(k0 + k) * ns + j0 + q : Cd, okc);
+            }
+            cp_async_commit();
+        };
         long long acc[4][4];
         float cr[4][4];
 #pragma unroll
@@ -341,37 +392,33 @@ k_rotate_fx(const double *__restrict__ A, long lda, const unsigned *__restrict__
                 cr[x][y] = 0.0f;
                 slice[(x * 4 + y) * kThreads + tid] = 0;
             }
+        issue(0);
         int nk = 0;
-        for (int k0 = 0; k0 < ns; k0 += RK) {
-            {   // A tile: rows r0 .. r0+63, columns k0 .. k0+15, each on its column's grid
-                const int rr = tid & 63, kc = tid >> 6;
+        for (int st = 0; st < nst; ++st) {
+            if (st + 1 < nst)
+                issue(st + 1);
+            else
+                cp_async_commit();  // an empty group keeps the wait count uniform
+            cp_async_wait1();
+            __syncthreads();
+            {   // convert this stage's A elements onto their columns' grids
+                const int k0 = st * RK, b = st & 1;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int k = kc + 4 * u;
-                    const long row = r0 + rr;
-                    const bool ok = row < nd && k0 + k < ns;
-                    As[k * FT + rr] = ok ? fx_el(A[row + (long)(k0 + k) * lda],
-                                                 bound_exponent(bA[k0 + k]))
-                                         : fx_el(0.0, 0);
-                }
-            }
-            {   // C tile: rows k0 .. k0+15 of the grid form, columns j0 .. j0+63
-                const int c = tid & 63, kr = tid >> 6;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int k = kr + 4 * u;
-                    Cs[k * FT + c] = (k0 + k < ns && j0 + c < ns) ? Cd[(long)(k0 + k) * ns + j0 + c]
-                                                                  : fx_el(0.0, 0);
+                    const int e = tid + kThreads * u, k = e >> 6, q = e & 63;
+                    const int E = k0 + k < ns ? bound_exponent(bA[k0 + k]) : 0;
+                    As[k * FT + q] = fx_el(Araw[(b * RK + k) * FT + q], E);
                 }
             }
             __syncthreads();
+            const FxEl *cs = Cs + (st & 1) * RK * FT;
 #pragma unroll 2
             for (int kk = 0; kk < RK; ++kk) {
                 FxEl a[4], c[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     a[u] = As[kk * FT + ty + 16 * u];
-                    c[u] = Cs[kk * FT + tx + 16 * u];
+                    c[u] = cs[kk * FT + tx + 16 * u];
                 }
 #pragma unroll
                 for (int x = 0; x < 4; ++x)
@@ -383,7 +430,7 @@ k_rotate_fx(const double *__restrict__ A, long lda, const unsigned *__restrict__
                     }
             }
             nk += RK;
-            if (nk == kChunk || k0 + RK >= ns) {  // flush the chunk into the slice sums
+            if (nk == kChunk || st + 1 == nst) {  // flush the chunk into the slice sums
                 nk = 0;
 #pragma unroll
                 for (int x = 0; x < 4; ++x)
@@ -395,7 +442,7 @@ k_rotate_fx(const double *__restrict__ A, long lda, const unsigned *__restrict__
                         cr[x][y] = 0.0f;
                     }
             }
-            __syncthreads();
+            __syncthreads();  // slot st & 1 and the converted tile are free again
         }
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
@@ -421,7 +468,6 @@ cudaError_t rotate_f64_fx(const double *A, long lda, const unsigned *bA, long nd
                           const double *C, double *out, long ldo, void *ws, cudaStream_t st)
 {
     if (ns <= 0 || nd <= 0) return cudaSuccess;
-    constexpr unsigned kRotSmem = 2u * 16 * FT * sizeof(FxEl) + kSliceBytes;  // 64 KB
     static bool attr_set = false;
     if (!attr_set) {
         const cudaError_t e = cudaFuncSetAttribute(
