@@ -12,7 +12,9 @@
 //
 // Rotation angles follow Golub & Van Loan's symmetric Schur decomposition (Algorithm
 // 8.4.1); a rotation is skipped when |a_pq| <= 4 eps ||A||_F, and the sweeps stop after a
-// sweep that skipped all of them (as in dense.cu's single-CTA version).
+// sweep that skipped all of them (as in dense.cu's single-CTA version). A round that
+// skips all of its rotations changes nothing, so it needs neither the update pass nor the
+// barrier (every CTA takes that decision from the same data).
 //
 // The grid barrier is a counter/generation pair in global memory; the kernel is launched
 // cooperatively (all CTAs co-resident), and every wait is bounded: after kBarrierSpins
@@ -57,7 +59,7 @@ k_jacobi_grid(T *A0, T *A1, T *V, T *diag, int n, GridBarrier *bar, int *status,
     __shared__ int sp[kMaxDense / 2], sq[kMaxDense / 2];
     __shared__ T sc[kMaxDense / 2], ss[kMaxDense / 2];
     __shared__ double red[NT / 32];
-    __shared__ int any_rot;
+    __shared__ int any_rot, round_rot;
     if (*((volatile int *)status) != 0) return;  // the reduction step failed
     const unsigned nb = gridDim.x;
     const long nn = (long)n * n;
@@ -80,6 +82,8 @@ k_jacobi_grid(T *A0, T *A1, T *V, T *diag, int n, GridBarrier *bar, int *status,
         if (threadIdx.x == 0) any_rot = 0;
         __syncthreads();
         for (int r = 0; r < m - 1; ++r) {
+            if (threadIdx.x == 0) round_rot = 0;
+            __syncthreads();
             for (int k = threadIdx.x; k < half; k += NT) {
                 int p, q;
                 pair_of(r, k, m, p, q);
@@ -94,6 +98,7 @@ k_jacobi_grid(T *A0, T *A1, T *V, T *diag, int n, GridBarrier *bar, int *status,
                         c = (T)1 / sqrt((T)1 + t * t);
                         s = t * c;
                         any_rot = 1;
+                        round_rot = 1;
                     }
                 }
                 sp[k] = p;
@@ -102,6 +107,9 @@ k_jacobi_grid(T *A0, T *A1, T *V, T *diag, int n, GridBarrier *bar, int *status,
                 ss[k] = s;
             }
             __syncthreads();
+            // a round without rotations leaves A and V as they are; every CTA computed the
+            // same angles from the same copy, so all of them skip it (and its barrier)
+            if (!round_rot) continue;
             // 2 x 2 blocks: next = J_1^T cur J_2 (every entry of next is written)
             for (long b = gtid; b < (long)half * half; b += gstride) {
                 const int k1 = (int)(b % half), k2 = (int)(b / half);
