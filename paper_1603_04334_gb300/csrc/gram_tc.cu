@@ -44,33 +44,49 @@
 namespace sparc {
 
 namespace {
-constexpr int kTile = 128;                     // MMA M = N = 128
-constexpr int kChunk = 256;                    // rows per exactness chunk
-constexpr int kStep = 32;                      // rows per pipeline stage
-constexpr int kStepsPerChunk = kChunk / kStep;
-constexpr int kDigits = 3;
-constexpr int kClasses = 3;
-constexpr int kBlobElems = kTile * kStep;      // 4096 BF16 = 8 KB
-constexpr unsigned kOperandBytes = kDigits * kBlobElems * 2;  // 24 KB
-constexpr unsigned kStageBytes = 2 * kOperandBytes;           // 48 KB
-constexpr int kStages = 3;
+constexpr int kTile = 128;                     // MMA M (A columns per tile)
 constexpr int kEpiWarps = 8;
-constexpr int kEpiCols = 64;                   // G columns per epilogue thread
-// ring, then the low parts of the epilogue's running pair sums ([warp][column][lane])
-constexpr unsigned kLowBytes = kEpiWarps * kEpiCols * 32 * 4;  // 64 KB
-constexpr unsigned kSmemBytes = kStages * kStageBytes + kLowBytes + 1024;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr unsigned kWaitLimit = 1u << 22;
 constexpr int kTmemCols = 512;
 constexpr int kNonFinite = INT32_MIN;          // exponent sentinel of a chunk with Inf/NaN
-
 // core-matrix offsets inside a blob (elements): K-adjacent cores 2048 B apart, M/N-adjacent
 // cores 128 B apart
 constexpr unsigned kLbo = 2048, kSbo = 128;
+}  // namespace
 
+// The two representations. Tc23 (mixed form): entries rounded to 23 bits of the chunk's
+// largest, three digits, classes 0..2, 256-row chunks, 128 x 128 tiles. Tc47 (FP64 form):
+// 47 bits, six digits, classes 0..5 (21 digit MMAs per 16 rows; a class sums at most six
+// digit products, so 128-row chunks keep it below 2^24), 128 x 64 half tiles (six class
+// accumulators of 64 columns fit the 512 tensor-memory columns).
+struct Tc23 {
+    static constexpr int kDigits = 3, kClasses = 3, kBits = 23, kChunk = 256, kStep = 32,
+                         kN = 128, kStages = 3;
+};
+struct Tc47 {
+    static constexpr int kDigits = 6, kClasses = 6, kBits = 47, kChunk = 128, kStep = 16,
+                         kN = 64, kStages = 3;
+};
+template <class C> struct TcDims {
+    static constexpr int kStepsPerChunk = C::kChunk / C::kStep;
+    static constexpr int kBlobElems = kTile * C::kStep;                    // BF16 per blob
+    static constexpr unsigned kOperandBytes = C::kDigits * kBlobElems * 2;
+    static constexpr unsigned kStageBytes = 2 * kOperandBytes;
+    static constexpr int kHalves = kTile / C::kN;                          // CTAs per tile
+    static constexpr int kEpiCols = C::kN / 2;                             // per epilogue warp
+    // ring, then the low parts of the epilogue's running pair sums ([warp][column][lane])
+    static constexpr unsigned kLowBytes = kEpiWarps * kEpiCols * 32 * 4;
+    static constexpr unsigned kSmemBytes = C::kStages * kStageBytes + kLowBytes + 1024;
+    static_assert(C::kClasses * C::kN <= kTmemCols, "class accumulators exceed tensor memory");
+    static_assert(C::kBits == 8 * (C::kDigits - 1) + 7, "top digit must stay within [0, 128]");
+};
+
+namespace {
+template <class C>
 __device__ __forceinline__ long blob_offset(int cb, long step, int s, long nstep)
 {
-    return (((long)cb * nstep + step) * kDigits + s) * kBlobElems;
+    return (((long)cb * nstep + step) * C::kDigits + s) * TcDims<C>::kBlobElems;
 }
 
 __device__ __forceinline__ int in_blob(int k, int c)  // k: row in step, c: column (0..127)
@@ -95,26 +111,27 @@ template <> struct FBits<double> {
 }  // namespace
 
 // Digits and exponents of one operand. CTA: one chunk (blockIdx.y) x 8 columns
-// (blockIdx.x), one warp per column, 8 rows per lane. Rows past nd and columns past ns are
-// zero; a chunk column holding Inf or NaN gets the exponent kNonFinite.
-template <typename T>
+// (blockIdx.x), one warp per column, kChunk / 32 rows per lane. Rows past nd and columns
+// past ns are zero; a chunk column holding Inf or NaN gets the exponent kNonFinite.
+template <class C, typename T>
 __global__ void __launch_bounds__(256)
 k_tc_digits(const T *__restrict__ X, long ld, long nd, int ns, long nstep,
             __nv_bfloat16 *__restrict__ D, int *__restrict__ E, int ns_pad)
 {
     using B = FBits<T>;
     using U = typename B::U;
+    constexpr int R = C::kChunk / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int col = blockIdx.x * 8 + warp;
     const long chunk = blockIdx.y;
-    const long k0 = chunk * kChunk;
-    U mag[8];
-    bool ng[8];
+    const long k0 = chunk * C::kChunk;
+    U mag[R];
+    bool ng[R];
     U mx = 0;
     bool bad = false;
     const U inf = (U)B::kExpMask << B::kMant;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < R; ++u) {
         const long k = k0 + lane + 32 * u;
         T x = (T)0;
         if (col < ns && k < nd) x = X[k + (long)col * ld];
@@ -136,38 +153,43 @@ k_tc_digits(const T *__restrict__ X, long ld, long nd, int ns, long nstep,
     if (lane == 0 && col < ns_pad) E[chunk * ns_pad + col] = bad ? kNonFinite : e;
     const int cb = col >> 7, c = col & 127;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < R; ++u) {
         const long k = k0 + lane + 32 * u;
         long N = 0;
         if (!bad && mag[u] != 0) {
             const int bx = (int)(mag[u] >> B::kMant);
             const U m = (mag[u] & (((U)1 << B::kMant) - 1)) | (bx ? ((U)1 << B::kMant) : 0);
             const int ebx = bx ? bx : 1;
-            // N = round(m 2^(ebx - bias - mant + 23 - e)); the shift is >= 1 since |x| < 2^e
-            const int sh = e + B::kBias + B::kMant - 23 - ebx;
+            // N = round(m 2^(ebx - bias - mant + kBits - e)) in [0, 2^kBits]
+            const int sh = e + B::kBias + B::kMant - C::kBits - ebx;
             if (sh <= 0)
-                N = (long)m << (-sh);  // cannot happen for |x| < 2^e; kept total
+                N = (long)m << (-sh);  // exact: FP32 inputs of the 47-bit form
             else if (sh < 8 * (int)sizeof(U))
                 N = (long)((m + ((U)1 << (sh - 1))) >> sh);
         }
-        const int d3 = (int)(((N + 128) & 255) - 128);
-        const long N1 = (N - d3) >> 8;
-        const int d2 = (int)(((N1 + 128) & 255) - 128);
-        const int d1 = (int)((N1 - d2) >> 8);
+        // balanced base-256 digits from the bottom; the top one lies in [0, 128]
+        int d[C::kDigits];
+#pragma unroll
+        for (int s = C::kDigits - 1; s > 0; --s) {
+            d[s] = (int)(((N + 128) & 255) - 128);
+            N = (N - d[s]) >> 8;
+        }
+        d[0] = (int)N;
         const int sg = ng[u] ? -1 : 1;
-        const long step = k / kStep;
-        const int kl = (int)(k % kStep);
+        const long step = k / C::kStep;
+        const int kl = (int)(k % C::kStep);
         if (col < ns_pad) {
-            const long base = ((long)cb * nstep + step) * kDigits * kBlobElems + in_blob(kl, c);
-            D[base] = __float2bfloat16_rn((float)(sg * d1));
-            D[base + kBlobElems] = __float2bfloat16_rn((float)(sg * d2));
-            D[base + 2 * kBlobElems] = __float2bfloat16_rn((float)(sg * d3));
+            const long base = blob_offset<C>(cb, step, 0, nstep) + in_blob(kl, c);
+#pragma unroll
+            for (int s = 0; s < C::kDigits; ++s)
+                D[base + (long)s * TcDims<C>::kBlobElems] = __float2bfloat16_rn((float)(sg * d[s]));
         }
     }
 }
 
 // 2^(e - 7) as an FP32 factor (the chunk scale 2^(e_i + e_j - 14) is applied as two such
-// factors, each exact); 0 below the FP32 normal range, NaN for a non-finite chunk.
+// factors, each exact); 0 below the FP32 normal range, NaN for a non-finite chunk. The
+// scale is the same for both forms: 2 kBits - 2 * 8 (kDigits - 1) = 14.
 __device__ __forceinline__ float pow2_factor(int e)
 {
     if (e == kNonFinite) return __int_as_float(0x7FC00000);
@@ -184,14 +206,20 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e)
     e = (a - (s - bb)) + (b - bb);
 }
 
-// tiles[t] = (A column block, B column block); part: nsplit x ntiles x 128 x 128 doubles,
-// element (r, c) of a tile at r * 128 + c (r: A column, c: B column).
+// tiles[t] = (A column block, B column block); a tile is computed by kHalves CTAs, each
+// for kN of its 128 B columns. part: nsplit x ntiles x 128 x 128 doubles, element (r, c) of
+// a tile at r * 128 + c (r: A column, c: B column).
+template <class C>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
           const __nv_bfloat16 *__restrict__ DB, const int *__restrict__ EB, int ns_pad, long nstep,
           const int2 *__restrict__ tiles, int ntiles, int nsplit, double *__restrict__ part,
           int *err)
 {
+    using Dm = TcDims<C>;
+    constexpr int kStages = C::kStages, kStepsPerChunk = Dm::kStepsPerChunk;
+    constexpr unsigned kStageBytes = Dm::kStageBytes, kOperandBytes = Dm::kOperandBytes;
+    constexpr int kEpiCols = Dm::kEpiCols;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full, acc_empty, drain;
     __shared__ uint32_t tmem_base;
@@ -200,7 +228,9 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
     unsigned char *smem =
         (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x % ntiles, split = blockIdx.x / ntiles;
+    const int hf = blockIdx.x % Dm::kHalves;
+    const int tile = (blockIdx.x / Dm::kHalves) % ntiles;
+    const int split = blockIdx.x / (Dm::kHalves * ntiles);
     const int2 tb = tiles[tile];
     const long nchunk = nstep / kStepsPerChunk;
     const long c0 = (long)split * nchunk / nsplit, c1 = (long)(split + 1) * nchunk / nsplit;
@@ -231,7 +261,7 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
     };
 
     if (warp == 0) {
-        // ---- producer: A and B blobs of each 64-row step into the ring ----
+        // ---- producer: A and B blobs of each step into the ring ----
         if (lane == 0) {
             long issued = 0;
             for (long st = st0; st < st1 && !abort_flag; ++st) {
@@ -244,9 +274,9 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                 }
                 unsigned char *dst = smem + (size_t)s * kStageBytes;
                 mbar_arrive_expect_tx(&full[s], one ? kOperandBytes : kStageBytes);
-                bulk_load(dst, DA + blob_offset(tb.x, st, 0, nstep), kOperandBytes, &full[s]);
+                bulk_load(dst, DA + blob_offset<C>(tb.x, st, 0, nstep), kOperandBytes, &full[s]);
                 if (!one)
-                    bulk_load(dst + kOperandBytes, DB + blob_offset(tb.y, st, 0, nstep),
+                    bulk_load(dst + kOperandBytes, DB + blob_offset<C>(tb.y, st, 0, nstep),
                               kOperandBytes, &full[s]);
                 issued = j + 1;
             }
@@ -263,7 +293,9 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
     } else if (warp == 1) {
         // ---- MMA issuer ----
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16_f32(kTile, kTile);
+            constexpr uint32_t idesc = idesc_bf16_f32(kTile, C::kN);
+            // this CTA's kN B columns start kN / 8 core matrices into the blob
+            const unsigned boff = (unsigned)(hf * (C::kN / 8) * kSbo);
             for (long st = st0; st < st1 && !abort_flag; ++st) {
                 const long j = st - st0;
                 const int s = (int)(j % kStages);
@@ -284,21 +316,21 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                 const unsigned char *a = smem + (size_t)s * kStageBytes;
                 const unsigned char *b = one ? a : a + kOperandBytes;
 #pragma unroll
-                for (int ks = 0; ks < kStep / 16; ++ks) {
+                for (int ks = 0; ks < C::kStep / 16; ++ks) {
 #pragma unroll
-                    for (int sa = 0; sa < kDigits; ++sa) {
+                    for (int sa = 0; sa < C::kDigits; ++sa) {
 #pragma unroll
-                        for (int sb = 0; sb < kDigits; ++sb) {
+                        for (int sb = 0; sb < C::kDigits; ++sb) {
                             const int w = sa + sb;
-                            if (w >= kClasses) continue;
+                            if (w >= C::kClasses) continue;
                             // in this loop order the first product of every class is the one
                             // with sa = 0; at the start of a chunk it overwrites the accumulator
                             const bool first = kin == 0 && ks == 0 && sa == 0;
-                            const uint64_t ad =
-                                smem_desc(a + sa * kBlobElems * 2 + ks * 2 * kLbo, kLbo, kSbo);
-                            const uint64_t bd =
-                                smem_desc(b + sb * kBlobElems * 2 + ks * 2 * kLbo, kLbo, kSbo);
-                            tc_mma_bf16(tmem + (uint32_t)(w * kTile), ad, bd, idesc, !first);
+                            const uint64_t ad = smem_desc(
+                                a + sa * Dm::kBlobElems * 2 + ks * 2 * kLbo, kLbo, kSbo);
+                            const uint64_t bd = smem_desc(
+                                b + sb * Dm::kBlobElems * 2 + ks * 2 * kLbo + boff, kLbo, kSbo);
+                            tc_mma_bf16(tmem + (uint32_t)(w * C::kN), ad, bd, idesc, !first);
                         }
                     }
                 }
@@ -312,7 +344,7 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
     } else {
         // ---- epilogue: flush each chunk's class accumulators into FP32-pair sums ----
         const int q = warp & 3;                 // tensor-memory lane quarter of this warp
-        const int half = (warp - 2) >> 2;       // columns 64 half .. 64 half + 63
+        const int hw = (warp - 2) >> 2;         // columns kEpiCols hw .. of this CTA's kN
         const int r = q * 32 + lane;            // tile row = A column within the block
         const int colA = tb.x * kTile + r;
         float H[kEpiCols];
@@ -332,25 +364,30 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
             }
             tc_fence_after();
             const float fA = pow2_factor(EA[c * ns_pad + colA]);
-            const int *eb = EB + c * ns_pad + tb.y * kTile + half * 64;
+            const int *eb = EB + c * ns_pad + tb.y * kTile + hf * C::kN + hw * kEpiCols;
 #pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 64 + g * 8);
-                uint32_t v0[8], v1[8], v2[8];
-                tmem_ld8(ta, v0);
-                tmem_ld8(ta + kTile, v1);
-                tmem_ld8(ta + 2 * kTile, v2);
+            for (int g = 0; g < kEpiCols / 8; ++g) {
+                const uint32_t ta =
+                    tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hw * kEpiCols + g * 8);
+                uint32_t v[C::kClasses][8];
+#pragma unroll
+                for (int w = 0; w < C::kClasses; ++w) tmem_ld8(ta + (uint32_t)(w * C::kN), v[w]);
                 tmem_wait_ld();
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const float a0 = __uint_as_float(v0[u]);
-                    const float a1 = __uint_as_float(v1[u]) * 0.00390625f;      // 2^-8
-                    const float a2 = __uint_as_float(v2[u]) * 1.52587890625e-05f;  // 2^-16
-                    float h, l, h2, l2;
-                    two_sum_f(a0, a1, h, l);
-                    two_sum_f(h, a2, h2, l2);
+                    // sum_w class_w 2^(-8 w) as a pair (each class value is an exact integer)
+                    float h = __uint_as_float(v[0][u]), l = 0.0f;
+                    float wt = 1.0f;
+#pragma unroll
+                    for (int w = 1; w < C::kClasses; ++w) {
+                        wt *= 0.00390625f;  // 2^-8
+                        float t, e2;
+                        two_sum_f(h, __uint_as_float(v[w][u]) * wt, t, e2);
+                        h = t;
+                        l += e2;
+                    }
                     const float f = fA * pow2_factor(eb[g * 8 + u]);
-                    const float ph = h2 * f, pl = (l + l2) * f;
+                    const float ph = h * f, pl = l * f;
                     float sh, se;
                     two_sum_f(H[g * 8 + u], ph, sh, se);
                     H[g * 8 + u] = sh;
@@ -361,7 +398,8 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty);
         }
-        double *o = part + ((long)split * ntiles + tile) * kTile * kTile + (long)r * kTile + half * 64;
+        double *o = part + ((long)split * ntiles + tile) * kTile * kTile + (long)r * kTile +
+                    hf * C::kN + hw * kEpiCols;
 #pragma unroll
         for (int u = 0; u < kEpiCols; ++u) o[u] = (double)H[u] + (double)Lw[u * 32];
     }
@@ -402,19 +440,21 @@ struct TcPlan {
     size_t digits_bytes, exps_bytes, part_bytes, tiles_bytes;
 };
 
+template <class C>
 TcPlan tc_plan(long nd, int ns, bool sym)
 {
     TcPlan p;
     p.nblk = (ns + kTile - 1) / kTile;
     p.ns_pad = p.nblk * kTile;
-    p.nchunk = (nd + kChunk - 1) / kChunk;
-    p.nstep = p.nchunk * kStepsPerChunk;
+    p.nchunk = (nd + C::kChunk - 1) / C::kChunk;
+    p.nstep = p.nchunk * TcDims<C>::kStepsPerChunk;
     p.ntiles = sym ? p.nblk * (p.nblk + 1) / 2 : p.nblk * p.nblk;
-    long s = (152 + p.ntiles - 1) / p.ntiles;
+    const long ctas = (long)p.ntiles * TcDims<C>::kHalves;
+    long s = (152 + ctas - 1) / ctas;
     if (s > p.nchunk) s = p.nchunk;
     if (s < 1) s = 1;
     p.nsplit = (int)s;
-    p.digits_bytes = (size_t)kDigits * p.ns_pad * p.nstep * kStep * 2;
+    p.digits_bytes = (size_t)C::kDigits * p.ns_pad * p.nstep * C::kStep * 2;
     p.exps_bytes = (size_t)p.nchunk * p.ns_pad * sizeof(int);
     p.part_bytes = (size_t)p.nsplit * p.ntiles * kTile * kTile * sizeof(double);
     p.tiles_bytes = (size_t)p.ntiles * sizeof(int2);
@@ -422,35 +462,43 @@ TcPlan tc_plan(long nd, int ns, bool sym)
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
-}  // namespace
 
-size_t gram_tc_workspace(long nd, int ns, bool same_operand, bool sym)
+template <class C>
+size_t tc_workspace(long nd, int ns, bool same_operand, bool sym)
 {
-    const TcPlan p = tc_plan(nd, ns, sym);
+    const TcPlan p = tc_plan<C>(nd, ns, sym);
     const int nops = same_operand ? 1 : 2;
     return nops * (align256(p.digits_bytes) + align256(p.exps_bytes)) + align256(p.part_bytes) +
            align256(p.tiles_bytes);
 }
+}  // namespace
 
-template <typename T>
+size_t gram_tc_workspace(long nd, int ns, bool same_operand, bool sym)
+{
+    return tc_workspace<Tc23>(nd, ns, same_operand, sym);
+}
+size_t gram_tc47_workspace(long nd, int ns) { return tc_workspace<Tc47>(nd, ns, false, true); }
+
+template <class C, typename T>
 static cudaError_t tc_digits(const T *X, long ld, long nd, int ns, const TcPlan &p,
                              __nv_bfloat16 *D, int *E, cudaStream_t st)
 {
     if (p.nchunk > 65535) return cudaErrorInvalidValue;
     dim3 grid(p.ns_pad / 8, (unsigned)p.nchunk);
-    k_tc_digits<T><<<grid, 256, 0, st>>>(X, ld, nd, ns, p.nstep, D, E, p.ns_pad);
+    k_tc_digits<C, T><<<grid, 256, 0, st>>>(X, ld, nd, ns, p.nstep, D, E, p.ns_pad);
     note_launch();
     return cudaGetLastError();
 }
 
 // Tile list (host-built, uploaded) and the kernel's shared-memory attribute.
+template <class C>
 static cudaError_t tc_prepare(const TcPlan &p, bool sym, int2 *tiles, cudaStream_t st)
 {
     static bool attr_set = false;
     cudaError_t e;
     if (!attr_set) {
-        e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmemBytes);
+        e = cudaFuncSetAttribute(k_gram_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TcDims<C>::kSmemBytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -462,13 +510,15 @@ static cudaError_t tc_prepare(const TcPlan &p, bool sym, int2 *tiles, cudaStream
     return cudaMemcpyAsync(tiles, host_tiles, p.tiles_bytes, cudaMemcpyHostToDevice, st);
 }
 
+template <class C>
 static cudaError_t tc_run(const TcPlan &p, const __nv_bfloat16 *DA, const int *EA,
                           const __nv_bfloat16 *DB, const int *EB, const int2 *tiles,
                           double *part, int ns, bool sym, double *G, int *err, cudaStream_t st)
 {
-    k_gram_tc<<<p.ntiles * p.nsplit, kThreads, kSmemBytes, st>>>(DA, EA, DB, EB, p.ns_pad, p.nstep,
-                                                                  tiles, p.ntiles, p.nsplit, part,
-                                                                  err);
+    const int ctas = p.ntiles * p.nsplit * TcDims<C>::kHalves;
+    k_gram_tc<C><<<ctas, kThreads, TcDims<C>::kSmemBytes, st>>>(DA, EA, DB, EB, p.ns_pad, p.nstep,
+                                                                tiles, p.ntiles, p.nsplit, part,
+                                                                err);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -477,14 +527,15 @@ static cudaError_t tc_run(const TcPlan &p, const __nv_bfloat16 *DA, const int *E
     return cudaGetLastError();
 }
 
-template <typename TA, typename TB>
-cudaError_t gram_tc(const TA *A, long lda, const TB *B, long ldb, long nd, int ns, double *G,
-                    void *ws, size_t ws_bytes, bool sym, int *err, cudaStream_t st)
+template <class C, typename TA, typename TB>
+static cudaError_t gram_tc_impl(const TA *A, long lda, const TB *B, long ldb, long nd, int ns,
+                                double *G, void *ws, size_t ws_bytes, bool sym, int *err,
+                                cudaStream_t st)
 {
     if (ns <= 0 || nd <= 0) return cudaErrorInvalidValue;
     const bool same = (const void *)A == (const void *)B && sizeof(TA) == sizeof(TB) && lda == ldb;
-    const TcPlan p = tc_plan(nd, ns, sym);
-    if (ws_bytes < gram_tc_workspace(nd, ns, same, sym)) return cudaErrorInvalidValue;
+    const TcPlan p = tc_plan<C>(nd, ns, sym);
+    if (ws_bytes < tc_workspace<C>(nd, ns, same, sym)) return cudaErrorInvalidValue;
     unsigned char *w = (unsigned char *)ws;
     auto take = [&](size_t b) {
         unsigned char *r = w;
@@ -503,20 +554,20 @@ cudaError_t gram_tc(const TA *A, long lda, const TB *B, long ldb, long nd, int n
     int2 *tiles = (int2 *)take(p.tiles_bytes);
 
     cudaError_t e;
-    if ((e = tc_prepare(p, sym, tiles, st)) != cudaSuccess) return e;
-    if ((e = tc_digits<TA>(A, lda, nd, ns, p, DA, EA, st)) != cudaSuccess) return e;
-    if (!same && (e = tc_digits<TB>(B, ldb, nd, ns, p, DB, EB, st)) != cudaSuccess) return e;
-    return tc_run(p, DA, EA, DB, EB, tiles, part, ns, sym, G, err, st);
+    if ((e = tc_prepare<C>(p, sym, tiles, st)) != cudaSuccess) return e;
+    if ((e = tc_digits<C, TA>(A, lda, nd, ns, p, DA, EA, st)) != cudaSuccess) return e;
+    if (!same && (e = tc_digits<C, TB>(B, ldb, nd, ns, p, DB, EB, st)) != cudaSuccess) return e;
+    return tc_run<C>(p, DA, EA, DB, EB, tiles, part, ns, sym, G, err, st);
 }
 
-template <typename TA, typename TB>
-cudaError_t gram_tc_pair(const TA *A, long lda, const TB *B, long ldb, long nd, int ns,
-                         double *M, double *Hm, void *ws, size_t ws_bytes, int *err,
-                         cudaStream_t st)
+template <class C, typename TA, typename TB>
+static cudaError_t gram_tc_pair_impl(const TA *A, long lda, const TB *B, long ldb, long nd,
+                                     int ns, double *M, double *Hm, void *ws, size_t ws_bytes,
+                                     int *err, cudaStream_t st)
 {
     if (ns <= 0 || nd <= 0) return cudaErrorInvalidValue;
-    const TcPlan p = tc_plan(nd, ns, true);
-    if (ws_bytes < gram_tc_workspace(nd, ns, false, true)) return cudaErrorInvalidValue;
+    const TcPlan p = tc_plan<C>(nd, ns, true);
+    if (ws_bytes < tc_workspace<C>(nd, ns, false, true)) return cudaErrorInvalidValue;
     unsigned char *w = (unsigned char *)ws;
     auto take = [&](size_t b) {
         unsigned char *r = w;
@@ -530,12 +581,35 @@ cudaError_t gram_tc_pair(const TA *A, long lda, const TB *B, long ldb, long nd, 
     double *part = (double *)take(p.part_bytes);
     int2 *tiles = (int2 *)take(p.tiles_bytes);
     cudaError_t e;
-    if ((e = tc_prepare(p, true, tiles, st)) != cudaSuccess) return e;
-    if ((e = tc_digits<TA>(A, lda, nd, ns, p, DA, EA, st)) != cudaSuccess) return e;
-    if ((e = tc_digits<TB>(B, ldb, nd, ns, p, DB, EB, st)) != cudaSuccess) return e;
-    if ((e = tc_run(p, DA, EA, DA, EA, tiles, part, ns, true, M, err, st)) != cudaSuccess)
+    if ((e = tc_prepare<C>(p, true, tiles, st)) != cudaSuccess) return e;
+    if ((e = tc_digits<C, TA>(A, lda, nd, ns, p, DA, EA, st)) != cudaSuccess) return e;
+    if ((e = tc_digits<C, TB>(B, ldb, nd, ns, p, DB, EB, st)) != cudaSuccess) return e;
+    if ((e = tc_run<C>(p, DA, EA, DA, EA, tiles, part, ns, true, M, err, st)) != cudaSuccess)
         return e;
-    return tc_run(p, DA, EA, DB, EB, tiles, part, ns, true, Hm, err, st);
+    return tc_run<C>(p, DA, EA, DB, EB, tiles, part, ns, true, Hm, err, st);
+}
+
+template <typename TA, typename TB>
+cudaError_t gram_tc(const TA *A, long lda, const TB *B, long ldb, long nd, int ns, double *G,
+                    void *ws, size_t ws_bytes, bool sym, int *err, cudaStream_t st)
+{
+    return gram_tc_impl<Tc23, TA, TB>(A, lda, B, ldb, nd, ns, G, ws, ws_bytes, sym, err, st);
+}
+
+template <typename TA, typename TB>
+cudaError_t gram_tc_pair(const TA *A, long lda, const TB *B, long ldb, long nd, int ns,
+                         double *M, double *Hm, void *ws, size_t ws_bytes, int *err,
+                         cudaStream_t st)
+{
+    return gram_tc_pair_impl<Tc23, TA, TB>(A, lda, B, ldb, nd, ns, M, Hm, ws, ws_bytes, err, st);
+}
+
+cudaError_t gram_tc47_pair(const double *A, long lda, const double *B, long ldb, long nd, int ns,
+                           double *M, double *Hm, void *ws, size_t ws_bytes, int *err,
+                           cudaStream_t st)
+{
+    return gram_tc_pair_impl<Tc47, double, double>(A, lda, B, ldb, nd, ns, M, Hm, ws, ws_bytes,
+                                                   err, st);
 }
 
 template cudaError_t gram_tc_pair<float, double>(const float *, long, const double *, long, long,

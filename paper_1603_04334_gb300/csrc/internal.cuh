@@ -225,13 +225,9 @@ cudaError_t rotate_f64_df(const double *A, long lda, long nd, int ns, const doub
                           long ldo, cudaStream_t st);
 // FP64 Gram with a caller-chosen number of row slices (part: nsplit * ns * ns doubles).
 int gram_default_splits(int ns, long nd);
-// G = A^T B for FP64 blocks on the column grids of bA, bB (bounds as for stencil_f64),
-// integer and FP32 arithmetic (gram_fx.cu); part: gram_part_elems(ns, nd) doubles.
-cudaError_t gram_f64_fx(const double *A, long lda, const unsigned *bA, const double *B,
-                        long ldb, const unsigned *bB, long nd, int ns, double *G, double *part,
-                        cudaStream_t st, bool sym);
-// out = A C (C: ns x ns FP64, column-major) for an FP64 block A with column bounds bA, in
-// the same arithmetic; ws: rotate_fx_workspace(ns) bytes of device memory.
+// out = A C (C: ns x ns FP64, column-major) for an FP64 block A with column bounds bA (as
+// for stencil_f64), integer and FP32 arithmetic (rotate_fx.cu); ws: rotate_fx_workspace(ns)
+// bytes of device memory.
 size_t rotate_fx_workspace(int ns);
 cudaError_t rotate_f64_fx(const double *A, long lda, const unsigned *bA, long nd, int ns,
                           const double *C, double *out, long ldo, void *ws, cudaStream_t st);
@@ -241,6 +237,12 @@ cudaError_t rotate_f64_fx(const double *A, long lda, const unsigned *bA, long nd
 // diagonal and mirrors them. ws: at least gram_tc_workspace(nd, ns, A == B, sym) bytes,
 // 256-byte aligned. A bounded wait that expires sets *err.
 size_t gram_tc_workspace(long nd, int ns, bool same_operand, bool sym);
+// The same contractions for FP64 blocks in the 47-bit form (six digits per entry, classes
+// 0..5): M = A^T A and Hm = A^T B, both symmetric; ws: gram_tc47_workspace(nd, ns) bytes.
+size_t gram_tc47_workspace(long nd, int ns);
+cudaError_t gram_tc47_pair(const double *A, long lda, const double *B, long ldb, long nd, int ns,
+                           double *M, double *Hm, void *ws, size_t ws_bytes, int *err,
+                           cudaStream_t st);
 template <typename TA, typename TB>
 cudaError_t gram_tc(const TA *A, long lda, const TB *B, long ldb, long nd, int ns, double *G,
                     void *ws, size_t ws_bytes, bool sym, int *err, cudaStream_t st);

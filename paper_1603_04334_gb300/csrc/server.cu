@@ -244,15 +244,21 @@ size_t sparc_request_bytes(const sparc_request *q)
     const size_t per_entry = 4 + 4 + 32 + 32 + 16 + 16 + 32 + 4 + 4 + 16 + 32 + 16;
     const size_t entries = na * (size_t)nodes_in_support_box(q->h, 3.0);
     size_t b = per_node * (size_t)nd + per_entry * entries + 4096 * 64;
-    // workspaces: projection coefficients, H Y_f (FP64), rotated H X (residuals), Gram
-    // partials (FP64 form) or the tensor-core Gram (mixed form), Ns x Ns matrices, Lanczos
+    // workspaces: projection coefficients, H Y_f (FP64), rotated H X (residuals), the
+    // tensor-core Gram of either form, Ns x Ns matrices, Lanczos
     b += sizeof(double) * 4 * na * ns;
     b += sizeof(double) * (size_t)nd * ns;
     b += es * (size_t)nd * ns;
-    if (q->dtype == SPARC_F32)
+    if (q->dtype == SPARC_F32) {
         b += gram_tc_workspace(nd, ns, false, true);
-    else
-        b += sizeof(double) * (size_t)gram_part_elems(ns, nd);
+    } else {
+        // 47-bit tensor-core Gram, column bounds of the filter's blocks and of H Y_f,
+        // V_eff - shift pairs, grid form of the rotation matrix
+        b += gram_tc47_workspace(nd, ns);
+        b += sizeof(unsigned) * ((size_t)(q->degree + 1) * ns + 2 * (size_t)ns);
+        b += 8 * (size_t)nd;
+        b += rotate_fx_workspace(ns);
+    }
     b += sizeof(double) * (4 * (size_t)ns * ns + 2 * (size_t)ns + (size_t)dense_work_elems(ns));
     b += sizeof(double) * (3 * (size_t)nd + kDotBlocks + 4096);
     // the request's two orbital blocks

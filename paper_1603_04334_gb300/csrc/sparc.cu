@@ -410,7 +410,7 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
         HX = (double *)ctx->hx;
     }
     // H Yf in FP64. FP64 blocks: column bounds of Yf (one pass) and of H Yf (raised by its
-    // application) for the integer-arithmetic Gram
+    // application) for the rotations on the fixed-point grids
     unsigned *bY = nullptr, *bH = nullptr;
     if (sizeof(T) == 8) {
         TRY(ensure(ctx, ctx->bsc, ctx->bsc_bytes, sizeof(unsigned) * 2 * (size_t)ns));
@@ -425,11 +425,10 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
     // M_s = Yf^T Yf, H_s = Yf^T (H Yf)
     DenseBufs d;
     TRY(dense_bufs(ctx, ns, d));
-    TRY(ensure(ctx, ctx->part, ctx->part_bytes, sizeof(double) * (size_t)gram_part_elems(ns, nd)));
-    double *part = (double *)ctx->part;
     if (sizeof(T) == 8) {
-        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64_fx((const double *)Yf, ld, bY, (const double *)Yf, ld, bY, nd, ns, d.M, part, ctx->st, true)); }
-        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64_fx((const double *)Yf, ld, bY, HX, ld, bH, nd, ns, d.Hs, part, ctx->st, true)); }
+        // both contractions on the tensor cores in the 47-bit digit form (gram_tc.cu)
+        TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, gram_tc47_workspace(nd, ns)));
+        { PHASE(SPARC_PHASE_GRAM); CK(gram_tc47_pair((const double *)Yf, ld, HX, ld, nd, ns, d.M, d.Hs, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st)); }
     } else {
         // mixed-precision form: both contractions on the tensor cores (gram_tc.cu)
         TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, gram_tc_workspace(nd, ns, false, true)));
