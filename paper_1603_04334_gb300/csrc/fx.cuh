@@ -1,7 +1,7 @@
 // fx.cuh -- per-column magnitude bounds of FP64 blocks and the fixed-point grid they
-// define, shared by the FP64 stencil (stencil_df.cu), the FP64 rotation (rotate_fx.cu),
-// the pair scatter (nonlocal.cu) and the bound pass (bounds.cu). A bound is the largest
-// high word (bits 32..62) of |y| over a column; it only grows.
+// define, shared by the FP64 stencil (stencil_df.cu), the pair scatter (nonlocal.cu) and
+// the bound pass (bounds.cu). A bound is the largest high word (bits 32..62) of |y| over a
+// column; it only grows.
 #pragma once
 #include <cuda_runtime.h>
 

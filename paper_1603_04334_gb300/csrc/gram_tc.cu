@@ -206,15 +206,117 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e)
     e = (a - (s - bb)) + (b - bb);
 }
 
+// FP32 -> FP64 by moving the exponent field (integer operations; FP32 subnormals count as
+// zero, Inf / NaN stay so): the rotation writes one output per thread and column, where an
+// FP64 conversion instruction per value would load the FP64 pipe.
+__device__ __forceinline__ double widen_int(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu, sg = u & 0x80000000u;
+    unsigned hi = sg | ((e + 896u) << 20) | (m >> 3), lo = m << 29;
+    if (e == 0u) hi = sg, lo = 0u;
+    if (e == 0xffu) hi = sg | 0x7ff00000u | (m ? 0x80000u : 0u), lo = 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// Digits of the transposed operand: B = Y^T for the rotation, so the K dimension runs over
+// Y's columns and each Y row gets its own exponent per chunk of kChunk columns. CTA: 32
+// rows (lanes) x the chunk's kChunk / 8 groups of 8 columns (warps): loads are coalesced
+// across lanes, the row's largest entry is reduced through shared memory, and each thread
+// writes its 8 values of a digit as one 16-byte store (the 8 K-adjacent elements of a core
+// matrix row are contiguous, and the 32 rows of a warp fill 512 contiguous bytes). Rows past
+// nd and columns past ns are zero.
+template <class C>
+__global__ void __launch_bounds__(32 * (C::kChunk / 8))
+k_tc_digits_t(const double *__restrict__ Y, long ld, long nd, int ns, long nstep,
+              __nv_bfloat16 *__restrict__ D, int *__restrict__ E, long nd_pad)
+{
+    using B = FBits<double>;
+    using U = B::U;
+    constexpr int G = C::kChunk / 8;  // column groups (warps)
+    __shared__ U red[G][32];
+    __shared__ int bad_s[G][32];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const long row = (long)blockIdx.x * 32 + lane;
+    const long chunk = blockIdx.y;
+    const int kb = (int)(chunk * C::kChunk) + g * 8;  // first column of this thread's group
+    const bool live = row < nd;
+    double x[8];
+    U mx = 0;
+    int bad = 0;
+    const U inf = (U)B::kExpMask << B::kMant;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        x[t] = (live && kb + t < ns) ? Y[row + (long)(kb + t) * ld] : 0.0;
+        const U m = B::mag(x[t]);
+        bad |= m >= inf;
+        mx = m > mx ? m : mx;
+    }
+    red[g][lane] = mx;
+    bad_s[g][lane] = bad;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+        mx = red[q][lane] > mx ? red[q][lane] : mx;
+        bad |= bad_s[q][lane];
+    }
+    const int bxm = (int)(mx >> B::kMant);
+    const int e = mx == 0 ? 0 : (bxm == 0 ? 2 - B::kBias : bxm - B::kBias + 1);
+    if (g == 0 && row < nd_pad) E[chunk * nd_pad + row] = bad ? kNonFinite : e;
+    if (row >= nd_pad) return;
+    int d[C::kDigits][8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const U mag = B::mag(x[t]);
+        long N = 0;
+        if (!bad && mag != 0) {
+            const int bx = (int)(mag >> B::kMant);
+            const U m = (mag & (((U)1 << B::kMant) - 1)) | (bx ? ((U)1 << B::kMant) : 0);
+            const int ebx = bx ? bx : 1;
+            const int sh = e + B::kBias + B::kMant - C::kBits - ebx;
+            if (sh <= 0)
+                N = (long)m << (-sh);
+            else if (sh < 64)
+                N = (long)((m + ((U)1 << (sh - 1))) >> sh);
+        }
+        const int sg = B::neg(x[t]) ? -1 : 1;
+#pragma unroll
+        for (int s2 = C::kDigits - 1; s2 > 0; --s2) {
+            const int v = (int)(((N + 128) & 255) - 128);
+            d[s2][t] = sg * v;
+            N = (N - v) >> 8;
+        }
+        d[0][t] = sg * (int)N;
+    }
+    // the 8 columns kb .. kb+7 lie in one K-step (kStep is a multiple of 8) and one core
+    const int cb = (int)(row >> 7), c = (int)(row & 127);
+    const long base = blob_offset<C>(cb, kb / C::kStep, 0, nstep) + in_blob(kb % C::kStep, c);
+#pragma unroll
+    for (int s2 = 0; s2 < C::kDigits; ++s2) {
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = __float2bfloat16_rn((float)d[s2][t]);
+        *reinterpret_cast<uint4 *>(D + base + (long)s2 * TcDims<C>::kBlobElems) =
+            *reinterpret_cast<const uint4 *>(v);
+    }
+}
+
 // tiles[t] = (A column block, B column block); a tile is computed by kHalves CTAs, each
 // for kN of its 128 B columns. part: nsplit x ntiles x 128 x 128 doubles, element (r, c) of
 // a tile at r * 128 + c (r: A column, c: B column).
-template <class C>
+// Work units: a unit is one tile half (kN of the tile's 128 B columns) over a range of
+// chunks. Gram mode: CTA b owns unit b (units = halves x tiles x splits). ROT (the rotation,
+// see rotate_tc below): tile t is (t % mblk, t / mblk) over all chunks, the CTAs are
+// persistent and walk units b, b + gridDim.x, ... with the ring, the MMAs and the epilogue
+// running on across units; B's exponents have the row stride eb_ld, and the epilogue
+// writes out[i + j ldo] (i: B column, j: A column) for i < nrow, j < ncol.
+template <class C, bool ROT>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
           const __nv_bfloat16 *__restrict__ DB, const int *__restrict__ EB, int ns_pad, long nstep,
           const int2 *__restrict__ tiles, int ntiles, int nsplit, double *__restrict__ part,
-          int *err)
+          int *err, int eb_ld = 0, int mblk = 1, double *__restrict__ out = nullptr, long ldo = 0,
+          long nrow = 0, int ncol = 0)
 {
     using Dm = TcDims<C>;
     constexpr int kStages = C::kStages, kStepsPerChunk = Dm::kStepsPerChunk;
@@ -228,15 +330,26 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
     unsigned char *smem =
         (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int hf = blockIdx.x % Dm::kHalves;
-    const int tile = (blockIdx.x / Dm::kHalves) % ntiles;
-    const int split = blockIdx.x / (Dm::kHalves * ntiles);
-    const int2 tb = tiles[tile];
     const long nchunk = nstep / kStepsPerChunk;
-    const long c0 = (long)split * nchunk / nsplit, c1 = (long)(split + 1) * nchunk / nsplit;
-    const long st0 = c0 * kStepsPerChunk, st1 = c1 * kStepsPerChunk;
-    // a diagonal tile of A^T A reads one operand: B's descriptors point at A's blobs
-    const bool one = DA == DB && tb.x == tb.y;
+    const int nunits = ROT ? ntiles * Dm::kHalves : (int)gridDim.x;
+    const int ustride = ROT ? (int)gridDim.x : nunits;
+    struct Unit {
+        int hf, tile, split;
+        int2 tb;
+        long c0, c1;
+        bool one;  // a diagonal tile of A^T A reads one operand: B's descriptors use A's blobs
+    };
+    auto unit = [&](int u) {
+        Unit w;
+        w.hf = u % Dm::kHalves;
+        w.tile = (u / Dm::kHalves) % ntiles;
+        w.split = u / (Dm::kHalves * ntiles);
+        w.tb = ROT ? make_int2(w.tile % mblk, w.tile / mblk) : tiles[w.tile];
+        w.c0 = ROT ? 0 : (long)w.split * nchunk / nsplit;
+        w.c1 = ROT ? nchunk : (long)(w.split + 1) * nchunk / nsplit;
+        w.one = !ROT && DA == DB && w.tb.x == w.tb.y;
+        return w;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -261,30 +374,34 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
     };
 
     if (warp == 0) {
-        // ---- producer: A and B blobs of each step into the ring ----
+        // ---- producer: A and B blobs of each step into the ring, unit after unit ----
         if (lane == 0) {
-            long issued = 0;
-            for (long st = st0; st < st1 && !abort_flag; ++st) {
-                const long j = st - st0;
-                const int s = (int)(j % kStages);
-                if (j >= kStages &&
-                    !mbar_wait(&empty[s], (unsigned)(((j / kStages) & 1) ^ 1), kWaitLimit)) {
-                    fail();
-                    break;
+            long j = 0, issued = 0;  // steps handed to the ring over all units
+            for (int u = blockIdx.x; u < nunits && !abort_flag; u += ustride) {
+                const Unit w = unit(u);
+                for (long st = w.c0 * kStepsPerChunk; st < w.c1 * kStepsPerChunk && !abort_flag;
+                     ++st, ++j) {
+                    const int s = (int)(j % kStages);
+                    if (j >= kStages &&
+                        !mbar_wait(&empty[s], (unsigned)(((j / kStages) & 1) ^ 1), kWaitLimit)) {
+                        fail();
+                        break;
+                    }
+                    unsigned char *dst = smem + (size_t)s * kStageBytes;
+                    mbar_arrive_expect_tx(&full[s], w.one ? kOperandBytes : kStageBytes);
+                    bulk_load(dst, DA + blob_offset<C>(w.tb.x, st, 0, nstep), kOperandBytes,
+                              &full[s]);
+                    if (!w.one)
+                        bulk_load(dst + kOperandBytes, DB + blob_offset<C>(w.tb.y, st, 0, nstep),
+                                  kOperandBytes, &full[s]);
+                    issued = j + 1;
                 }
-                unsigned char *dst = smem + (size_t)s * kStageBytes;
-                mbar_arrive_expect_tx(&full[s], one ? kOperandBytes : kStageBytes);
-                bulk_load(dst, DA + blob_offset<C>(tb.x, st, 0, nstep), kOperandBytes, &full[s]);
-                if (!one)
-                    bulk_load(dst + kOperandBytes, DB + blob_offset<C>(tb.y, st, 0, nstep),
-                              kOperandBytes, &full[s]);
-                issued = j + 1;
             }
             if (abort_flag) {
                 // wait (bounded) for the last copy issued into each stage
                 for (int s = 0; s < kStages; ++s) {
                     long last = -1;
-                    for (long j = s; j < issued; j += kStages) last = j;
+                    for (long q = s; q < issued; q += kStages) last = q;
                     if (last >= 0)
                         mbar_wait(&full[s], (unsigned)((last / kStages) & 1), kWaitLimit);
                 }
@@ -294,48 +411,54 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
         // ---- MMA issuer ----
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16_f32(kTile, C::kN);
-            // this CTA's kN B columns start kN / 8 core matrices into the blob
-            const unsigned boff = (unsigned)(hf * (C::kN / 8) * kSbo);
-            for (long st = st0; st < st1 && !abort_flag; ++st) {
-                const long j = st - st0;
-                const int s = (int)(j % kStages);
-                const int kin = (int)(j % kStepsPerChunk);
-                const long chunk = j / kStepsPerChunk;
-                if (kin == 0 && chunk > 0) {
-                    if (!mbar_wait(&acc_empty, (unsigned)((chunk - 1) & 1), kWaitLimit)) {
+            long j = 0, cc = 0;  // steps and chunks over all units
+            for (int u = blockIdx.x; u < nunits && !abort_flag; u += ustride) {
+                const Unit w = unit(u);
+                // this unit's kN B columns start kN / 8 core matrices into the blob
+                const unsigned boff = (unsigned)(w.hf * (C::kN / 8) * kSbo);
+                const long st0 = w.c0 * kStepsPerChunk;
+                for (long st = st0; st < w.c1 * kStepsPerChunk && !abort_flag; ++st, ++j) {
+                    const int s = (int)(j % kStages);
+                    const int kin = (int)((st - st0) % kStepsPerChunk);
+                    if (kin == 0 && cc > 0) {
+                        if (!mbar_wait(&acc_empty, (unsigned)((cc - 1) & 1), kWaitLimit)) {
+                            fail();
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    if (!mbar_wait(&full[s], (unsigned)((j / kStages) & 1), kWaitLimit)) {
                         fail();
                         break;
                     }
                     tc_fence_after();
-                }
-                if (!mbar_wait(&full[s], (unsigned)((j / kStages) & 1), kWaitLimit)) {
-                    fail();
-                    break;
-                }
-                tc_fence_after();
-                const unsigned char *a = smem + (size_t)s * kStageBytes;
-                const unsigned char *b = one ? a : a + kOperandBytes;
+                    const unsigned char *a = smem + (size_t)s * kStageBytes;
+                    const unsigned char *b = w.one ? a : a + kOperandBytes;
 #pragma unroll
-                for (int ks = 0; ks < C::kStep / 16; ++ks) {
+                    for (int ks = 0; ks < C::kStep / 16; ++ks) {
 #pragma unroll
-                    for (int sa = 0; sa < C::kDigits; ++sa) {
+                        for (int sa = 0; sa < C::kDigits; ++sa) {
 #pragma unroll
-                        for (int sb = 0; sb < C::kDigits; ++sb) {
-                            const int w = sa + sb;
-                            if (w >= C::kClasses) continue;
-                            // in this loop order the first product of every class is the one
-                            // with sa = 0; at the start of a chunk it overwrites the accumulator
-                            const bool first = kin == 0 && ks == 0 && sa == 0;
-                            const uint64_t ad = smem_desc(
-                                a + sa * Dm::kBlobElems * 2 + ks * 2 * kLbo, kLbo, kSbo);
-                            const uint64_t bd = smem_desc(
-                                b + sb * Dm::kBlobElems * 2 + ks * 2 * kLbo + boff, kLbo, kSbo);
-                            tc_mma_bf16(tmem + (uint32_t)(w * C::kN), ad, bd, idesc, !first);
+                            for (int sb = 0; sb < C::kDigits; ++sb) {
+                                const int cl = sa + sb;
+                                if (cl >= C::kClasses) continue;
+                                // in this loop order the first product of every class is the
+                                // one with sa = 0; at a chunk start it overwrites the class
+                                const bool first = kin == 0 && ks == 0 && sa == 0;
+                                const uint64_t ad = smem_desc(
+                                    a + sa * Dm::kBlobElems * 2 + ks * 2 * kLbo, kLbo, kSbo);
+                                const uint64_t bd = smem_desc(
+                                    b + sb * Dm::kBlobElems * 2 + ks * 2 * kLbo + boff, kLbo, kSbo);
+                                tc_mma_bf16(tmem + (uint32_t)(cl * C::kN), ad, bd, idesc, !first);
+                            }
                         }
                     }
+                    tc_commit(&empty[s]);  // stage free once these MMAs are done
+                    if (kin == kStepsPerChunk - 1) {
+                        tc_commit(&acc_full);  // chunk complete
+                        ++cc;
+                    }
                 }
-                tc_commit(&empty[s]);                      // stage free once these MMAs are done
-                if (kin == kStepsPerChunk - 1) tc_commit(&acc_full);  // chunk complete
             }
             // all MMAs issued by this thread are complete before tensor memory is freed
             tc_commit(&drain);
@@ -346,62 +469,81 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
         const int q = warp & 3;                 // tensor-memory lane quarter of this warp
         const int hw = (warp - 2) >> 2;         // columns kEpiCols hw .. of this CTA's kN
         const int r = q * 32 + lane;            // tile row = A column within the block
-        const int colA = tb.x * kTile + r;
         float H[kEpiCols];
         float *Lw = reinterpret_cast<float *>(smem + (size_t)kStages * kStageBytes) +
                     (size_t)(warp - 2) * kEpiCols * 32 + lane;  // Lw[u * 32]: column u
+        long cc = 0;  // chunks over all units
+        bool ok = true;
+        for (int u = blockIdx.x; u < nunits && ok; u += ustride) {
+            const Unit w = unit(u);
+            const int colA = w.tb.x * kTile + r;
 #pragma unroll
-        for (int u = 0; u < kEpiCols; ++u) {
-            H[u] = 0.0f;
-            Lw[u * 32] = 0.0f;
-        }
-        for (long c = c0; c < c1; ++c) {
-            bool ok = mbar_wait(&acc_full, (unsigned)((c - c0) & 1), kWaitLimit) && !abort_flag;
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) {
-                if (lane == 0) fail();
-                break;
+            for (int x = 0; x < kEpiCols; ++x) {
+                H[x] = 0.0f;
+                Lw[x * 32] = 0.0f;
             }
-            tc_fence_after();
-            const float fA = pow2_factor(EA[c * ns_pad + colA]);
-            const int *eb = EB + c * ns_pad + tb.y * kTile + hf * C::kN + hw * kEpiCols;
-#pragma unroll
-            for (int g = 0; g < kEpiCols / 8; ++g) {
-                const uint32_t ta =
-                    tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hw * kEpiCols + g * 8);
-                uint32_t v[C::kClasses][8];
-#pragma unroll
-                for (int w = 0; w < C::kClasses; ++w) tmem_ld8(ta + (uint32_t)(w * C::kN), v[w]);
-                tmem_wait_ld();
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    // sum_w class_w 2^(-8 w) as a pair (each class value is an exact integer)
-                    float h = __uint_as_float(v[0][u]), l = 0.0f;
-                    float wt = 1.0f;
-#pragma unroll
-                    for (int w = 1; w < C::kClasses; ++w) {
-                        wt *= 0.00390625f;  // 2^-8
-                        float t, e2;
-                        two_sum_f(h, __uint_as_float(v[w][u]) * wt, t, e2);
-                        h = t;
-                        l += e2;
-                    }
-                    const float f = fA * pow2_factor(eb[g * 8 + u]);
-                    const float ph = h * f, pl = l * f;
-                    float sh, se;
-                    two_sum_f(H[g * 8 + u], ph, sh, se);
-                    H[g * 8 + u] = sh;
-                    Lw[(g * 8 + u) * 32] += se + pl;
+            for (long c = w.c0; c < w.c1; ++c, ++cc) {
+                ok = mbar_wait(&acc_full, (unsigned)(cc & 1), kWaitLimit) && !abort_flag;
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) {
+                    if (lane == 0) fail();
+                    break;
                 }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty);
-        }
-        double *o = part + ((long)split * ntiles + tile) * kTile * kTile + (long)r * kTile +
-                    hf * C::kN + hw * kEpiCols;
+                tc_fence_after();
+                const float fA = pow2_factor(EA[c * ns_pad + colA]);
+                const int *eb = EB + c * (ROT ? eb_ld : ns_pad) + (long)w.tb.y * kTile +
+                                w.hf * C::kN + hw * kEpiCols;
 #pragma unroll
-        for (int u = 0; u < kEpiCols; ++u) o[u] = (double)H[u] + (double)Lw[u * 32];
+                for (int g = 0; g < kEpiCols / 8; ++g) {
+                    const uint32_t ta =
+                        tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hw * kEpiCols + g * 8);
+                    uint32_t v[C::kClasses][8];
+#pragma unroll
+                    for (int cl = 0; cl < C::kClasses; ++cl)
+                        tmem_ld8(ta + (uint32_t)(cl * C::kN), v[cl]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int x = 0; x < 8; ++x) {
+                        // sum_w class_w 2^(-8 w) as a pair (each class value an exact integer)
+                        float h = __uint_as_float(v[0][x]), l = 0.0f;
+                        float wt = 1.0f;
+#pragma unroll
+                        for (int cl = 1; cl < C::kClasses; ++cl) {
+                            wt *= 0.00390625f;  // 2^-8
+                            float t, e2;
+                            two_sum_f(h, __uint_as_float(v[cl][x]) * wt, t, e2);
+                            h = t;
+                            l += e2;
+                        }
+                        const float f = fA * pow2_factor(eb[g * 8 + x]);
+                        const float ph = h * f, pl = l * f;
+                        float sh, se;
+                        two_sum_f(H[g * 8 + x], ph, sh, se);
+                        H[g * 8 + x] = sh;
+                        Lw[(g * 8 + x) * 32] += se + pl;
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty);
+            }
+            if (!ok) break;
+            if (ROT) {
+                const long jc = (long)w.tb.x * kTile + r;
+                const long i0 = (long)w.tb.y * kTile + w.hf * C::kN + hw * kEpiCols;
+                if (jc < ncol) {
+                    double *o = out + i0 + jc * ldo;
+#pragma unroll
+                    for (int x = 0; x < kEpiCols; ++x)
+                        if (i0 + x < nrow) o[x] = widen_int(H[x]) + widen_int(Lw[x * 32]);
+                }
+            } else {
+                double *o = part + ((long)w.split * ntiles + w.tile) * kTile * kTile +
+                            (long)r * kTile + w.hf * C::kN + hw * kEpiCols;
+#pragma unroll
+                for (int x = 0; x < kEpiCols; ++x) o[x] = (double)H[x] + (double)Lw[x * 32];
+            }
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -497,7 +639,7 @@ static cudaError_t tc_prepare(const TcPlan &p, bool sym, int2 *tiles, cudaStream
     static bool attr_set = false;
     cudaError_t e;
     if (!attr_set) {
-        e = cudaFuncSetAttribute(k_gram_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_gram_tc<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TcDims<C>::kSmemBytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -516,7 +658,7 @@ static cudaError_t tc_run(const TcPlan &p, const __nv_bfloat16 *DA, const int *E
                           double *part, int ns, bool sym, double *G, int *err, cudaStream_t st)
 {
     const int ctas = p.ntiles * p.nsplit * TcDims<C>::kHalves;
-    k_gram_tc<C><<<ctas, kThreads, TcDims<C>::kSmemBytes, st>>>(DA, EA, DB, EB, p.ns_pad, p.nstep,
+    k_gram_tc<C, false><<<ctas, kThreads, TcDims<C>::kSmemBytes, st>>>(DA, EA, DB, EB, p.ns_pad, p.nstep,
                                                                 tiles, p.ntiles, p.nsplit, part,
                                                                 err);
     note_launch();
@@ -610,6 +752,89 @@ cudaError_t gram_tc47_pair(const double *A, long lda, const double *B, long ldb,
 {
     return gram_tc_pair_impl<Tc47, double, double>(A, lda, B, ldb, nd, ns, M, Hm, ws, ws_bytes,
                                                    err, st);
+}
+
+// ---- rotation out = Y C on the tensor cores (47-bit digits) ------------------------------
+// Written as the contraction G = A^T B with A = C (K = Ns rows, M = Ns columns) and
+// B = Y^T (N = Nd): G(j, i) = sum_k C_kj Y_ik = out(i, j). C gets exponents per (K chunk,
+// column), Y per (K chunk, row), so every product in a class accumulator shares one scale;
+// K = Ns is short, so each CTA owns one 128 x 64 tile over all of K (no split).
+namespace {
+struct RotPlan {
+    int ns_pad, mblk;
+    long nblk, nd_pad, nchunk, nstep;
+    size_t da_bytes, ea_bytes, db_bytes, eb_bytes;
+};
+RotPlan rot_plan(long nd, int ns)
+{
+    using C = Tc47;
+    RotPlan p;
+    p.mblk = (ns + kTile - 1) / kTile;
+    p.ns_pad = p.mblk * kTile;
+    p.nblk = (nd + kTile - 1) / kTile;
+    p.nd_pad = p.nblk * kTile;
+    p.nchunk = (ns + C::kChunk - 1) / C::kChunk;
+    p.nstep = p.nchunk * TcDims<C>::kStepsPerChunk;
+    p.da_bytes = (size_t)C::kDigits * p.ns_pad * p.nstep * C::kStep * 2;
+    p.ea_bytes = (size_t)p.nchunk * p.ns_pad * sizeof(int);
+    p.db_bytes = (size_t)C::kDigits * p.nd_pad * p.nstep * C::kStep * 2;
+    p.eb_bytes = (size_t)p.nchunk * p.nd_pad * sizeof(int);
+    return p;
+}
+}  // namespace
+
+size_t rotate_tc_workspace(long nd, int ns)
+{
+    const RotPlan p = rot_plan(nd, ns);
+    return align256(p.da_bytes) + align256(p.ea_bytes) + align256(p.db_bytes) +
+           align256(p.eb_bytes);
+}
+
+cudaError_t rotate_tc(const double *Y, long ldy, long nd, int ns, const double *Cm, double *out,
+                      long ldo, void *ws, size_t ws_bytes, int *err, cudaStream_t st)
+{
+    using C = Tc47;
+    if (ns <= 0 || nd <= 0) return cudaSuccess;
+    const RotPlan p = rot_plan(nd, ns);
+    if (ws_bytes < rotate_tc_workspace(nd, ns)) return cudaErrorInvalidValue;
+    const long ctas = (long)p.mblk * p.nblk * TcDims<C>::kHalves;
+    if (p.nchunk > 65535 || ctas > 0x7fffffffL || p.nd_pad / 32 > 0x7fffffffL)
+        return cudaErrorInvalidValue;
+    unsigned char *w = (unsigned char *)ws;
+    auto take = [&](size_t b) {
+        unsigned char *r = w;
+        w += align256(b);
+        return r;
+    };
+    __nv_bfloat16 *DA = (__nv_bfloat16 *)take(p.da_bytes);
+    int *EA = (int *)take(p.ea_bytes);
+    __nv_bfloat16 *DB = (__nv_bfloat16 *)take(p.db_bytes);
+    int *EB = (int *)take(p.eb_bytes);
+    static bool attr_set = false;
+    cudaError_t e;
+    if (!attr_set) {
+        e = cudaFuncSetAttribute(k_gram_tc<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TcDims<C>::kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    {   // A = C: K = Ns rows, M = Ns columns
+        dim3 grid(p.ns_pad / 8, (unsigned)p.nchunk);
+        k_tc_digits<C, double><<<grid, 256, 0, st>>>(Cm, ns, ns, ns, p.nstep, DA, EA, p.ns_pad);
+        note_launch();
+    }
+    {   // B = Y^T: K = Ns (Y's columns), N = Nd (Y's rows)
+        dim3 grid((unsigned)(p.nd_pad / 32), (unsigned)p.nchunk);
+        k_tc_digits_t<C><<<grid, 32 * (C::kChunk / 8), 0, st>>>(Y, ldy, nd, ns, p.nstep, DB, EB,
+                                                               p.nd_pad);
+        note_launch();
+    }
+    const unsigned grid = (unsigned)(ctas < 152 ? ctas : 152);  // persistent, one per SM
+    k_gram_tc<C, true><<<grid, kThreads, TcDims<C>::kSmemBytes, st>>>(
+        DA, EA, DB, EB, p.ns_pad, p.nstep, nullptr, (int)(p.mblk * p.nblk), 1, nullptr, err,
+        (int)p.nd_pad, p.mblk, out, ldo, nd, ns);
+    note_launch();
+    return cudaGetLastError();
 }
 
 template cudaError_t gram_tc_pair<float, double>(const float *, long, const double *, long, long,

@@ -225,12 +225,6 @@ cudaError_t rotate_f64_df(const double *A, long lda, long nd, int ns, const doub
                           long ldo, cudaStream_t st);
 // FP64 Gram with a caller-chosen number of row slices (part: nsplit * ns * ns doubles).
 int gram_default_splits(int ns, long nd);
-// out = A C (C: ns x ns FP64, column-major) for an FP64 block A with column bounds bA (as
-// for stencil_f64), integer and FP32 arithmetic (rotate_fx.cu); ws: rotate_fx_workspace(ns)
-// bytes of device memory.
-size_t rotate_fx_workspace(int ns);
-cudaError_t rotate_f64_fx(const double *A, long lda, const unsigned *bA, long nd, int ns,
-                          const double *C, double *out, long ldo, void *ws, cudaStream_t st);
 // Tensor-core Gram of the mixed-precision form (gram_tc.cu): G = A^T B (ns x ns FP64,
 // column-major) from operands rounded to 23 bits of each 256-row chunk's largest entry,
 // accumulated exactly on the tensor cores; sym computes the tiles on and above the
@@ -240,6 +234,11 @@ size_t gram_tc_workspace(long nd, int ns, bool same_operand, bool sym);
 // The same contractions for FP64 blocks in the 47-bit form (six digits per entry, classes
 // 0..5): M = A^T A and Hm = A^T B, both symmetric; ws: gram_tc47_workspace(nd, ns) bytes.
 size_t gram_tc47_workspace(long nd, int ns);
+// out = Y C (C: ns x ns FP64, column-major) on the tensor cores in the 47-bit digit form;
+// ws: rotate_tc_workspace(nd, ns) bytes.
+size_t rotate_tc_workspace(long nd, int ns);
+cudaError_t rotate_tc(const double *Y, long ldy, long nd, int ns, const double *C, double *out,
+                      long ldo, void *ws, size_t ws_bytes, int *err, cudaStream_t st);
 cudaError_t gram_tc47_pair(const double *A, long lda, const double *B, long ldb, long nd, int ns,
                            double *M, double *Hm, void *ws, size_t ws_bytes, int *err,
                            cudaStream_t st);

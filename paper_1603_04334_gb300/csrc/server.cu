@@ -252,12 +252,12 @@ size_t sparc_request_bytes(const sparc_request *q)
     if (q->dtype == SPARC_F32) {
         b += gram_tc_workspace(nd, ns, false, true);
     } else {
-        // 47-bit tensor-core Gram, column bounds of the filter's blocks and of H Y_f,
-        // V_eff - shift pairs, grid form of the rotation matrix
-        b += gram_tc47_workspace(nd, ns);
-        b += sizeof(unsigned) * ((size_t)(q->degree + 1) * ns + 2 * (size_t)ns);
+        // 47-bit tensor-core Gram and rotation (one workspace), column bounds of the
+        // filter's blocks, V_eff - shift pairs
+        const size_t wg = gram_tc47_workspace(nd, ns), wr = rotate_tc_workspace(nd, ns);
+        b += wg > wr ? wg : wr;
+        b += sizeof(unsigned) * ((size_t)(q->degree + 1) * ns + (size_t)ns);
         b += 8 * (size_t)nd;
-        b += rotate_fx_workspace(ns);
     }
     b += sizeof(double) * (4 * (size_t)ns * ns + 2 * (size_t)ns + (size_t)dense_work_elems(ns));
     b += sizeof(double) * (3 * (size_t)nd + kDotBlocks + 4096);

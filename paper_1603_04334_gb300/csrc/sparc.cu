@@ -67,7 +67,6 @@ struct sparc_ctx {
     void *bnd = nullptr;     size_t bnd_bytes = 0;   // column bounds of the FP64 filter's blocks
     void *bsc = nullptr;     size_t bsc_bytes = 0;   // column bounds of other FP64 H applications
     void *vc = nullptr;      size_t vc_bytes = 0;    // V_eff - vc_shift as FP32 pairs
-    void *rws = nullptr;     size_t rws_bytes = 0;   // grid form of the rotation matrix
     double vc_shift = 0.0;   bool vc_valid = false;
     int *flags = nullptr;                            // device status words
     double *pin = nullptr;                           // pinned host staging (2*1024+16)
@@ -409,25 +408,19 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
         TRY(ensure(ctx, ctx->hx, ctx->hx_bytes, sizeof(double) * (size_t)ns * ld));
         HX = (double *)ctx->hx;
     }
-    // H Yf in FP64. FP64 blocks: column bounds of Yf (one pass) and of H Yf (raised by its
-    // application) for the rotations on the fixed-point grids
-    unsigned *bY = nullptr, *bH = nullptr;
-    if (sizeof(T) == 8) {
-        TRY(ensure(ctx, ctx->bsc, ctx->bsc_bytes, sizeof(unsigned) * 2 * (size_t)ns));
-        bY = (unsigned *)ctx->bsc;
-        bH = bY + ns;
-        CK(cudaMemsetAsync(bY, 0, sizeof(unsigned) * 2 * (size_t)ns, ctx->st));
-        CK(colmax_f64((const double *)Yf, ns, ld, nd, bY, ctx->st));
-        TRY(step_f64(ctx, (const double *)Yf, nullptr, HX, ns, ld, 1.0, 0.0, 0.0, bY, bH));
-    } else {
+    // H Yf in FP64
+    if (sizeof(T) == 8)
+        TRY(step_f64(ctx, (const double *)Yf, nullptr, HX, ns, ld, 1.0, 0.0, 0.0));
+    else
         TRY(apply_f32in_f64(ctx, (const float *)Yf, HX, ns, ld));
-    }
     // M_s = Yf^T Yf, H_s = Yf^T (H Yf)
     DenseBufs d;
     TRY(dense_bufs(ctx, ns, d));
     if (sizeof(T) == 8) {
-        // both contractions on the tensor cores in the 47-bit digit form (gram_tc.cu)
-        TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, gram_tc47_workspace(nd, ns)));
+        // both contractions on the tensor cores in the 47-bit digit form (gram_tc.cu); the
+        // rotations below reuse the workspace
+        const size_t wg = gram_tc47_workspace(nd, ns), wr = rotate_tc_workspace(nd, ns);
+        TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, wg > wr ? wg : wr));
         { PHASE(SPARC_PHASE_GRAM); CK(gram_tc47_pair((const double *)Yf, ld, HX, ld, nd, ns, d.M, d.Hs, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st)); }
     } else {
         // mixed-precision form: both contractions on the tensor cores (gram_tc.cu)
@@ -454,10 +447,9 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
         TRY(ensure(ctx, ctx->rotx, ctx->rotx_bytes, sizeof(T) * (size_t)ns * ld));
         xout = (T *)ctx->rotx;
     }
-    if (sizeof(T) == 8) {
-        TRY(ensure(ctx, ctx->rws, ctx->rws_bytes, rotate_fx_workspace(ns)));
-        { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64_fx((const double *)Yf, ld, bY, nd, ns, d.Cf, (double *)xout, ld, ctx->rws, ctx->st)); }
-    } else
+    if (sizeof(T) == 8)
+        { PHASE(SPARC_PHASE_ROTATE); CK(rotate_tc((const double *)Yf, ld, nd, ns, d.Cf, (double *)xout, ld, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st)); }
+    else
         { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f32((const float *)Yf, ld, nd, ns, d.Cf, (float *)xout, ld, ctx->st)); }
     if (resid_host) {
         // H X = (H Y_f) (L^-T Q); residuals against the rotated block. The FP32 form rotates
@@ -465,7 +457,7 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
         TRY(ensure(ctx, ctx->roth, ctx->roth_bytes, sizeof(T) * (size_t)ns * ld));
         if (sizeof(T) == 8) {
             double *hxr = (double *)ctx->roth;
-            { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64_fx(HX, ld, bH, nd, ns, d.Cf, hxr, ld, ctx->rws, ctx->st)); }
+            { PHASE(SPARC_PHASE_ROTATE); CK(rotate_tc(HX, ld, nd, ns, d.Cf, hxr, ld, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st)); }
             { PHASE(SPARC_PHASE_OTHER); CK(resid_f64((const double *)xout, hxr, ld, nd, ns, d.ritz, d.resid, ctx->st)); }
         } else {
             float *hxr = (float *)ctx->roth;
@@ -561,7 +553,7 @@ void free_ctx(sparc_ctx *c)
     if (!c) return;
     void *ps[] = {c->V, c->Vf, c->Vdf, c->atom_ptr, c->idx, c->ent_atom, c->chi, c->gchi, c->chi_f,
                   c->gchi_f, c->chi_df, c->uniq_node, c->uniq_ptr, c->ent_list, c->nl_atom, c->nl_gf, c->nl_gdf, c->C, c->hx, c->rotx, c->roth, c->part,
-                  c->tcws, c->dm, c->lz, c->bnd, c->bsc, c->vc, c->rws, c->flags};
+                  c->tcws, c->dm, c->lz, c->bnd, c->bsc, c->vc, c->flags};
     for (void *p : ps) dfree(p);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->prof.used) cudaEventDestroy(e);
