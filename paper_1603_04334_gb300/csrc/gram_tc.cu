@@ -308,15 +308,16 @@ k_tc_digits_t(const double *__restrict__ Y, long ld, long nd, int ns, long nstep
 // chunks. Gram mode: CTA b owns unit b (units = halves x tiles x splits). ROT (the rotation,
 // see rotate_tc below): tile t is (t % mblk, t / mblk) over all chunks, the CTAs are
 // persistent and walk units b, b + gridDim.x, ... with the ring, the MMAs and the epilogue
-// running on across units; B's exponents have the row stride eb_ld, and the epilogue
-// writes out[i + j ldo] (i: B column, j: A column) for i < nrow, j < ncol.
+// running on across units; A's and B's exponents have the row strides ea_ld and eb_ld, and
+// the epilogue writes out[i + j ldo] (i: A column, j: B column) for i < nrow, j < ncol, a
+// warp's lanes covering 32 consecutive i (coalesced).
 template <class C, bool ROT>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
           const __nv_bfloat16 *__restrict__ DB, const int *__restrict__ EB, int ns_pad, long nstep,
           const int2 *__restrict__ tiles, int ntiles, int nsplit, double *__restrict__ part,
           int *err, int eb_ld = 0, int mblk = 1, double *__restrict__ out = nullptr, long ldo = 0,
-          long nrow = 0, int ncol = 0)
+          long nrow = 0, int ncol = 0, long ea_ld = 0)
 {
     using Dm = TcDims<C>;
     constexpr int kStages = C::kStages, kStepsPerChunk = Dm::kStepsPerChunk;
@@ -331,6 +332,7 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
         (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long nchunk = nstep / kStepsPerChunk;
+    const long ea_stride = ROT ? ea_ld : ns_pad;
     const int nunits = ROT ? ntiles * Dm::kHalves : (int)gridDim.x;
     const int ustride = ROT ? (int)gridDim.x : nunits;
     struct Unit {
@@ -476,7 +478,7 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
         bool ok = true;
         for (int u = blockIdx.x; u < nunits && ok; u += ustride) {
             const Unit w = unit(u);
-            const int colA = w.tb.x * kTile + r;
+            const long colA = (long)w.tb.x * kTile + r;
 #pragma unroll
             for (int x = 0; x < kEpiCols; ++x) {
                 H[x] = 0.0f;
@@ -490,7 +492,7 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                     break;
                 }
                 tc_fence_after();
-                const float fA = pow2_factor(EA[c * ns_pad + colA]);
+                const float fA = pow2_factor(EA[c * ea_stride + colA]);
                 const int *eb = EB + c * (ROT ? eb_ld : ns_pad) + (long)w.tb.y * kTile +
                                 w.hf * C::kN + hw * kEpiCols;
 #pragma unroll
@@ -529,13 +531,13 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
             }
             if (!ok) break;
             if (ROT) {
-                const long jc = (long)w.tb.x * kTile + r;
-                const long i0 = (long)w.tb.y * kTile + w.hf * C::kN + hw * kEpiCols;
-                if (jc < ncol) {
-                    double *o = out + i0 + jc * ldo;
+                const long i = (long)w.tb.x * kTile + r;
+                const long j0 = (long)w.tb.y * kTile + w.hf * C::kN + hw * kEpiCols;
+                if (i < nrow) {
+                    double *o = out + i + j0 * ldo;
 #pragma unroll
                     for (int x = 0; x < kEpiCols; ++x)
-                        if (i0 + x < nrow) o[x] = widen_int(H[x]) + widen_int(Lw[x * 32]);
+                        if (j0 + x < ncol) o[(long)x * ldo] = widen_int(H[x]) + widen_int(Lw[x * 32]);
                 }
             } else {
                 double *o = part + ((long)w.split * ntiles + w.tile) * kTile * kTile +
@@ -755,10 +757,11 @@ cudaError_t gram_tc47_pair(const double *A, long lda, const double *B, long ldb,
 }
 
 // ---- rotation out = Y C on the tensor cores (47-bit digits) ------------------------------
-// Written as the contraction G = A^T B with A = C (K = Ns rows, M = Ns columns) and
-// B = Y^T (N = Nd): G(j, i) = sum_k C_kj Y_ik = out(i, j). C gets exponents per (K chunk,
-// column), Y per (K chunk, row), so every product in a class accumulator shares one scale;
-// K = Ns is short, so each CTA owns one 128 x 64 tile over all of K (no split).
+// Written as the contraction G = A^T B with A = Y^T (K = Ns: Y's columns, M = Nd: Y's rows)
+// and B = C (N = Ns): G(i, j) = sum_k Y_ik C_kj = out(i, j). Y gets exponents per (K chunk,
+// row), C per (K chunk, column), so every product in a class accumulator shares one scale.
+// K = Ns is short, so a unit is one 128 x 64 tile over all of K; the tensor-memory lanes
+// hold Y's rows, so each store of the epilogue covers 32 consecutive rows of a column.
 namespace {
 struct RotPlan {
     int ns_pad, mblk;
@@ -830,9 +833,10 @@ cudaError_t rotate_tc(const double *Y, long ldy, long nd, int ns, const double *
         note_launch();
     }
     const unsigned grid = (unsigned)(ctas < 152 ? ctas : 152);  // persistent, one per SM
+    // A: Y's digits (nblk row blocks, exponent stride nd_pad); B: C's (mblk column blocks)
     k_gram_tc<C, true><<<grid, kThreads, TcDims<C>::kSmemBytes, st>>>(
-        DA, EA, DB, EB, p.ns_pad, p.nstep, nullptr, (int)(p.mblk * p.nblk), 1, nullptr, err,
-        (int)p.nd_pad, p.mblk, out, ldo, nd, ns);
+        DB, EB, DA, EA, p.ns_pad, p.nstep, nullptr, (int)(p.mblk * p.nblk), 1, nullptr, err,
+        p.ns_pad, (int)p.nblk, out, ldo, nd, ns, p.nd_pad);
     note_launch();
     return cudaGetLastError();
 }
