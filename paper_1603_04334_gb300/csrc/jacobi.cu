@@ -175,7 +175,10 @@ static cudaError_t jacobi_grid_t(T *A0, T *A1, T *V, T *diag, int n, GridBarrier
         coop_blocks = sms * (per > 0 ? per : 1);
     }
     const long half = (n + 1) / 2;
-    long want = (half * half + NT - 1) / NT;  // one 2 x 2 block of A per thread
+    // a round's FP64 work (the 2 x 2 blocks and the columns of V) spread over four times
+    // the CTAs that one block per thread would take: the FP64 pipes of more SMs, at the
+    // cost of a barrier over more CTAs
+    long want = 4 * ((half * half + NT - 1) / NT);
     if (want < 1) want = 1;
     int G = (int)(want < coop_blocks ? want : coop_blocks);
     if (G > 152) G = 152;
