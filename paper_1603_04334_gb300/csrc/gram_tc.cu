@@ -306,7 +306,8 @@ k_tc_digits_t(const double *__restrict__ Y, long ld, long nd, int ns, long nstep
 // a tile at r * 128 + c (r: A column, c: B column).
 // Work units: a unit is one tile half (kN of the tile's 128 B columns) over a range of
 // chunks. Gram mode: CTA b owns unit b (units = halves x tiles x splits). ROT (the rotation,
-// see rotate_tc below): tile t is (t % mblk, t / mblk) over all chunks, the CTAs are
+// see rotate_tc below): tile t is (t / mblk, t % mblk) over all chunks (mblk = B blocks, so
+// the units that share an A block run side by side and find it in L2), the CTAs are
 // persistent and walk units b, b + gridDim.x, ... with the ring, the MMAs and the epilogue
 // running on across units; A's and B's exponents have the row strides ea_ld and eb_ld, and
 // the epilogue writes out[i + j ldo] (i: A column, j: B column) for i < nrow, j < ncol, a
@@ -346,7 +347,7 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
         w.hf = u % Dm::kHalves;
         w.tile = (u / Dm::kHalves) % ntiles;
         w.split = u / (Dm::kHalves * ntiles);
-        w.tb = ROT ? make_int2(w.tile % mblk, w.tile / mblk) : tiles[w.tile];
+        w.tb = ROT ? make_int2(w.tile / mblk, w.tile % mblk) : tiles[w.tile];
         w.c0 = ROT ? 0 : (long)w.split * nchunk / nsplit;
         w.c1 = ROT ? nchunk : (long)(w.split + 1) * nchunk / nsplit;
         w.one = !ROT && DA == DB && w.tb.x == w.tb.y;
@@ -833,10 +834,11 @@ cudaError_t rotate_tc(const double *Y, long ldy, long nd, int ns, const double *
         note_launch();
     }
     const unsigned grid = (unsigned)(ctas < 152 ? ctas : 152);  // persistent, one per SM
-    // A: Y's digits (nblk row blocks, exponent stride nd_pad); B: C's (mblk column blocks)
+    // A: Y's digits (nblk row blocks, exponent stride nd_pad); B: C's (mblk column blocks,
+    // the fastest tile index)
     k_gram_tc<C, true><<<grid, kThreads, TcDims<C>::kSmemBytes, st>>>(
         DB, EB, DA, EA, p.ns_pad, p.nstep, nullptr, (int)(p.mblk * p.nblk), 1, nullptr, err,
-        p.ns_pad, (int)p.nblk, out, ldo, nd, ns, p.nd_pad);
+        p.ns_pad, p.mblk, out, ldo, nd, ns, p.nd_pad);
     note_launch();
     return cudaGetLastError();
 }

@@ -237,6 +237,13 @@ size_t gram_tc47_workspace(long nd, int ns);
 // out = Y C (C: ns x ns FP64, column-major) on the tensor cores in the 47-bit digit form;
 // ws: rotate_tc_workspace(nd, ns) bytes.
 size_t rotate_tc_workspace(long nd, int ns);
+// The FP64 form's Gram and rotation run on the tensor cores while their digit workspace (12
+// bytes per element of both operands) stays within 24 GB; larger blocks keep FP32-pair
+// arithmetic on the CUDA cores.
+inline bool fp64_on_tensor_cores(long nd, int ns)
+{
+    return gram_tc47_workspace(nd, ns) <= ((size_t)24 << 30);
+}
 cudaError_t rotate_tc(const double *Y, long ldy, long nd, int ns, const double *C, double *out,
                       long ldo, void *ws, size_t ws_bytes, int *err, cudaStream_t st);
 cudaError_t gram_tc47_pair(const double *A, long lda, const double *B, long ldb, long nd, int ns,

@@ -435,7 +435,7 @@ constexpr int kScatDfNodes = 256;
 constexpr int kScatDfCols = 8;
 }  // namespace
 
-__global__ void __launch_bounds__(kScatDfNodes)
+__global__ void __launch_bounds__(kScatDfNodes, 3)
 k_scatter_df(double *out, long ld, int ncols, long nuniq, const int *__restrict__ uniq_node,
              const int *__restrict__ uniq_ptr, const int *__restrict__ nl_atom,
              const float2 *__restrict__ g, const float2 *__restrict__ Cs, unsigned *bOut)
@@ -447,28 +447,28 @@ k_scatter_df(double *out, long ld, int ncols, long nuniq, const int *__restrict_
     if (live) {
         const long node = uniq_node[u];
         const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
-        // all column sums first (coefficients from L1 / L2), then every output read is
-        // issued before any store: kScatDfCols independent DRAM reads in flight per thread
-        double v[kScatDfCols];
-#pragma unroll
-        for (int k = 0; k < kScatDfCols; ++k) {
-            const int c = c0 + k;
-            float vh = 0.0f, vl = 0.0f;
-            if (c < c1) {
-                for (int q = q0; q < q1; ++q) {
-                    const float2 *cs = Cs + (long)nl_atom[q] * 4 * ncols + c;
-#pragma unroll
-                    for (int l = 0; l < 4; ++l) mac(g[4L * q + l], cs[(long)l * ncols], vh, vl);
-                }
-            }
-            v[k] = pair_to_double(vh, vl);
-        }
+        // the output reads go first (kScatDfCols DRAM reads in flight while the sums are
+        // formed); each entry's atom and coefficients are loaded once for all columns, and
+        // per column the entries are summed in ascending order as before
         double *op = out + node + (long)c0 * ld;
 #pragma unroll
         for (int k = 0; k < kScatDfCols; ++k) o[k] = c0 + k < c1 ? op[(long)k * ld] : 0.0;
+        float vh[kScatDfCols], vl[kScatDfCols];
+#pragma unroll
+        for (int k = 0; k < kScatDfCols; ++k) vh[k] = vl[k] = 0.0f;
+        for (int q = q0; q < q1; ++q) {
+            const float2 *cs = Cs + (long)nl_atom[q] * 4 * ncols + c0;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const float2 gl = g[4L * q + l];
+#pragma unroll
+                for (int k = 0; k < kScatDfCols; ++k)
+                    if (c0 + k < c1) mac(gl, cs[(long)l * ncols + k], vh[k], vl[k]);
+            }
+        }
 #pragma unroll
         for (int k = 0; k < kScatDfCols; ++k) {
-            o[k] += v[k];
+            o[k] += pair_to_double(vh[k], vl[k]);
             if (c0 + k < c1) op[(long)k * ld] = o[k];
         }
     } else {

@@ -252,10 +252,14 @@ size_t sparc_request_bytes(const sparc_request *q)
     if (q->dtype == SPARC_F32) {
         b += gram_tc_workspace(nd, ns, false, true);
     } else {
-        // 47-bit tensor-core Gram and rotation (one workspace), column bounds of the
-        // filter's blocks, V_eff - shift pairs
-        const size_t wg = gram_tc47_workspace(nd, ns), wr = rotate_tc_workspace(nd, ns);
-        b += wg > wr ? wg : wr;
+        // 47-bit tensor-core Gram and rotation (one workspace) or, for large blocks, the
+        // FP32-pair Gram's partials; column bounds of the filter's blocks, V_eff - shift pairs
+        if (fp64_on_tensor_cores(nd, ns)) {
+            const size_t wg = gram_tc47_workspace(nd, ns), wr = rotate_tc_workspace(nd, ns);
+            b += wg > wr ? wg : wr;
+        } else {
+            b += sizeof(double) * (size_t)gram_part_elems(ns, nd);
+        }
         b += sizeof(unsigned) * ((size_t)(q->degree + 1) * ns + (size_t)ns);
         b += 8 * (size_t)nd;
     }

@@ -416,12 +416,19 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
     // M_s = Yf^T Yf, H_s = Yf^T (H Yf)
     DenseBufs d;
     TRY(dense_bufs(ctx, ns, d));
-    if (sizeof(T) == 8) {
+    const bool tc64 = sizeof(T) == 8 && fp64_on_tensor_cores(nd, ns);
+    if (tc64) {
         // both contractions on the tensor cores in the 47-bit digit form (gram_tc.cu); the
         // rotations below reuse the workspace
         const size_t wg = gram_tc47_workspace(nd, ns), wr = rotate_tc_workspace(nd, ns);
         TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, wg > wr ? wg : wr));
         { PHASE(SPARC_PHASE_GRAM); CK(gram_tc47_pair((const double *)Yf, ld, HX, ld, nd, ns, d.M, d.Hs, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st)); }
+    } else if (sizeof(T) == 8) {
+        // blocks whose digit workspace would be too large: FP32-pair Grams (gram_df.cu)
+        TRY(ensure(ctx, ctx->part, ctx->part_bytes, sizeof(double) * (size_t)gram_part_elems(ns, nd)));
+        double *part = (double *)ctx->part;
+        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64((const double *)Yf, ld, (const double *)Yf, ld, nd, ns, d.M, part, ctx->st, true)); }
+        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64((const double *)Yf, ld, HX, ld, nd, ns, d.Hs, part, ctx->st, true)); }
     } else {
         // mixed-precision form: both contractions on the tensor cores (gram_tc.cu)
         TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, gram_tc_workspace(nd, ns, false, true)));
@@ -448,7 +455,10 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
         xout = (T *)ctx->rotx;
     }
     if (sizeof(T) == 8)
-        { PHASE(SPARC_PHASE_ROTATE); CK(rotate_tc((const double *)Yf, ld, nd, ns, d.Cf, (double *)xout, ld, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st)); }
+    {
+        if (tc64) { PHASE(SPARC_PHASE_ROTATE); CK(rotate_tc((const double *)Yf, ld, nd, ns, d.Cf, (double *)xout, ld, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st)); }
+        else { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64((const double *)Yf, ld, nd, ns, d.Cf, (double *)xout, ld, ctx->st)); }
+    }
     else
         { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f32((const float *)Yf, ld, nd, ns, d.Cf, (float *)xout, ld, ctx->st)); }
     if (resid_host) {
@@ -457,7 +467,8 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
         TRY(ensure(ctx, ctx->roth, ctx->roth_bytes, sizeof(T) * (size_t)ns * ld));
         if (sizeof(T) == 8) {
             double *hxr = (double *)ctx->roth;
-            { PHASE(SPARC_PHASE_ROTATE); CK(rotate_tc(HX, ld, nd, ns, d.Cf, hxr, ld, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st)); }
+            if (tc64) { PHASE(SPARC_PHASE_ROTATE); CK(rotate_tc(HX, ld, nd, ns, d.Cf, hxr, ld, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st)); }
+            else { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64(HX, ld, nd, ns, d.Cf, hxr, ld, ctx->st)); }
             { PHASE(SPARC_PHASE_OTHER); CK(resid_f64((const double *)xout, hxr, ld, nd, ns, d.ritz, d.resid, ctx->st)); }
         } else {
             float *hxr = (float *)ctx->roth;
