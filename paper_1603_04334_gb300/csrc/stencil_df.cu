@@ -29,6 +29,8 @@
 // whose pair overflows FP32 (|alpha (V_p - shift)| or the Laplacian scale near 2^100 and
 // beyond). Each launch can raise the output's column bounds (atomicMax), which is how the
 // filter hands the bound of Y_{j+1} to the next step without another pass over the block.
+#include <type_traits>
+
 #include "df.cuh"
 #include "fx.cuh"
 #include "internal.cuh"
@@ -200,7 +202,13 @@ k_stencil_df(const TI *__restrict__ Y, const double *Yprev, double *out,
     double pcur = (act && Pc) ? Pc[pij + (unsigned)k0 * plane] : 0.0;
     unsigned omax = 0u;
     __syncthreads();
-    for (int k = k0; k < k1; ++k) {
+    // The plane loop is unrolled 13 times, one copy per rotation of the z queue: in the
+    // copy of phase PH, logical queue entry t (plane k - R + t) sits in q[(PH + t) % 13], so
+    // the queue is never shifted.
+    int k = k0;
+    auto step = [&](auto phase) {
+        constexpr int PH = decltype(phase)::value;
+        constexpr int Q = 2 * R + 1;
         const int b = (k - k0) & 1;
         const unsigned pk = (unsigned)k * plane;
         // loads for plane k+1 (and the queue entry k+R+1), consumed after the compute
@@ -222,14 +230,14 @@ k_stencil_df(const TI *__restrict__ Y, const double *Yprev, double *out,
         if (act && kn < n2) gq = Yc[pij + (unsigned)kn * plane];
         if (act) {
             // h^2 D L_h y in units of 2^(EY-28): exact integer sums of d, FP32 sums of r
-            const int2 c = q[R];
+            const int2 c = q[(PH + R) % Q];
             const int2 *row = s + b * (SY * SX) + me;
             long long A = (long long)cf.W[0] * c.x;
             float Rs = cf.Wf[0] * __int_as_float(c.y);
 #pragma unroll
             for (int r = 1; r <= R; ++r) {
                 const int2 xa = row[r], xb = row[-r], ya = row[r * SX], yb = row[-r * SX];
-                const int2 za = q[R + r], zb = q[R - r];
+                const int2 za = q[(PH + R + r) % Q], zb = q[(PH + R - r) % Q];
                 const int sd = (xa.x + xb.x + ya.x) + (yb.x + za.x + zb.x);
                 const float sr = ((__int_as_float(xa.y) + __int_as_float(xb.y)) +
                                   (__int_as_float(ya.y) + __int_as_float(yb.y))) +
@@ -263,20 +271,30 @@ k_stencil_df(const TI *__restrict__ Y, const double *Yprev, double *out,
             omax = max(omax, abs_hi_word(o));
             Oc[pij + pk] = o;
         }
-#pragma unroll
-        for (int t = 0; t < 2 * R; ++t) q[t] = q[t + 1];
-        q[2 * R] = (act && kn < n2) ? to_fx(gq, EY) : zero;
+        // plane k - R leaves the queue; its slot takes plane k + R + 1 (logical entry 2R
+        // of the next phase), and the next phase's centre is plane k + 1
+        q[PH % Q] = (act && kn < n2) ? to_fx(gq, EY) : zero;
         vcur = vnext;
         pcur = pnext;
         if (more) {
             int2 *nb = s + (b ^ 1) * (SY * SX);
-            nb[me] = q[R];
+            nb[me] = q[(PH + 1 + R) % Q];
 #pragma unroll
             for (int u = 0; u < 2; ++u)
                 if (hs[u] >= 0) nb[hs[u]] = hv[u] ? to_fx(g[u], EY) : zero;
         }
         __syncthreads();
+        ++k;
+    };
+#define SPARC_DF_STEP(P)                                                                 \
+    if (k >= k1) break;                                                                  \
+    step(std::integral_constant<int, P>{});
+    for (;;) {
+        SPARC_DF_STEP(0) SPARC_DF_STEP(1) SPARC_DF_STEP(2) SPARC_DF_STEP(3) SPARC_DF_STEP(4)
+        SPARC_DF_STEP(5) SPARC_DF_STEP(6) SPARC_DF_STEP(7) SPARC_DF_STEP(8) SPARC_DF_STEP(9)
+        SPARC_DF_STEP(10) SPARC_DF_STEP(11) SPARC_DF_STEP(12)
     }
+#undef SPARC_DF_STEP
     if (bOut) {
         omax = __reduce_max_sync(0xffffffffu, omax);
         if ((tid & 31) == 0 && omax) raise_bound(bOut + col, omax);

@@ -3,25 +3,28 @@
 // Sec. 3.4) fed by the Tensor Memory Accelerator.
 //
 // The FP32 filter step moves 12 B per point-orbital and should run at HBM speed. A CTA owns
-// a 32 x 16 tile of (x, y) for one column and streams along z. One elected thread keeps a
+// a 32 x 16 tile of (x, y) for one column and streams along z. A producer warp keeps a
 // ring of kStages shared-memory planes filled with 4-D tiled TMA loads
 // (cp.async.bulk.tensor) of the tile plus its radius-6 halo: the box starts 8 nodes left
 // of the tile so that the x coordinate stays 16-byte aligned, and nodes outside the grid
 // are zero-filled by the TMA unit, which is exactly the zero-Dirichlet boundary. Each
-// plane's arrival is signalled through an mbarrier (expect-tx); all waits are bounded and
-// report a timeout through a device flag instead of hanging.
+// plane's arrival is signalled through a `full` mbarrier (expect-tx), its release by the
+// four compute warps through an `empty` mbarrier; all waits are bounded and report a
+// timeout through a device flag instead of hanging.
 //
-// Each thread computes 4 consecutive x nodes of one row with 128-bit shared loads
+// Each compute thread takes 4 consecutive x nodes of one row with 128-bit shared loads
 // (5 loads cover x-6 .. x+9 of the four nodes, 12 more the y neighbours) and keeps the
 // z neighbours of its four nodes in a 13-deep register queue of float4, filled from each
-// newly arrived plane. The queue needs planes t .. t+6 of the ring, so with kStages = 10
-// the loads run 4 planes ahead of the compute.
+// newly arrived plane. The arithmetic runs on packed FP32 pairs (two nodes per add or
+// fused multiply-add), each operation rounded as the scalar form would round it. The
+// queue needs planes t .. t+6 of the ring, so with kStages = 10 the loads run 3 planes
+// ahead of the compute.
 //
 // Y_{j-1} (one third of the step's traffic) rides in the same ring: the TMA load that
 // brings plane t of Y also brings the halo-free tile of Y_{j-1} at the plane whose compute
 // first needs plane t (z - 6), completing on the same mbarrier, so every HBM stream of the
 // step is an asynchronous bulk copy. V_eff (one plane shared by all columns, L2-resident)
-// is prefetched into registers one plane ahead.
+// is prefetched into registers two planes ahead.
 //
 // Requirements (checked on the host, else the plain kernel of stencil.cu runs): n0 and ld
 // multiples of 4 and 16-byte aligned block pointers (TMA strides and float4 accesses).
@@ -44,137 +47,238 @@ constexpr int kPlaneBytes = kW * kH * 4;   // Y plane with halo
 constexpr int kTileBytes = kBX * kTY * 4;  // Y_{j-1} tile, no halo
 constexpr int kStageFloats = kW * kH + kBX * kTY;
 constexpr unsigned kWaitLimit = 1u << 22;
+constexpr int kTmaCompute = kTX * kTY;      // compute threads of k_stencil_f32_tma (4 warps)
+constexpr int kTmaThreads = kTmaCompute + 32;  // + the producer warp
 }  // namespace
 
-__global__ void __launch_bounds__(kTX *kTY)
+// Step coefficients as packed pairs for the FP32x2 instructions (both lanes equal).
+struct StepCoef2 {
+    float2 w[kR + 1];
+    float2 c0, alpha, nbeta;
+};
+
+__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+
+// One plane of the step for the thread's four nodes, as two packed pairs (nodes 0-1 and
+// 2-3). row: the plane row at node i - 8 (20 values cover i - 8 .. i + 11); the z queue
+// slot of logical entry k (plane tc - 6 + k) is (PH + k) % 13, a compile-time index. Per
+// node: (c0 + alpha V) y + sum_r w_r ((x+r + x-r) + (y+r + y-r) + (z+r + z-r)), each
+// operation rounded as in the scalar form (the x sums of odd radii, whose pairs straddle
+// a register pair boundary, stay scalar).
+template <int PH>
+__device__ __forceinline__ void plane_math(const float *row, const float4 (&q)[2 * kR + 1],
+                                           const float4 &vv, const StepCoef2 &cf, float2 &aA,
+                                           float2 &aB)
+{
+    constexpr int Q = 2 * kR + 1;
+    float f[20];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const float4 v = *reinterpret_cast<const float4 *>(row + 4 * m);
+        f[4 * m] = v.x;
+        f[4 * m + 1] = v.y;
+        f[4 * m + 2] = v.z;
+        f[4 * m + 3] = v.w;
+    }
+    const float4 c = q[(PH + kR) % Q];
+    aA = __fmul2_rn(__ffma2_rn(cf.alpha, lo2(vv), cf.c0), lo2(c));
+    aB = __fmul2_rn(__ffma2_rn(cf.alpha, hi2(vv), cf.c0), hi2(c));
+#pragma unroll
+    for (int r = 1; r <= kR; ++r) {
+        const float4 yp = *reinterpret_cast<const float4 *>(row + r * kW + 8);
+        const float4 ym = *reinterpret_cast<const float4 *>(row - r * kW + 8);
+        const float4 zp = q[(PH + kR + r) % Q], zm = q[(PH + kR - r) % Q];
+        float2 xA, xB;
+        if (r % 2 == 0) {
+            xA = __fadd2_rn(make_float2(f[8 + r], f[9 + r]), make_float2(f[8 - r], f[9 - r]));
+            xB = __fadd2_rn(make_float2(f[10 + r], f[11 + r]), make_float2(f[10 - r], f[11 - r]));
+        } else {
+            xA = make_float2(f[8 + r] + f[8 - r], f[9 + r] + f[9 - r]);
+            xB = make_float2(f[10 + r] + f[10 - r], f[11 + r] + f[11 - r]);
+        }
+        const float2 tA = __fadd2_rn(__fadd2_rn(xA, __fadd2_rn(lo2(yp), lo2(ym))),
+                                     __fadd2_rn(lo2(zp), lo2(zm)));
+        const float2 tB = __fadd2_rn(__fadd2_rn(xB, __fadd2_rn(hi2(yp), hi2(ym))),
+                                     __fadd2_rn(hi2(zp), hi2(zm)));
+        aA = __ffma2_rn(cf.w[r], tA, aA);
+        aB = __ffma2_rn(cf.w[r], tB, aB);
+    }
+}
+
+// Consumer state of one compute thread of k_stencil_f32_tma.
+struct TmaConsumer {
+    const float *sm;
+    uint64_t *full, *empty;
+    float *Oc;
+    const float *V;
+    long p, plane;  // p: the thread's node offset at the current compute plane
+    int k, k1;      // current compute z, end of the chunk
+    int sc;         // stage of the compute plane tc
+    int sn;         // stage of plane tc + 6 (its centre enters the queue)
+    unsigned pn;    // parity of plane tc + 6's current use of its stage
+    int ty, tx, lane;
+    bool act, hasP;
+};
+
+template <int PH>
+__device__ __forceinline__ bool plane_step(TmaConsumer &s, float4 (&q)[2 * kR + 1], float4 &vv,
+                                           float4 &v1, const StepCoef2 &cf)
+{
+    constexpr int Q = 2 * kR + 1;
+    float4 v2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (s.act && s.k + 2 < s.k1) v2 = *reinterpret_cast<const float4 *>(s.V + s.p + 2 * s.plane);
+    // warp-uniform outcome, so that a timed-out wait never splits the warp's __syncwarp
+    if (!__all_sync(0xffffffffu, mbar_wait(&s.full[s.sn], s.pn, kWaitLimit))) return false;
+    const float *stn = s.sm + (long)s.sn * kStageFloats;
+    q[(PH + 2 * kR) % Q] = *reinterpret_cast<const float4 *>(stn + (kR + s.ty) * kW + 8 + 4 * s.tx);
+    const float *row = s.sm + (long)s.sc * kStageFloats + (kR + s.ty) * kW + 4 * s.tx;
+    float2 aA, aB;
+    plane_math<PH>(row, q, vv, cf, aA, aB);
+    if (s.act) {
+        if (s.hasP) {
+            const float4 pv =
+                *reinterpret_cast<const float4 *>(stn + kH * kW + s.ty * kBX + 4 * s.tx);
+            aA = __ffma2_rn(cf.nbeta, lo2(pv), aA);
+            aB = __ffma2_rn(cf.nbeta, hi2(pv), aB);
+        }
+        *reinterpret_cast<float4 *>(s.Oc + s.p) = make_float4(aA.x, aA.y, aB.x, aB.y);
+    }
+    vv = v1;
+    v1 = v2;
+    // plane tc's stage is free once the whole warp has read it
+    __syncwarp();
+    if (s.lane == 0) mbar_arrive(&s.empty[s.sc]);
+    if (++s.sc == kStages) s.sc = 0;
+    if (++s.sn == kStages) {
+        s.sn = 0;
+        s.pn ^= 1u;
+    }
+    ++s.k;
+    s.p += s.plane;
+    return true;
+}
+
+// Block: four compute warps (8 x 16 threads, 4 x-nodes each) and one producer warp whose
+// elected lane keeps the ring full. A stage is handed back through its `empty` mbarrier
+// (one arrival per compute warp) as soon as the plane's compute is done, so the warps run
+// without a block-wide barrier per plane and the producer refills each stage the moment
+// it is free. The plane loop is unrolled 13 times, one copy per rotation of the z queue,
+// so the queue is never shifted.
+__global__ void __launch_bounds__(kTmaThreads, 3)
 k_stencil_f32_tma(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmP,
                   bool hasP, float *out, const float *__restrict__ V, int n0, int n1, int n2,
-                  long ld, int nzc, int zchunk, StepCoef<float> cf, int *err)
+                  long ld, int nzc, int zchunk, StepCoef2 cf, int *err)
 {
     // stage s: Y plane [kH][kW] then the Y_{j-1} tile [kTY][kBX]
     extern __shared__ __align__(128) float sm[];
     __shared__ __align__(8) uint64_t full[kStages];
+    __shared__ __align__(8) uint64_t empty[kStages];
     __shared__ int timed_out;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * kTX + tx;
+    const int tid = threadIdx.x;
     const int i0 = blockIdx.x * kBX, j0 = blockIdx.y * kTY;
     const int col = blockIdx.z / nzc;
     const int k0 = (blockIdx.z % nzc) * zchunk;
     const int k1 = min(n2, k0 + zchunk);
     const int T = (k1 - k0) + 2 * kR;  // planes k0-6 .. k1+5
-    const int i = i0 + 4 * tx, j = j0 + ty;
-    const bool act = (i < n0) && (j < n1);
-    const long plane = (long)n0 * n1;
-    const long pij = (long)i + (long)n0 * j;
-    float *Oc = out + (long)col * ld;
 
     if (tid == 0) {
-        tma_prefetch_desc(&tmY);
-        if (hasP) tma_prefetch_desc(&tmP);
-        for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kTmaCompute / 32);
+        }
         mbar_fence_init();
         timed_out = 0;
     }
     __syncthreads();
-    int issued = 0;  // planes 0 .. issued-1 have been handed to the TMA unit (thread 0)
-    // plane t of Y (z = k0 - 6 + t) into stage t % kStages, with the Y_{j-1} tile of the
-    // plane computed when plane t completes the z queue (z - 6), if that plane is in range
-    auto issue = [&](int t) {
-        const int s = t % kStages;
-        const bool p = hasP && t >= 2 * kR;
-        float *st = sm + (long)s * kStageFloats;
-        mbar_arrive_expect_tx(&full[s], kPlaneBytes + (p ? kTileBytes : 0));
-        tma_load_4d(st, &tmY, &full[s], i0 - 8, j0 - kR, k0 - kR + t, col);
-        if (p) tma_load_4d(st + kH * kW, &tmP, &full[s], i0, j0, k0 - 2 * kR + t, col);
-        issued = t + 1;
-    };
-    auto wait = [&](int t) -> bool {
-        return mbar_wait(&full[t % kStages], (unsigned)((t / kStages) & 1), kWaitLimit);
-    };
-    auto center = [&](int t) -> float4 {
-        return *reinterpret_cast<const float4 *>(sm + (long)(t % kStages) * kStageFloats +
-                                                 (kR + ty) * kW + 8 + 4 * tx);
-    };
-    if (tid == 0)
-        for (int t = 0; t < kStages && t < T; ++t) issue(t);
-
-    bool ok = true;
-    float4 q[2 * kR + 1];
-    // planes 0..5 only feed the queue: read them, then hand their stages to planes
-    // kStages .. kStages+5
-    for (int t = 0; t < kR; ++t) {
-        ok = ok && wait(t);
-        q[t] = center(t);
-    }
-    if (!ok) timed_out = 1;
-    __syncthreads();
-    if (tid == 0 && !timed_out)
-        for (int t = kStages; t < kStages + kR && t < T; ++t) issue(t);
-    for (int t = kR; t < 2 * kR; ++t) {
-        ok = ok && wait(t);
-        q[t] = center(t);
-    }
-    if (!ok) timed_out = 1;
-    __syncthreads();
-
-    float4 vv = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (act) vv = *reinterpret_cast<const float4 *>(V + pij + (long)k0 * plane);
-    for (int tc = kR; tc < T - kR && !timed_out; ++tc) {  // plane tc is z = k0 - 6 + tc
-        const int k = k0 - kR + tc;
-        const long p = pij + (long)k * plane;
-        float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (act && k + 1 < k1) vn = *reinterpret_cast<const float4 *>(V + p + plane);
-        if (!wait(tc + kR)) timed_out = 1;
-        q[2 * kR] = center(tc + kR);
-        const float *pl = sm + (long)(tc % kStages) * kStageFloats;
-        const float *row = pl + (kR + ty) * kW + 4 * tx;  // x offset 4tx = node i - 8
-        float f[20];
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            const float4 v = *reinterpret_cast<const float4 *>(row + 4 * m);
-            f[4 * m] = v.x;
-            f[4 * m + 1] = v.y;
-            f[4 * m + 2] = v.z;
-            f[4 * m + 3] = v.w;
-        }
-        float acc[4];
-        const float *c4 = &q[kR].x;
-        const float *v4 = &vv.x;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = (cf.c0 + cf.alpha * v4[u]) * c4[u];
-#pragma unroll
-        for (int r = 1; r <= kR; ++r) {
-            const float4 yp = *reinterpret_cast<const float4 *>(row + r * kW + 8);
-            const float4 ym = *reinterpret_cast<const float4 *>(row - r * kW + 8);
-            const float *a = &yp.x, *b = &ym.x, *zp = &q[kR + r].x, *zm = &q[kR - r].x;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float t = (f[8 + u + r] + f[8 + u - r]) + (a[u] + b[u]) + (zp[u] + zm[u]);
-                acc[u] += cf.w[r] * t;
+    int issued = 0;  // planes handed to the TMA unit (producer lane)
+    if (tid >= kTmaCompute) {
+        if (tid == kTmaCompute) {
+            tma_prefetch_desc(&tmY);
+            if (hasP) tma_prefetch_desc(&tmP);
+            // plane t of Y (z = k0 - 6 + t) into stage t % kStages, with the Y_{j-1} tile
+            // of the plane computed when plane t completes the z queue (z - 6)
+            for (int t = 0; t < T; ++t) {
+                const int s = t % kStages;
+                if (t >= kStages &&
+                    !mbar_wait(&empty[s], (unsigned)((t / kStages - 1) & 1), kWaitLimit)) {
+                    timed_out = 1;
+                    break;
+                }
+                const bool p = hasP && t >= 2 * kR;
+                float *st = sm + (long)s * kStageFloats;
+                mbar_arrive_expect_tx(&full[s], kPlaneBytes + (p ? kTileBytes : 0));
+                tma_load_4d(st, &tmY, &full[s], i0 - 8, j0 - kR, k0 - kR + t, col);
+                if (p) tma_load_4d(st + kH * kW, &tmP, &full[s], i0, j0, k0 - 2 * kR + t, col);
+                issued = t + 1;
             }
         }
-        if (act) {
-            float4 o = make_float4(acc[0], acc[1], acc[2], acc[3]);
-            if (hasP) {
-                const float4 pv = *reinterpret_cast<const float4 *>(
-                    sm + (long)((tc + kR) % kStages) * kStageFloats + kH * kW + ty * kBX + 4 * tx);
-                o.x -= cf.beta * pv.x;
-                o.y -= cf.beta * pv.y;
-                o.z -= cf.beta * pv.z;
-                o.w -= cf.beta * pv.w;
-            }
-            *reinterpret_cast<float4 *>(Oc + p) = o;
-        }
-        vv = vn;
+    } else {
+        TmaConsumer s;
+        s.sm = sm;
+        s.full = full;
+        s.empty = empty;
+        s.tx = tid % kTX;
+        s.ty = tid / kTX;
+        s.lane = tid & 31;
+        const int i = i0 + 4 * s.tx, j = j0 + s.ty;
+        s.act = (i < n0) && (j < n1);
+        s.hasP = hasP;
+        s.plane = (long)n0 * n1;
+        s.k = k0;
+        s.k1 = k1;
+        s.p = (long)i + (long)n0 * j + (long)k0 * s.plane;
+        s.Oc = out + (long)col * ld;
+        s.V = V;
+        auto center = [&](int t) -> float4 {
+            return *reinterpret_cast<const float4 *>(sm + (long)(t % kStages) * kStageFloats +
+                                                     (kR + s.ty) * kW + 8 + 4 * s.tx);
+        };
+        bool ok = true;
+        float4 q[2 * kR + 1];
+        // planes 0..5 only feed the queue (their stages go back at once); planes 6..11
+        // are the first compute planes
 #pragma unroll
-        for (int t = 0; t < 2 * kR; ++t) q[t] = q[t + 1];
-        __syncthreads();  // every thread is done with plane tc's stage
-        if (tid == 0 && !timed_out && tc + kStages < T) issue(tc + kStages);
+        for (int t = 0; t < 2 * kR; ++t) {
+            if (ok)
+                ok = __all_sync(0xffffffffu, mbar_wait(&full[t % kStages],
+                                                       (unsigned)((t / kStages) & 1), kWaitLimit));
+            q[t] = center(t);
+            if (t < kR) {
+                __syncwarp();
+                if (s.lane == 0) mbar_arrive(&empty[t % kStages]);
+            }
+        }
+        s.sc = kR % kStages;
+        s.sn = (2 * kR) % kStages;
+        s.pn = (unsigned)(((2 * kR) / kStages) & 1);
+        float4 vv = make_float4(0.f, 0.f, 0.f, 0.f), v1 = vv;
+        if (s.act) vv = *reinterpret_cast<const float4 *>(V + s.p);
+        if (s.act && k0 + 1 < k1) v1 = *reinterpret_cast<const float4 *>(V + s.p + s.plane);
+        int tc = kR;
+        const int tend = T - kR;
+        if (ok) {
+#define SPARC_PLANE(PH)                                                                  \
+    if (tc >= tend) break;                                                               \
+    if (!plane_step<PH>(s, q, vv, v1, cf)) {                                             \
+        ok = false;                                                                      \
+        break;                                                                           \
+    }                                                                                    \
+    ++tc;
+            for (;;) {
+                SPARC_PLANE(0) SPARC_PLANE(1) SPARC_PLANE(2) SPARC_PLANE(3) SPARC_PLANE(4)
+                SPARC_PLANE(5) SPARC_PLANE(6) SPARC_PLANE(7) SPARC_PLANE(8) SPARC_PLANE(9)
+                SPARC_PLANE(10) SPARC_PLANE(11) SPARC_PLANE(12)
+            }
+#undef SPARC_PLANE
+        }
+        if (!ok) timed_out = 1;
     }
+    __syncthreads();
     if (timed_out) {
         // leave no TMA write in flight into this CTA's shared memory: wait (bounded) for
         // the latest issued plane of every stage, then report
-        if (tid == 0) {
+        if (tid == kTmaCompute) {
             atomicExch(err, 1);
             for (int s = 0; s < kStages; ++s) {
                 int last = -1;  // latest plane issued into stage s
@@ -455,9 +559,14 @@ cudaError_t stencil_f32_tma(const DevHam &H, const float *Y, const float *Yprev,
     const int gx = (H.n0 + kBX - 1) / kBX, gy = (H.n1 + kTY - 1) / kTY;
     int nzc, zchunk;
     stencil_z_split(H.n2, (long)gx * gy, ncols, nzc, zchunk);
-    dim3 grid(gx, gy, ncols * nzc), block(kTX, kTY);
-    k_stencil_f32_tma<<<grid, block, smem, st>>>(mapY, mapP, Yprev != nullptr, out, H.Vf, H.n0,
-                                                 H.n1, H.n2, ld, nzc, zchunk, cf, err);
+    StepCoef2 c2;
+    for (int r = 0; r <= kR; ++r) c2.w[r] = make_float2(cf.w[r], cf.w[r]);
+    c2.c0 = make_float2(cf.c0, cf.c0);
+    c2.alpha = make_float2(cf.alpha, cf.alpha);
+    c2.nbeta = make_float2(-cf.beta, -cf.beta);
+    dim3 grid(gx, gy, ncols * nzc);
+    k_stencil_f32_tma<<<grid, kTmaThreads, smem, st>>>(mapY, mapP, Yprev != nullptr, out, H.Vf,
+                                                       H.n0, H.n1, H.n2, ld, nzc, zchunk, c2, err);
     note_launch();
     return cudaGetLastError();
 }
