@@ -343,10 +343,54 @@ def run_ours(args, rank, world, local_rank):
            "phases_ms": {k: round(v[1], 3) for k, v in prof.items()},
            "ritz_lowest": [float(x) for x in ritz[:4]],
            "max_resid": float(np.max(resid)) if resid is not None else None}
+    out["after_rotation"] = after_rotation(ctx, X64 if mixed else X, ritz, w, stream,
+                                           fp64_alu_peak_tflops(sm_max))
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(w, args.seed, budget_s=args.cpu_budget)
     ctx.close()
     return out
+
+
+def after_rotation(ctx, X, ritz, w, stream, fp64_peak_tflops: float, reps: int = 10) -> dict:
+    """Times the steps after the rotation on the solved block, apart from the solve:
+    occupations and Fermi level (N_e = Ns, kT = 1e-3 Ha), density, non-local force. Each is
+    the median of `reps` CUDA-event timings on the context stream after 3 warm-up calls."""
+    import torch
+
+    nelec, kT = float(w.ns), 1e-3
+    mu, g = ctx.occupations(ritz, nelec, kT)
+    rho = torch.empty(w.nd, dtype=torch.float64, device=X.device)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    t_occ = timed(lambda: ctx.occupations(ritz, nelec, kT))
+    t_rho = timed(lambda: ctx.density(X, g, rho))
+    t_f = timed(lambda: ctx.nonlocal_force(X, g))
+    es = X.element_size()
+    nsup = ctx.info()["nsupport"]
+    rho_bytes = w.nd * w.ns * es + 8 * w.nd
+    rho_fp64 = 2 * w.nd * w.ns            # one multiply and one fused multiply-add per term
+    f_fp64 = 52 * nsup * w.ns             # 36 for the gradient, 16 for the projections
+    peak_inst = fp64_peak_tflops * 1e12 / 2  # FP64 instructions/s (an FMA counts 2 flops)
+    return {"nelec": nelec, "kT": kT, "lambda_f": mu,
+            "occupations_ms": t_occ,
+            "density_ms": t_rho,
+            "density_GBps": rho_bytes / (t_rho / 1e3) / 1e9,
+            "density_fp64_inst_frac": rho_fp64 / (t_rho / 1e3) / peak_inst,
+            "force_ms": t_f,
+            "force_fp64_inst_frac": f_fp64 / (t_f / 1e3) / peak_inst,
+            "support_entries": nsup}
 
 
 # ----------------------------------------------------------------------------------

@@ -177,6 +177,44 @@ sparc_status sparc_chefsi_step(sparc_ctx *ctx, sparc_dtype dtype, void *X, void 
                                int ncols, long ld, int degree, double *bounds_inout,
                                double *ritz_host, double *resid_host);
 
+/* ---- after the rotation: occupations, density, non-local force ------------------- */
+
+/* Occupations and Fermi level, Eq. (FermiEnergyConstraintFormulation), Sec. 3.4:
+ * lambda_f is the root of 2 sum_n g_n = N_e with g_n = 1 / (1 + exp((lambda_n -
+ * lambda_f) / kT)) (the paper uses kT = 1e-3 Ha, Sec. 5). lambda_host: ns eigenvalues
+ * (host, any order); nelec in (0, 2 ns); kT > 0. Writes *lambda_f_host and, unless
+ * g_host is NULL, g_host[ns] (host). The root is found on the device (one CTA: Newton
+ * steps safeguarded by bisection; the paper uses Brent's method, Sec. 4). Where all
+ * levels sit more than ~37 kT from the root, the occupations round to 0 and 1 and every
+ * point of that gap is a root in double precision: g is then exact, lambda_f any point
+ * of it. Synchronises. Errors: SPARC_ERR_ARG (NULL pointers, ns <= 0, nelec or kT out of
+ * range), SPARC_ERR_NONFINITE (an eigenvalue is NaN or Inf; outputs unset),
+ * SPARC_ERR_TIMEOUT (no convergence in 200 steps). */
+sparc_status sparc_occupations(sparc_ctx *ctx, const double *lambda_host, int ns, double nelec,
+                               double kT, double *lambda_f_host, double *g_host);
+
+/* Electron density, Sec. 3.4 (the equation after Eq. OrbitalTransformation):
+ * rho[p] = (2 / h^3) sum_n g_n x_n[p]^2 over the ncols columns x_n of X (Euclidean-
+ * normalised orbitals, as sparc_orth_rr returns them; F64 or F32 block, accumulated in
+ * FP64). g_host: ncols occupations (host, copied before the call returns); rho: Nd
+ * doubles of caller-owned device memory, x fastest. Asynchronous. Errors: SPARC_ERR_ARG. */
+sparc_status sparc_density(sparc_ctx *ctx, sparc_dtype dtype, const void *X, int ncols, long ld,
+                           const double *g_host, double *rho);
+
+/* Non-local atomic force, Eq. (NonlocForce:Discrete) with Y and W of Eq. (NonLocForce:U:W),
+ * Algorithm non-localForceCalculation:
+ *     f_J = -4 sum_n g_n sum_lm gamma_Jl Y_Jnlm W_Jnlm,
+ *     Y_Jnlm = h^3 sum psi_n chi_Jlm,  W_Jnlm = h^3 sum (grad_h psi_n) chi_Jlm,
+ * over the projector support of atom J, grad_h the order-2n_o finite-difference gradient
+ * of Eq. (gradient:approximate) with zero-Dirichlet values. psi_n = x_n / h^(3/2), x_n the
+ * Euclidean-normalised columns of X: with that normalisation f_J is minus the derivative
+ * of E_nl = 2 sum_n g_n x_n^T V_nl x_n in R_J (the paper's density formula uses x_n
+ * itself). X: F64 or F32 block; g_host: ncols occupations (host); force_host: 3 natoms
+ * doubles (x, y, z per atom; untouched when the cluster has no atoms). FP64 arithmetic.
+ * Synchronises. Errors: SPARC_ERR_ARG. */
+sparc_status sparc_nonlocal_force(sparc_ctx *ctx, sparc_dtype dtype, const void *X, int ncols,
+                                  long ld, const double *g_host, double *force_host);
+
 /* ---- instrumentation ------------------------------------------------------------ */
 
 /* Phases timed by the context's profiler. */

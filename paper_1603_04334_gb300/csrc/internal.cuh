@@ -340,4 +340,26 @@ cudaError_t resid_f32(const float *X, const float *HX, long ld, long nd, int nco
 // flag |= 1 if any of n values is NaN or Inf
 cudaError_t check_finite(const double *a, long n, int *flag, cudaStream_t st);
 
+// ---- observables.cu -----------------------------------------------------------------
+// Fermi level of Eq. (FermiEnergyConstraintFormulation): *mu with 2 sum g_n = nelec, g
+// (ns values) the occupations at *mu; *status 0 converged, 1 not converged, 2 non-finite
+// eigenvalue. One CTA; lam, mu, g, status on the device.
+cudaError_t fermi_level(const double *lam, int ns, double nelec, double kT, double *mu,
+                        double *g, int *status, cudaStream_t st);
+// rho[p] = (2 / h^3) sum_n g_n X[p + n ld]^2, p < nd (g: ncols values on the device)
+template <typename T>
+cudaError_t density(const T *X, long ld, int ncols, long nd, const double *g, double h,
+                    double *rho, cudaStream_t st);
+// Weights w~_p of Eq. (gradient:approximate) for radius n_o (1/h included), zero beyond.
+struct GradCoef {
+    double w[kRadius + 1];
+};
+GradCoef grad_coef(int radius, double h);
+// Non-local force of Eq. (NonlocForce:Discrete): f (3 natoms) from the columns X, occupations
+// g (ncols) and gamma (4 natoms); yw: 16 natoms ncols doubles of workspace.
+template <typename T>
+cudaError_t nonlocal_force(const DevHam &H, const T *X, long ld, int ncols, const double *g,
+                           const double *gamma, const GradCoef &wg, double *yw, double *f,
+                           cudaStream_t st);
+
 }  // namespace sparc

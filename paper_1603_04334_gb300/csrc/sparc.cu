@@ -69,6 +69,8 @@ struct sparc_ctx {
     void *vc = nullptr;      size_t vc_bytes = 0;    // V_eff - vc_shift as FP32 pairs
     double vc_shift = 0.0;   bool vc_valid = false;
     int *flags = nullptr;                            // device status words
+    void *obs = nullptr;     size_t obs_bytes = 0;   // occupations, density and force data
+    std::vector<double> gamma;                       // KB coefficients, 4 per atom (host)
     double *pin = nullptr;                           // pinned host staging (2*1024+16)
     int *pin_i = nullptr;
     Profiler prof;
@@ -564,7 +566,7 @@ void free_ctx(sparc_ctx *c)
     if (!c) return;
     void *ps[] = {c->V, c->Vf, c->Vdf, c->atom_ptr, c->idx, c->ent_atom, c->chi, c->gchi, c->chi_f,
                   c->gchi_f, c->chi_df, c->uniq_node, c->uniq_ptr, c->ent_list, c->nl_atom, c->nl_gf, c->nl_gdf, c->C, c->hx, c->rotx, c->roth, c->part,
-                  c->tcws, c->dm, c->lz, c->bnd, c->bsc, c->vc, c->flags};
+                  c->tcws, c->dm, c->lz, c->bnd, c->bsc, c->vc, c->flags, c->obs};
     for (void *p : ps) dfree(p);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->prof.used) cudaEventDestroy(e);
@@ -579,6 +581,7 @@ sparc_status build_tables(sparc_ctx *ctx, const sparc_atoms *at)
     const int na = at->natoms;
     H.natoms = na;
     if (na == 0) return SPARC_OK;
+    ctx->gamma.assign(at->gamma, at->gamma + 4 * (size_t)na);
     double *R = nullptr, *G = nullptr;
     int *counts = nullptr;
     TRY(dmalloc(ctx, R, 3 * (size_t)na));
@@ -1068,6 +1071,84 @@ sparc_status sparc_selftest_timeout(sparc_ctx *ctx, int which)
         return SPARC_OK;
     }
     return fail(ctx, SPARC_ERR_ARG, "which must be 0 (mbarrier) or 1 (grid barrier), got %d", which);
+}
+
+
+// --- after the rotation: occupations, density, non-local force ---------------------------
+sparc_status sparc_occupations(sparc_ctx *ctx, const double *lambda_host, int ns, double nelec,
+                               double kT, double *lambda_f_host, double *g_host)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    ctx->err.clear();
+    if (!lambda_host || !lambda_f_host) return fail(ctx, SPARC_ERR_ARG, "lambda and lambda_f must not be NULL");
+    if (ns <= 0) return fail(ctx, SPARC_ERR_ARG, "ns must be positive (got %d)", ns);
+    if (!(kT > 0.0) || !std::isfinite(kT)) return fail(ctx, SPARC_ERR_ARG, "kT must be positive and finite");
+    if (!(nelec > 0.0) || !(nelec < 2.0 * ns))
+        return fail(ctx, SPARC_ERR_ARG, "N_e must lie in (0, 2 ns) = (0, %d) (got %g)", 2 * ns, nelec);
+    // workspace: lambda, g, mu, status
+    TRY(ensure(ctx, ctx->obs, ctx->obs_bytes, sizeof(double) * (2 * (size_t)ns + 2)));
+    double *lam = (double *)ctx->obs, *g = lam + ns, *mu = g + ns;
+    int *status = (int *)(mu + 1);
+    CK(cudaMemcpyAsync(lam, lambda_host, sizeof(double) * ns, cudaMemcpyHostToDevice, ctx->st));
+    { PHASE(SPARC_PHASE_OTHER); CK(fermi_level(lam, ns, nelec, kT, mu, g, status, ctx->st)); }
+    int st = 0;
+    CK(cudaMemcpyAsync(lambda_f_host, mu, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    if (g_host) CK(cudaMemcpyAsync(g_host, g, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (st == 2) return fail(ctx, SPARC_ERR_NONFINITE, "an eigenvalue is NaN or Inf");
+    if (st != 0) return fail(ctx, SPARC_ERR_TIMEOUT, "the Fermi-level iteration did not converge");
+    return SPARC_OK;
+}
+
+sparc_status sparc_density(sparc_ctx *ctx, sparc_dtype dtype, const void *X, int ncols, long ld,
+                           const double *g_host, double *rho)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    ctx->err.clear();
+    TRY(check_block(ctx, X, ncols, ld, "X"));
+    if (!g_host || !rho) return fail(ctx, SPARC_ERR_ARG, "g and rho must not be NULL");
+    if (dtype != SPARC_F64 && dtype != SPARC_F32) return fail(ctx, SPARC_ERR_ARG, "unknown dtype %d", (int)dtype);
+    TRY(ensure(ctx, ctx->obs, ctx->obs_bytes, sizeof(double) * (size_t)ncols));
+    double *g = (double *)ctx->obs;
+    CK(cudaMemcpyAsync(g, g_host, sizeof(double) * ncols, cudaMemcpyHostToDevice, ctx->st));
+    PHASE(SPARC_PHASE_OTHER);
+    if (dtype == SPARC_F64)
+        CK(density<double>((const double *)X, ld, ncols, ctx->H.nd, g, ctx->H.h, rho, ctx->st));
+    else
+        CK(density<float>((const float *)X, ld, ncols, ctx->H.nd, g, ctx->H.h, rho, ctx->st));
+    return SPARC_OK;
+}
+
+sparc_status sparc_nonlocal_force(sparc_ctx *ctx, sparc_dtype dtype, const void *X, int ncols,
+                                  long ld, const double *g_host, double *force_host)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    ctx->err.clear();
+    TRY(check_block(ctx, X, ncols, ld, "X"));
+    if (!g_host || !force_host) return fail(ctx, SPARC_ERR_ARG, "g and force must not be NULL");
+    if (dtype != SPARC_F64 && dtype != SPARC_F32) return fail(ctx, SPARC_ERR_ARG, "unknown dtype %d", (int)dtype);
+    const int na = ctx->H.natoms;
+    if (na == 0) return SPARC_OK;
+    // workspace: g, gamma, f, then the per (atom, column) projections y, w
+    const size_t nw = (size_t)ncols + 4 * (size_t)na + 3 * (size_t)na + 16 * (size_t)na * ncols;
+    TRY(ensure(ctx, ctx->obs, ctx->obs_bytes, sizeof(double) * nw));
+    double *g = (double *)ctx->obs, *gam = g + ncols, *f = gam + 4 * (size_t)na,
+           *yw = f + 3 * (size_t)na;
+    CK(cudaMemcpyAsync(g, g_host, sizeof(double) * ncols, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(gam, ctx->gamma.data(), sizeof(double) * 4 * na, cudaMemcpyHostToDevice,
+                       ctx->st));
+    const GradCoef wg = grad_coef(ctx->H.radius, ctx->H.h);
+    {
+        PHASE(SPARC_PHASE_OTHER);
+        if (dtype == SPARC_F64)
+            CK(nonlocal_force<double>(ctx->H, (const double *)X, ld, ncols, g, gam, wg, yw, f, ctx->st));
+        else
+            CK(nonlocal_force<float>(ctx->H, (const float *)X, ld, ncols, g, gam, wg, yw, f, ctx->st));
+    }
+    CK(cudaMemcpyAsync(force_host, f, sizeof(double) * 3 * na, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return SPARC_OK;
 }
 
 }  // extern "C"

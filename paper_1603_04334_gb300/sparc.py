@@ -38,7 +38,8 @@ EXPORTS = ("sparc_create", "sparc_destroy", "sparc_last_error", "sparc_get_veff"
            "sparc_profile_enable",
            "sparc_profile_read", "sparc_profile_reset", "sparc_launch_count",
            "sparc_gram_noalloc", "sparc_sync", "sparc_selftest_timeout",
-           "sparc_gram_tc", "sparc_device_bytes")
+           "sparc_gram_tc", "sparc_device_bytes", "sparc_occupations", "sparc_density",
+           "sparc_nonlocal_force")
 
 PHASES = ("stencil", "project", "scatter", "gram", "dense", "rotate", "other")
 
@@ -101,6 +102,9 @@ def load(build_if_missing: bool = True):
     L.sparc_selftest_timeout.argtypes = [vp, ip]
     # allocation-free G = A^T B: (A, B, nd, ncols, ld, G, stream)
     L.sparc_gram_noalloc.argtypes = [vp, vp, C.c_long, ip, C.c_long, vp, vp]
+    L.sparc_occupations.argtypes = [vp, dp, ip, C.c_double, C.c_double, dp, dp]
+    L.sparc_density.argtypes = [vp, ip, vp, ip, C.c_long, dp, vp]
+    L.sparc_nonlocal_force.argtypes = [vp, ip, vp, ip, C.c_long, dp, dp]
     for name in EXPORTS:
         f = getattr(L, name)
         if name != "sparc_last_error" and f.restype is not C.c_char_p:
@@ -292,6 +296,46 @@ class Context:
                                           _dtype_code(B), C.c_void_p(B.data_ptr()), ncols, ld,
                                           C.c_void_p(G.data_ptr())))
         return G
+
+    def occupations(self, lam, nelec: float, kT: float = 1e-3):
+        """Fermi level and occupations of the eigenvalues lam (host array):
+        returns (lambda_f, g)."""
+        lam, lp = _darr(lam)
+        g = np.zeros(lam.shape[0])
+        mu = C.c_double()
+        self._check(self._L.sparc_occupations(self._h, lp, lam.shape[0], float(nelec),
+                                              float(kT), C.byref(mu),
+                                              g.ctypes.data_as(C.POINTER(C.c_double))))
+        return mu.value, g
+
+    def density(self, X, g, rho=None):
+        """rho = (2 / h^3) sum_n g_n x_n^2 on the device (Nd doubles); returns rho."""
+        import torch
+        ncols, ld = _block(X, "X")
+        nd = self.info()["nd"]
+        if rho is None:
+            rho = torch.empty(nd, dtype=torch.float64, device=X.device)
+        if rho.dtype != torch.float64 or rho.numel() < nd or not rho.is_contiguous():
+            raise ValueError("rho must be a contiguous float64 tensor of Nd values")
+        g, gp = _darr(g)
+        if g.shape[0] != ncols:
+            raise ValueError("g needs one occupation per column")
+        self._check(self._L.sparc_density(self._h, _dtype_code(X), C.c_void_p(X.data_ptr()),
+                                          ncols, ld, gp, C.c_void_p(rho.data_ptr())))
+        return rho
+
+    def nonlocal_force(self, X, g) -> np.ndarray:
+        """Non-local force on each atom, shape (natoms, 3)."""
+        ncols, ld = _block(X, "X")
+        natoms = self.info()["natoms"]
+        g, gp = _darr(g)
+        if g.shape[0] != ncols:
+            raise ValueError("g needs one occupation per column")
+        f = np.zeros((max(natoms, 1), 3))
+        self._check(self._L.sparc_nonlocal_force(self._h, _dtype_code(X),
+                                                 C.c_void_p(X.data_ptr()), ncols, ld, gp,
+                                                 f.ctypes.data_as(C.POINTER(C.c_double))))
+        return f[:natoms]
 
     def chefsi_step(self, X, work, degree: int, bounds: Sequence[float],
                     want_resid: bool = True):
