@@ -353,7 +353,8 @@ def run_ours(args, rank, world, local_rank):
 
 def after_rotation(ctx, X, ritz, w, stream, fp64_peak_tflops: float, reps: int = 10) -> dict:
     """Times the steps after the rotation on the solved block, apart from the solve:
-    occupations and Fermi level (N_e = Ns, kT = 1e-3 Ha), density, non-local force. Each is
+    occupations and Fermi level (N_e = Ns, kT = 1e-3 Ha), density, non-local force, and the
+    electrostatic potential of that density (CG to a relative residual of 1e-10). Each is
     the median of `reps` CUDA-event timings on the context stream after 3 warm-up calls."""
     import torch
 
@@ -377,6 +378,15 @@ def after_rotation(ctx, X, ritz, w, stream, fp64_peak_tflops: float, reps: int =
     t_occ = timed(lambda: ctx.occupations(ritz, nelec, kT))
     t_rho = timed(lambda: ctx.density(X, g, rho))
     t_f = timed(lambda: ctx.nonlocal_force(X, g))
+    # electrostatic potential of the density with the atoms' pseudocharges (CG to 1e-10)
+    ctx.density(X, g, rho)
+    phi = torch.empty_like(rho)
+    pois = {}
+
+    def solve_phi():
+        _, pois["iters"], pois["relres"] = ctx.poisson(rho, phi, tol=1e-10)
+
+    t_p = timed(solve_phi)
     es = X.element_size()
     nsup = ctx.info()["nsupport"]
     rho_bytes = w.nd * w.ns * es + 8 * w.nd
@@ -390,7 +400,9 @@ def after_rotation(ctx, X, ritz, w, stream, fp64_peak_tflops: float, reps: int =
             "density_fp64_inst_frac": rho_fp64 / (t_rho / 1e3) / peak_inst,
             "force_ms": t_f,
             "force_fp64_inst_frac": f_fp64 / (t_f / 1e3) / peak_inst,
-            "support_entries": nsup}
+            "support_entries": nsup,
+            "poisson_ms": t_p, "poisson_cg_iters": pois["iters"],
+            "poisson_relres": pois["relres"]}
 
 
 # ----------------------------------------------------------------------------------

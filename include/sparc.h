@@ -215,6 +215,26 @@ sparc_status sparc_density(sparc_ctx *ctx, sparc_dtype dtype, const void *X, int
 sparc_status sparc_nonlocal_force(sparc_ctx *ctx, sparc_dtype dtype, const void *X, int ncols,
                                   long ld, const double *g_host, double *force_host);
 
+/* Electrostatic potential, Sec. 3.3: phi solves -(1/4 pi) L_h phi = rho + b - d (Eq.
+ * FD:PoissonDiscrete) with zero Dirichlet values, where
+ *   b = -(1/4 pi) L_h sum_J V_J (Eq. PseudochargeDiscrete, Algorithm
+ *       PseudochargeCalculation), V_J = -Z_J erf(|x - R_J| / rc_erf) / |x - R_J| the atoms'
+ *       local potential, evaluated at the grid nodes and at the n_o nodes beyond each
+ *       face; it integrates to -Z_J (the sign of the attractive V_J);
+ *   d = the charge correction of Eq. (Phi:correction) from the multipole boundary values
+ *       of Eq. (phi:BC:discrete), l_max = 6 (Sec. 4), |x| measured from the box centre
+ *       ((n_d - 1) h / 2 per axis).
+ * Conjugate gradients with a Jacobi preconditioner (the paper's block-Jacobi on one block
+ * per processor; here the diagonal) from phi = 0, until ||r|| <= tol ||rhs||.
+ * rho: Nd doubles (device, x fastest) or NULL for rho = 0; phi: Nd doubles (device,
+ * caller-owned) for the result; b_out: Nd doubles (device) for b, or NULL. Writes the
+ * iteration count and the final relative residual to *iters_host / *relres_host (each may
+ * be NULL). Needs the atoms' charges Z at sparc_create. Synchronises. Errors:
+ * SPARC_ERR_ARG (NULL phi, tol outside (0, 1), maxit <= 0, no Z), SPARC_ERR_TIMEOUT (the
+ * tolerance not reached in maxit iterations; phi holds the last iterate). */
+sparc_status sparc_poisson(sparc_ctx *ctx, const double *rho, double *phi, double tol, int maxit,
+                           double *b_out, int *iters_host, double *relres_host);
+
 /* ---- instrumentation ------------------------------------------------------------ */
 
 /* Phases timed by the context's profiler. */

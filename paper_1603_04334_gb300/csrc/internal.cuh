@@ -362,4 +362,16 @@ cudaError_t nonlocal_force(const DevHam &H, const T *X, long ld, int ncols, cons
                            const double *gamma, const GradCoef &wg, double *yw, double *f,
                            cudaStream_t st);
 
+// ---- poisson.cu -------------------------------------------------------------------
+// Bytes of device workspace poisson_solve needs for an n0 x n1 x n2 grid.
+size_t poisson_workspace(int n0, int n1, int n2, int radius);
+// Electrostatic potential: phi (Nd) from rho (Nd, or null for zero) and the pseudocharges
+// of the atoms R (3 natoms), Z (natoms) with the potential -Z erf(r/rc)/r; b_out (Nd, or
+// null) receives the pseudocharge density. CG to ||r|| <= tol ||rhs|| or maxit iterations;
+// *iters_host and *relres_host report them. Synchronises.
+cudaError_t poisson_solve(const DevHam &H, const double *R, const double *Z, int natoms,
+                          double rc, const double *rho, double *phi, double *b_out, double tol,
+                          int maxit, void *ws, int *iters_host, double *relres_host,
+                          cudaStream_t st);
+
 }  // namespace sparc

@@ -71,6 +71,9 @@ struct sparc_ctx {
     int *flags = nullptr;                            // device status words
     void *obs = nullptr;     size_t obs_bytes = 0;   // occupations, density and force data
     std::vector<double> gamma;                       // KB coefficients, 4 per atom (host)
+    std::vector<double> atomR, atomZ;                // positions and valence charges (host)
+    double rc_erf = 1.0;
+    void *pois = nullptr;    size_t pois_bytes = 0;  // electrostatics workspace
     double *pin = nullptr;                           // pinned host staging (2*1024+16)
     int *pin_i = nullptr;
     Profiler prof;
@@ -566,7 +569,7 @@ void free_ctx(sparc_ctx *c)
     if (!c) return;
     void *ps[] = {c->V, c->Vf, c->Vdf, c->atom_ptr, c->idx, c->ent_atom, c->chi, c->gchi, c->chi_f,
                   c->gchi_f, c->chi_df, c->uniq_node, c->uniq_ptr, c->ent_list, c->nl_atom, c->nl_gf, c->nl_gdf, c->C, c->hx, c->rotx, c->roth, c->part,
-                  c->tcws, c->dm, c->lz, c->bnd, c->bsc, c->vc, c->flags, c->obs};
+                  c->tcws, c->dm, c->lz, c->bnd, c->bsc, c->vc, c->flags, c->obs, c->pois};
     for (void *p : ps) dfree(p);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->prof.used) cudaEventDestroy(e);
@@ -582,6 +585,9 @@ sparc_status build_tables(sparc_ctx *ctx, const sparc_atoms *at)
     H.natoms = na;
     if (na == 0) return SPARC_OK;
     ctx->gamma.assign(at->gamma, at->gamma + 4 * (size_t)na);
+    ctx->atomR.assign(at->R, at->R + 3 * (size_t)na);
+    if (at->Z) ctx->atomZ.assign(at->Z, at->Z + (size_t)na);
+    ctx->rc_erf = at->rc_erf;
     double *R = nullptr, *G = nullptr;
     int *counts = nullptr;
     TRY(dmalloc(ctx, R, 3 * (size_t)na));
@@ -1148,6 +1154,41 @@ sparc_status sparc_nonlocal_force(sparc_ctx *ctx, sparc_dtype dtype, const void 
     }
     CK(cudaMemcpyAsync(force_host, f, sizeof(double) * 3 * na, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
+    return SPARC_OK;
+}
+
+sparc_status sparc_poisson(sparc_ctx *ctx, const double *rho, double *phi, double tol, int maxit,
+                           double *b_out, int *iters_host, double *relres_host)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    ctx->err.clear();
+    if (!phi) return fail(ctx, SPARC_ERR_ARG, "phi must not be NULL");
+    if (!(tol > 0.0) || !(tol < 1.0)) return fail(ctx, SPARC_ERR_ARG, "tol must lie in (0, 1)");
+    if (maxit <= 0) return fail(ctx, SPARC_ERR_ARG, "maxit must be positive (got %d)", maxit);
+    const int na = ctx->H.natoms;
+    if (na > 0 && ctx->atomZ.size() != (size_t)na)
+        return fail(ctx, SPARC_ERR_ARG, "the context was created without valence charges Z");
+    const DevHam &H = ctx->H;
+    // the solver's workspace, then the atoms' positions and charges
+    const size_t wb = (poisson_workspace(H.n0, H.n1, H.n2, H.radius) + 255) & ~(size_t)255;
+    TRY(ensure(ctx, ctx->pois, ctx->pois_bytes, wb + sizeof(double) * (4 * (size_t)na + 1)));
+    double *R = (double *)((unsigned char *)ctx->pois + wb);
+    double *Z = R + 3 * (size_t)na;
+    if (na > 0) {
+        CK(cudaMemcpyAsync(R, ctx->atomR.data(), sizeof(double) * 3 * na, cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaMemcpyAsync(Z, ctx->atomZ.data(), sizeof(double) * na, cudaMemcpyHostToDevice, ctx->st));
+    }
+    int it = 0;
+    double rel = 0.0;
+    {
+        PHASE(SPARC_PHASE_OTHER);
+        CK(poisson_solve(H, R, Z, na, ctx->rc_erf, rho, phi, b_out, tol, maxit, ctx->pois, &it,
+                         &rel, ctx->st));
+    }
+    if (iters_host) *iters_host = it;
+    if (relres_host) *relres_host = rel;
+    if (!(rel <= tol))
+        return fail(ctx, SPARC_ERR_TIMEOUT, "CG stopped at relative residual %.3e after %d iterations", rel, it);
     return SPARC_OK;
 }
 

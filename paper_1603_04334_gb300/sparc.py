@@ -39,7 +39,7 @@ EXPORTS = ("sparc_create", "sparc_destroy", "sparc_last_error", "sparc_get_veff"
            "sparc_profile_read", "sparc_profile_reset", "sparc_launch_count",
            "sparc_gram_noalloc", "sparc_sync", "sparc_selftest_timeout",
            "sparc_gram_tc", "sparc_device_bytes", "sparc_occupations", "sparc_density",
-           "sparc_nonlocal_force")
+           "sparc_nonlocal_force", "sparc_poisson")
 
 PHASES = ("stencil", "project", "scatter", "gram", "dense", "rotate", "other")
 
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True):
     L.sparc_occupations.argtypes = [vp, dp, ip, C.c_double, C.c_double, dp, dp]
     L.sparc_density.argtypes = [vp, ip, vp, ip, C.c_long, dp, vp]
     L.sparc_nonlocal_force.argtypes = [vp, ip, vp, ip, C.c_long, dp, dp]
+    L.sparc_poisson.argtypes = [vp, vp, vp, C.c_double, ip, vp, C.POINTER(C.c_int), dp]
     for name in EXPORTS:
         f = getattr(L, name)
         if name != "sparc_last_error" and f.restype is not C.c_char_p:
@@ -336,6 +337,27 @@ class Context:
                                                  C.c_void_p(X.data_ptr()), ncols, ld, gp,
                                                  f.ctypes.data_as(C.POINTER(C.c_double))))
         return f[:natoms]
+
+    def poisson(self, rho=None, phi=None, tol: float = 1e-10, maxit: int = 4000,
+                want_b: bool = False):
+        """Electrostatic potential on the device: returns (phi, iterations, relative
+        residual) and, with want_b, the pseudocharge density as a fourth item."""
+        import torch
+        nd = self.info()["nd"]
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if phi is None:
+            phi = torch.empty(nd, dtype=torch.float64, device=dev)
+        for t, name in ((rho, "rho"), (phi, "phi")):
+            if t is not None and (t.dtype != torch.float64 or t.numel() < nd or
+                                  not t.is_contiguous() or not t.is_cuda):
+                raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of Nd values")
+        b = torch.empty(nd, dtype=torch.float64, device=phi.device) if want_b else None
+        it, rel = C.c_int(), C.c_double()
+        self._check(self._L.sparc_poisson(
+            self._h, C.c_void_p(rho.data_ptr()) if rho is not None else None,
+            C.c_void_p(phi.data_ptr()), float(tol), int(maxit),
+            C.c_void_p(b.data_ptr()) if b is not None else None, C.byref(it), C.byref(rel)))
+        return (phi, it.value, rel.value, b) if want_b else (phi, it.value, rel.value)
 
     def chefsi_step(self, X, work, degree: int, bounds: Sequence[float],
                     want_resid: bool = True):
