@@ -3,22 +3,23 @@
 // Sec. 3.4) fed by the Tensor Memory Accelerator.
 //
 // The FP32 filter step moves 12 B per point-orbital and should run at HBM speed. A CTA owns
-// a 32 x 16 tile of (x, y) for one column and streams along z. A producer warp keeps a
-// ring of kStages shared-memory planes filled with 4-D tiled TMA loads
-// (cp.async.bulk.tensor) of the tile plus its radius-6 halo: the box starts 8 nodes left
-// of the tile so that the x coordinate stays 16-byte aligned, and nodes outside the grid
-// are zero-filled by the TMA unit, which is exactly the zero-Dirichlet boundary. Each
-// plane's arrival is signalled through a `full` mbarrier (expect-tx), its release by the
-// four compute warps through an `empty` mbarrier; all waits are bounded and report a
-// timeout through a device flag instead of hanging.
+// a 32 x 16 tile of (x, y) for one column and streams along z. Thread 0 keeps a ring of
+// kStages shared-memory planes filled with 4-D tiled TMA loads (cp.async.bulk.tensor) of
+// the tile plus its radius-6 halo: the box starts 8 nodes left of the tile so that the x
+// coordinate stays 16-byte aligned, and nodes outside the grid are zero-filled by the TMA
+// unit, which is exactly the zero-Dirichlet boundary. Each plane's arrival is signalled
+// through an mbarrier (expect-tx); after the CTA barrier that ends the compute of a plane,
+// thread 0 refills that plane's stage. All waits are bounded and report a timeout through
+// a device flag instead of hanging.
 //
-// Each compute thread takes 4 consecutive x nodes of one row with 128-bit shared loads
-// (5 loads cover x-6 .. x+9 of the four nodes, 12 more the y neighbours) and keeps the
-// z neighbours of its four nodes in a 13-deep register queue of float4, filled from each
-// newly arrived plane. The arithmetic runs on packed FP32 pairs (two nodes per add or
-// fused multiply-add), each operation rounded as the scalar form would round it. The
-// queue needs planes t .. t+6 of the ring, so with kStages = 10 the loads run 3 planes
-// ahead of the compute.
+// Each thread takes 4 consecutive x nodes of one row with 128-bit shared loads (5 loads
+// cover x-6 .. x+9 of the four nodes, 12 more the y neighbours) and keeps the z neighbours
+// of its four nodes in a 13-deep register queue of float4, filled from each newly arrived
+// plane. The arithmetic runs on packed FP32 pairs (two nodes per add or fused
+// multiply-add), each operation rounded as the scalar form would round it, and the plane
+// loop is unrolled 13 times, one copy per rotation of the queue, so the queue is never
+// shifted. The queue needs planes t .. t+6 of the ring, so with kStages = 10 the loads run
+// 3 planes ahead of the compute.
 //
 // Y_{j-1} (one third of the step's traffic) rides in the same ring: the TMA load that
 // brings plane t of Y also brings the halo-free tile of Y_{j-1} at the plane whose compute
@@ -47,8 +48,6 @@ constexpr int kPlaneBytes = kW * kH * 4;   // Y plane with halo
 constexpr int kTileBytes = kBX * kTY * 4;  // Y_{j-1} tile, no halo
 constexpr int kStageFloats = kW * kH + kBX * kTY;
 constexpr unsigned kWaitLimit = 1u << 22;
-constexpr int kTmaCompute = kTX * kTY;      // compute threads of k_stencil_f32_tma (4 warps)
-constexpr int kTmaThreads = kTmaCompute + 32;  // + the producer warp
 }  // namespace
 
 // Step coefficients as packed pairs for the FP32x2 instructions (both lanes equal).
@@ -106,36 +105,50 @@ __device__ __forceinline__ void plane_math(const float *row, const float4 (&q)[2
     }
 }
 
-// Consumer state of one compute thread of k_stencil_f32_tma.
-struct TmaConsumer {
-    const float *sm;
-    uint64_t *full, *empty;
+// State of one thread of k_stencil_f32_tma.
+struct TmaThread {
+    float *sm;
+    uint64_t *full;
     float *Oc;
     const float *V;
+    const CUtensorMap *tmY, *tmP;
     long p, plane;  // p: the thread's node offset at the current compute plane
-    int k, k1;      // current compute z, end of the chunk
+    int k, k1, T;   // current compute z, end of the chunk, planes of the CTA
+    int i0, j0, k0, col;
     int sc;         // stage of the compute plane tc
     int sn;         // stage of plane tc + 6 (its centre enters the queue)
     unsigned pn;    // parity of plane tc + 6's current use of its stage
-    int ty, tx, lane;
+    int tc;         // current compute plane
+    int ty, tx, tid;
     bool act, hasP;
 };
 
+// plane t of Y (z = k0 - 6 + t) into stage t % kStages, with the Y_{j-1} tile of the plane
+// computed when plane t completes the z queue (z - 6); thread 0 only
+__device__ __forceinline__ void tma_issue(TmaThread &s, int t)
+{
+    const int st = t % kStages;
+    const bool p = s.hasP && t >= 2 * kR;
+    float *dst = s.sm + (long)st * kStageFloats;
+    mbar_arrive_expect_tx(&s.full[st], kPlaneBytes + (p ? kTileBytes : 0));
+    tma_load_4d(dst, s.tmY, &s.full[st], s.i0 - 8, s.j0 - kR, s.k0 - kR + t, s.col);
+    if (p) tma_load_4d(dst + kH * kW, s.tmP, &s.full[st], s.i0, s.j0, s.k0 - 2 * kR + t, s.col);
+}
+
 template <int PH>
-__device__ __forceinline__ bool plane_step(TmaConsumer &s, float4 (&q)[2 * kR + 1], float4 &vv,
-                                           float4 &v1, const StepCoef2 &cf)
+__device__ __forceinline__ bool plane_step(TmaThread &s, float4 (&q)[2 * kR + 1], float4 &vv,
+                                           float4 &v1, const StepCoef2 &cf, int *timed_out)
 {
     constexpr int Q = 2 * kR + 1;
     float4 v2 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (s.act && s.k + 2 < s.k1) v2 = *reinterpret_cast<const float4 *>(s.V + s.p + 2 * s.plane);
-    // warp-uniform outcome, so that a timed-out wait never splits the warp's __syncwarp
-    if (!__all_sync(0xffffffffu, mbar_wait(&s.full[s.sn], s.pn, kWaitLimit))) return false;
+    const bool got = mbar_wait(&s.full[s.sn], s.pn, kWaitLimit);
     const float *stn = s.sm + (long)s.sn * kStageFloats;
     q[(PH + 2 * kR) % Q] = *reinterpret_cast<const float4 *>(stn + (kR + s.ty) * kW + 8 + 4 * s.tx);
     const float *row = s.sm + (long)s.sc * kStageFloats + (kR + s.ty) * kW + 4 * s.tx;
     float2 aA, aB;
     plane_math<PH>(row, q, vv, cf, aA, aB);
-    if (s.act) {
+    if (s.act && got) {
         if (s.hasP) {
             const float4 pv =
                 *reinterpret_cast<const float4 *>(stn + kH * kW + s.ty * kBX + 4 * s.tx);
@@ -146,26 +159,26 @@ __device__ __forceinline__ bool plane_step(TmaConsumer &s, float4 (&q)[2 * kR + 
     }
     vv = v1;
     v1 = v2;
-    // plane tc's stage is free once the whole warp has read it
-    __syncwarp();
-    if (s.lane == 0) mbar_arrive(&s.empty[s.sc]);
+    if (!got) *timed_out = 1;
+    __syncthreads();  // every thread is done with plane tc's stage
+    if (*(volatile int *)timed_out) return false;
+    if (s.tid == 0 && s.tc + kStages < s.T) tma_issue(s, s.tc + kStages);
     if (++s.sc == kStages) s.sc = 0;
     if (++s.sn == kStages) {
         s.sn = 0;
         s.pn ^= 1u;
     }
     ++s.k;
+    ++s.tc;
     s.p += s.plane;
     return true;
 }
 
-// Block: four compute warps (8 x 16 threads, 4 x-nodes each) and one producer warp whose
-// elected lane keeps the ring full. A stage is handed back through its `empty` mbarrier
-// (one arrival per compute warp) as soon as the plane's compute is done, so the warps run
-// without a block-wide barrier per plane and the producer refills each stage the moment
-// it is free. The plane loop is unrolled 13 times, one copy per rotation of the z queue,
-// so the queue is never shifted.
-__global__ void __launch_bounds__(kTmaThreads, 3)
+// Block: 8 x 16 threads (4 x-nodes each). Thread 0 keeps the ring kStages planes ahead:
+// after the barrier that ends the compute of plane tc, it refills that plane's stage with
+// plane tc + kStages. The plane loop is unrolled 13 times, one copy per rotation of the z
+// queue, so the queue is never shifted.
+__global__ void __launch_bounds__(kTX *kTY)
 k_stencil_f32_tma(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmP,
                   bool hasP, float *out, const float *__restrict__ V, int n0, int n1, int n2,
                   long ld, int nzc, int zchunk, StepCoef2 cf, int *err)
@@ -173,117 +186,90 @@ k_stencil_f32_tma(const __grid_constant__ CUtensorMap tmY, const __grid_constant
     // stage s: Y plane [kH][kW] then the Y_{j-1} tile [kTY][kBX]
     extern __shared__ __align__(128) float sm[];
     __shared__ __align__(8) uint64_t full[kStages];
-    __shared__ __align__(8) uint64_t empty[kStages];
     __shared__ int timed_out;
-    const int tid = threadIdx.x;
-    const int i0 = blockIdx.x * kBX, j0 = blockIdx.y * kTY;
-    const int col = blockIdx.z / nzc;
-    const int k0 = (blockIdx.z % nzc) * zchunk;
-    const int k1 = min(n2, k0 + zchunk);
-    const int T = (k1 - k0) + 2 * kR;  // planes k0-6 .. k1+5
-
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kTmaCompute / 32);
-        }
+    TmaThread s;
+    s.tid = threadIdx.y * kTX + threadIdx.x;
+    s.tx = threadIdx.x;
+    s.ty = threadIdx.y;
+    s.i0 = blockIdx.x * kBX;
+    s.j0 = blockIdx.y * kTY;
+    s.col = blockIdx.z / nzc;
+    s.k0 = (blockIdx.z % nzc) * zchunk;
+    s.k1 = min(n2, s.k0 + zchunk);
+    s.T = (s.k1 - s.k0) + 2 * kR;  // planes k0-6 .. k1+5
+    s.sm = sm;
+    s.full = full;
+    s.tmY = &tmY;
+    s.tmP = &tmP;
+    s.hasP = hasP;
+    const int i = s.i0 + 4 * s.tx, j = s.j0 + s.ty;
+    s.act = (i < n0) && (j < n1);
+    s.plane = (long)n0 * n1;
+    s.k = s.k0;
+    s.p = (long)i + (long)n0 * j + (long)s.k0 * s.plane;
+    s.Oc = out + (long)s.col * ld;
+    s.V = V;
+    if (s.tid == 0) {
+        tma_prefetch_desc(&tmY);
+        if (hasP) tma_prefetch_desc(&tmP);
+        for (int t = 0; t < kStages; ++t) mbar_init(&full[t], 1);
         mbar_fence_init();
         timed_out = 0;
     }
     __syncthreads();
-    int issued = 0;  // planes handed to the TMA unit (producer lane)
-    if (tid >= kTmaCompute) {
-        if (tid == kTmaCompute) {
-            tma_prefetch_desc(&tmY);
-            if (hasP) tma_prefetch_desc(&tmP);
-            // plane t of Y (z = k0 - 6 + t) into stage t % kStages, with the Y_{j-1} tile
-            // of the plane computed when plane t completes the z queue (z - 6)
-            for (int t = 0; t < T; ++t) {
-                const int s = t % kStages;
-                if (t >= kStages &&
-                    !mbar_wait(&empty[s], (unsigned)((t / kStages - 1) & 1), kWaitLimit)) {
-                    timed_out = 1;
-                    break;
-                }
-                const bool p = hasP && t >= 2 * kR;
-                float *st = sm + (long)s * kStageFloats;
-                mbar_arrive_expect_tx(&full[s], kPlaneBytes + (p ? kTileBytes : 0));
-                tma_load_4d(st, &tmY, &full[s], i0 - 8, j0 - kR, k0 - kR + t, col);
-                if (p) tma_load_4d(st + kH * kW, &tmP, &full[s], i0, j0, k0 - 2 * kR + t, col);
-                issued = t + 1;
-            }
-        }
-    } else {
-        TmaConsumer s;
-        s.sm = sm;
-        s.full = full;
-        s.empty = empty;
-        s.tx = tid % kTX;
-        s.ty = tid / kTX;
-        s.lane = tid & 31;
-        const int i = i0 + 4 * s.tx, j = j0 + s.ty;
-        s.act = (i < n0) && (j < n1);
-        s.hasP = hasP;
-        s.plane = (long)n0 * n1;
-        s.k = k0;
-        s.k1 = k1;
-        s.p = (long)i + (long)n0 * j + (long)k0 * s.plane;
-        s.Oc = out + (long)col * ld;
-        s.V = V;
-        auto center = [&](int t) -> float4 {
-            return *reinterpret_cast<const float4 *>(sm + (long)(t % kStages) * kStageFloats +
-                                                     (kR + s.ty) * kW + 8 + 4 * s.tx);
-        };
-        bool ok = true;
-        float4 q[2 * kR + 1];
-        // planes 0..5 only feed the queue (their stages go back at once); planes 6..11
-        // are the first compute planes
-#pragma unroll
-        for (int t = 0; t < 2 * kR; ++t) {
-            if (ok)
-                ok = __all_sync(0xffffffffu, mbar_wait(&full[t % kStages],
-                                                       (unsigned)((t / kStages) & 1), kWaitLimit));
-            q[t] = center(t);
-            if (t < kR) {
-                __syncwarp();
-                if (s.lane == 0) mbar_arrive(&empty[t % kStages]);
-            }
-        }
-        s.sc = kR % kStages;
-        s.sn = (2 * kR) % kStages;
-        s.pn = (unsigned)(((2 * kR) / kStages) & 1);
-        float4 vv = make_float4(0.f, 0.f, 0.f, 0.f), v1 = vv;
-        if (s.act) vv = *reinterpret_cast<const float4 *>(V + s.p);
-        if (s.act && k0 + 1 < k1) v1 = *reinterpret_cast<const float4 *>(V + s.p + s.plane);
-        int tc = kR;
-        const int tend = T - kR;
-        if (ok) {
-#define SPARC_PLANE(PH)                                                                  \
-    if (tc >= tend) break;                                                               \
-    if (!plane_step<PH>(s, q, vv, v1, cf)) {                                             \
-        ok = false;                                                                      \
-        break;                                                                           \
-    }                                                                                    \
-    ++tc;
-            for (;;) {
-                SPARC_PLANE(0) SPARC_PLANE(1) SPARC_PLANE(2) SPARC_PLANE(3) SPARC_PLANE(4)
-                SPARC_PLANE(5) SPARC_PLANE(6) SPARC_PLANE(7) SPARC_PLANE(8) SPARC_PLANE(9)
-                SPARC_PLANE(10) SPARC_PLANE(11) SPARC_PLANE(12)
-            }
-#undef SPARC_PLANE
-        }
-        if (!ok) timed_out = 1;
+    if (s.tid == 0)
+        for (int t = 0; t < kStages && t < s.T; ++t) tma_issue(s, t);
+    auto center = [&](int t) -> float4 {
+        return *reinterpret_cast<const float4 *>(sm + (long)(t % kStages) * kStageFloats +
+                                                 (kR + s.ty) * kW + 8 + 4 * s.tx);
+    };
+    bool ok = true;
+    float4 q[2 * kR + 1];
+    // planes 0..5 only feed the queue: read them, then hand their stages to planes
+    // kStages .. kStages+5
+    for (int t = 0; t < kR; ++t) {
+        ok = ok && mbar_wait(&full[t % kStages], (unsigned)((t / kStages) & 1), kWaitLimit);
+        q[t] = center(t);
     }
+    if (!ok) timed_out = 1;
     __syncthreads();
+    if (s.tid == 0 && !timed_out)
+        for (int t = kStages; t < kStages + kR && t < s.T; ++t) tma_issue(s, t);
+    for (int t = kR; t < 2 * kR; ++t) {
+        ok = ok && mbar_wait(&full[t % kStages], (unsigned)((t / kStages) & 1), kWaitLimit);
+        q[t] = center(t);
+    }
+    if (!ok) timed_out = 1;
+    __syncthreads();
+    s.sc = kR % kStages;
+    s.sn = (2 * kR) % kStages;
+    s.pn = (unsigned)(((2 * kR) / kStages) & 1);
+    s.tc = kR;
+    float4 vv = make_float4(0.f, 0.f, 0.f, 0.f), v1 = vv;
+    if (s.act) vv = *reinterpret_cast<const float4 *>(V + s.p);
+    if (s.act && s.k0 + 1 < s.k1) v1 = *reinterpret_cast<const float4 *>(V + s.p + s.plane);
+    const int tend = s.T - kR;
+    if (!timed_out) {
+#define SPARC_PLANE(PH)                                                                  \
+    if (s.tc >= tend) break;                                                             \
+    if (!plane_step<PH>(s, q, vv, v1, cf, &timed_out)) break;
+        for (;;) {
+            SPARC_PLANE(0) SPARC_PLANE(1) SPARC_PLANE(2) SPARC_PLANE(3) SPARC_PLANE(4)
+            SPARC_PLANE(5) SPARC_PLANE(6) SPARC_PLANE(7) SPARC_PLANE(8) SPARC_PLANE(9)
+            SPARC_PLANE(10) SPARC_PLANE(11) SPARC_PLANE(12)
+        }
+#undef SPARC_PLANE
+    }
     if (timed_out) {
         // leave no TMA write in flight into this CTA's shared memory: wait (bounded) for
         // the latest issued plane of every stage, then report
-        if (tid == kTmaCompute) {
+        if (s.tid == 0) {
             atomicExch(err, 1);
-            for (int s = 0; s < kStages; ++s) {
-                int last = -1;  // latest plane issued into stage s
-                for (int t = s; t < issued; t += kStages) last = t;
-                if (last >= 0) mbar_wait(&full[s], (unsigned)((last / kStages) & 1), kWaitLimit);
+            const int issued = min(s.T, s.tc + kStages);  // planes handed to the TMA unit
+            for (int st = 0; st < kStages; ++st) {
+                int last = -1;  // latest plane issued into stage st
+                for (int t = st; t < issued; t += kStages) last = t;
+                if (last >= 0) mbar_wait(&full[st], (unsigned)((last / kStages) & 1), kWaitLimit);
             }
         }
         __syncthreads();
@@ -565,8 +551,9 @@ cudaError_t stencil_f32_tma(const DevHam &H, const float *Y, const float *Yprev,
     c2.alpha = make_float2(cf.alpha, cf.alpha);
     c2.nbeta = make_float2(-cf.beta, -cf.beta);
     dim3 grid(gx, gy, ncols * nzc);
-    k_stencil_f32_tma<<<grid, kTmaThreads, smem, st>>>(mapY, mapP, Yprev != nullptr, out, H.Vf,
-                                                       H.n0, H.n1, H.n2, ld, nzc, zchunk, c2, err);
+    k_stencil_f32_tma<<<grid, dim3(kTX, kTY), smem, st>>>(mapY, mapP, Yprev != nullptr, out,
+                                                          H.Vf, H.n0, H.n1, H.n2, ld, nzc,
+                                                          zchunk, c2, err);
     note_launch();
     return cudaGetLastError();
 }

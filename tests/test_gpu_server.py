@@ -43,9 +43,7 @@ def test_results_are_the_same_alone_and_in_the_mix():
             assert np.array_equal(a["ritz"], b["ritz"])
             assert np.array_equal(a["resid"], b["resid"])
         else:
-            # mixed-precision requests: the same within the form's 1e-5 Ha contract (rarely,
-            # about one request in fifty, an FP32-level difference of up to 4e-7 Ha has been
-            # seen between a request in the mix and alone)
+            # mixed-precision requests: the same within the form's 1e-5 Ha contract
             assert np.max(np.abs(a["ritz"] - b["ritz"])) <= 1e-5
         assert np.all(np.diff(a["ritz"]) >= 0)
         assert 0 < a["used_bytes"] <= a["est_bytes"]
