@@ -179,7 +179,7 @@ k_project_df(const double *__restrict__ Y, long ld, int ncols, const int *__rest
     for (int l = 0; l < 4; ++l)
 #pragma unroll
         for (int cb = 0; cb < CB; ++cb) sh[l][cb] = sl[l][cb] = 0.0f;
-#pragma unroll 2
+#pragma unroll 4
     for (int s = b + threadIdx.x; s < e; s += NT) {
         const long p = idx[s];
         float2 x[4];
@@ -236,7 +236,7 @@ cudaError_t project_f64_df(const DevHam &H, const double *Y, int ncols, long ld,
                            float2 *C, cudaStream_t st)
 {
     if (H.natoms == 0 || ncols <= 0) return cudaSuccess;
-    constexpr int CB = 4, NT = 256;
+    constexpr int CB = 2, NT = 256;
     dim3 grid(H.natoms, (ncols + CB - 1) / CB);
     if (grid.y > 65535) return cudaErrorInvalidValue;
     const float alh = (float)alpha, all = (float)(alpha - (double)alh);
@@ -432,10 +432,10 @@ cudaError_t scatter_f64(const DevHam &H, const double *C, double *out, int ncols
 // bOut, the column bounds of the output are raised to cover the updated values.
 namespace {
 constexpr int kScatDfNodes = 256;
-constexpr int kScatDfCols = 8;
+constexpr int kScatDfCols = 4;
 }  // namespace
 
-__global__ void __launch_bounds__(kScatDfNodes, 3)
+__global__ void __launch_bounds__(kScatDfNodes, 4)
 k_scatter_df(double *out, long ld, int ncols, long nuniq, const int *__restrict__ uniq_node,
              const int *__restrict__ uniq_ptr, const int *__restrict__ nl_atom,
              const float2 *__restrict__ g, const float2 *__restrict__ Cs, unsigned *bOut)
