@@ -843,6 +843,22 @@ cudaError_t rotate_tc(const double *Y, long ldy, long nd, int ns, const double *
     return cudaGetLastError();
 }
 
+__global__ void k_add_into(double *__restrict__ dst, const double *__restrict__ src, long n)
+{
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long)gridDim.x * blockDim.x)
+        dst[t] += src[t];
+}
+
+cudaError_t add_into(double *dst, const double *src, long n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const long b = (n + 255) / 256;
+    k_add_into<<<(unsigned)(b < 1216 ? b : 1216), 256, 0, st>>>(dst, src, n);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template cudaError_t gram_tc_pair<float, double>(const float *, long, const double *, long, long,
                                                  int, double *, double *, void *, size_t, int *,
                                                  cudaStream_t);

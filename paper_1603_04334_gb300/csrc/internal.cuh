@@ -237,13 +237,23 @@ size_t gram_tc47_workspace(long nd, int ns);
 // out = Y C (C: ns x ns FP64, column-major) on the tensor cores in the 47-bit digit form;
 // ws: rotate_tc_workspace(nd, ns) bytes.
 size_t rotate_tc_workspace(long nd, int ns);
-// The FP64 form's Gram and rotation run on the tensor cores while their digit workspace (12
-// bytes per element of both operands) stays within 24 GB; larger blocks keep FP32-pair
-// arithmetic on the CUDA cores.
-inline bool fp64_on_tensor_cores(long nd, int ns)
+// Rows per slab of the FP64 form's tensor-core Gram and rotation: the whole block when the
+// digit workspace (12 bytes per element of both operands) stays within 24 GB, else the
+// largest multiple of 256 rows, halving from nd, that does. Larger blocks are processed
+// slab by slab: the Grams of the slabs are summed (slabs start on 128-row chunk boundaries,
+// so every slab's digits are those the whole-block call would form) and the rotation's rows
+// are independent.
+inline long fp64_tc_slab_rows(long nd, int ns)
 {
-    return gram_tc47_workspace(nd, ns) <= ((size_t)24 << 30);
+    const size_t cap = (size_t)24 << 30;
+    long rows = nd;
+    while (rows > 256 &&
+           (gram_tc47_workspace(rows, ns) > cap || rotate_tc_workspace(rows, ns) > cap))
+        rows = (rows / 2 + 255) / 256 * 256;
+    return rows;
 }
+// dst[i] += src[i], i < n
+cudaError_t add_into(double *dst, const double *src, long n, cudaStream_t st);
 cudaError_t rotate_tc(const double *Y, long ldy, long nd, int ns, const double *C, double *out,
                       long ldo, void *ws, size_t ws_bytes, int *err, cudaStream_t st);
 cudaError_t gram_tc47_pair(const double *A, long lda, const double *B, long ldb, long nd, int ns,

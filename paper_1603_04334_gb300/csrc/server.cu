@@ -252,14 +252,12 @@ size_t sparc_request_bytes(const sparc_request *q)
     if (q->dtype == SPARC_F32) {
         b += gram_tc_workspace(nd, ns, false, true);
     } else {
-        // 47-bit tensor-core Gram and rotation (one workspace) or, for large blocks, the
-        // FP32-pair Gram's partials; column bounds of the filter's blocks, V_eff - shift pairs
-        if (fp64_on_tensor_cores(nd, ns)) {
-            const size_t wg = gram_tc47_workspace(nd, ns), wr = rotate_tc_workspace(nd, ns);
-            b += wg > wr ? wg : wr;
-        } else {
-            b += sizeof(double) * (size_t)gram_part_elems(ns, nd);
-        }
+        // 47-bit tensor-core Gram and rotation (one workspace, sized for a slab of rows, and
+        // the slab Grams' sums); column bounds of the filter's blocks, V_eff - shift pairs
+        const long slab = fp64_tc_slab_rows(nd, ns);
+        const size_t wg = gram_tc47_workspace(slab, ns), wr = rotate_tc_workspace(slab, ns);
+        b += wg > wr ? wg : wr;
+        if (slab < nd) b += sizeof(double) * 2 * (size_t)ns * ns;
         b += sizeof(unsigned) * ((size_t)(q->degree + 1) * ns + (size_t)ns);
         b += 8 * (size_t)nd;
     }

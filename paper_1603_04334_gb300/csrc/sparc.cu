@@ -421,19 +421,26 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
     // M_s = Yf^T Yf, H_s = Yf^T (H Yf)
     DenseBufs d;
     TRY(dense_bufs(ctx, ns, d));
-    const bool tc64 = sizeof(T) == 8 && fp64_on_tensor_cores(nd, ns);
+    // FP64 form: both contractions on the tensor cores in the 47-bit digit form (gram_tc.cu),
+    // slab by slab where the whole block's digits would exceed the workspace cap; the
+    // rotations below reuse the workspace
+    const bool tc64 = sizeof(T) == 8;
+    const long slab = tc64 ? fp64_tc_slab_rows(nd, ns) : nd;
     if (tc64) {
-        // both contractions on the tensor cores in the 47-bit digit form (gram_tc.cu); the
-        // rotations below reuse the workspace
-        const size_t wg = gram_tc47_workspace(nd, ns), wr = rotate_tc_workspace(nd, ns);
+        const size_t wg = gram_tc47_workspace(slab, ns), wr = rotate_tc_workspace(slab, ns);
         TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, wg > wr ? wg : wr));
-        { PHASE(SPARC_PHASE_GRAM); CK(gram_tc47_pair((const double *)Yf, ld, HX, ld, nd, ns, d.M, d.Hs, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st)); }
-    } else if (sizeof(T) == 8) {
-        // blocks whose digit workspace would be too large: FP32-pair Grams (gram_df.cu)
-        TRY(ensure(ctx, ctx->part, ctx->part_bytes, sizeof(double) * (size_t)gram_part_elems(ns, nd)));
-        double *part = (double *)ctx->part;
-        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64((const double *)Yf, ld, (const double *)Yf, ld, nd, ns, d.M, part, ctx->st, true)); }
-        { PHASE(SPARC_PHASE_GRAM); CK(gram_f64((const double *)Yf, ld, HX, ld, nd, ns, d.Hs, part, ctx->st, true)); }
+        const size_t nn = (size_t)ns * ns;
+        if (slab < nd) TRY(ensure(ctx, ctx->part, ctx->part_bytes, sizeof(double) * 2 * nn));
+        PHASE(SPARC_PHASE_GRAM);
+        for (long r0 = 0; r0 < nd; r0 += slab) {
+            const long rows = nd - r0 < slab ? nd - r0 : slab;
+            double *Mo = r0 ? (double *)ctx->part : d.M, *Ho = r0 ? (double *)ctx->part + nn : d.Hs;
+            CK(gram_tc47_pair((const double *)Yf + r0, ld, HX + r0, ld, rows, ns, Mo, Ho, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st));
+            if (r0) {
+                CK(add_into(d.M, Mo, (long)nn, ctx->st));
+                CK(add_into(d.Hs, Ho, (long)nn, ctx->st));
+            }
+        }
     } else {
         // mixed-precision form: both contractions on the tensor cores (gram_tc.cu)
         TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, gram_tc_workspace(nd, ns, false, true)));
@@ -459,12 +466,11 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
         TRY(ensure(ctx, ctx->rotx, ctx->rotx_bytes, sizeof(T) * (size_t)ns * ld));
         xout = (T *)ctx->rotx;
     }
-    if (sizeof(T) == 8)
-    {
-        if (tc64) { PHASE(SPARC_PHASE_ROTATE); CK(rotate_tc((const double *)Yf, ld, nd, ns, d.Cf, (double *)xout, ld, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st)); }
-        else { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64((const double *)Yf, ld, nd, ns, d.Cf, (double *)xout, ld, ctx->st)); }
-    }
-    else
+    if (sizeof(T) == 8) {
+        PHASE(SPARC_PHASE_ROTATE);
+        for (long r0 = 0; r0 < nd; r0 += slab)
+            CK(rotate_tc((const double *)Yf + r0, ld, nd - r0 < slab ? nd - r0 : slab, ns, d.Cf, (double *)xout + r0, ld, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st));
+    } else
         { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f32((const float *)Yf, ld, nd, ns, d.Cf, (float *)xout, ld, ctx->st)); }
     if (resid_host) {
         // H X = (H Y_f) (L^-T Q); residuals against the rotated block. The FP32 form rotates
@@ -472,8 +478,11 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
         TRY(ensure(ctx, ctx->roth, ctx->roth_bytes, sizeof(T) * (size_t)ns * ld));
         if (sizeof(T) == 8) {
             double *hxr = (double *)ctx->roth;
-            if (tc64) { PHASE(SPARC_PHASE_ROTATE); CK(rotate_tc(HX, ld, nd, ns, d.Cf, hxr, ld, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st)); }
-            else { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64(HX, ld, nd, ns, d.Cf, hxr, ld, ctx->st)); }
+            {
+                PHASE(SPARC_PHASE_ROTATE);
+                for (long r0 = 0; r0 < nd; r0 += slab)
+                    CK(rotate_tc(HX + r0, ld, nd - r0 < slab ? nd - r0 : slab, ns, d.Cf, hxr + r0, ld, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st));
+            }
             { PHASE(SPARC_PHASE_OTHER); CK(resid_f64((const double *)xout, hxr, ld, nd, ns, d.ritz, d.resid, ctx->st)); }
         } else {
             float *hxr = (float *)ctx->roth;
