@@ -21,6 +21,8 @@
 #include "grid.cuh"
 #include "internal.cuh"
 
+#include <atomic>
+
 namespace sparc {
 
 namespace {
@@ -338,7 +340,7 @@ __global__ void k_newton_schulz_coef(double *C, int n)
         C[t] = ((t % n) == (t / n) ? 1.5 : 0.0) - 0.5 * C[t];
 }
 
-static int g_chol_blocks = 0;  // co-resident CTAs of k_chol_grid (queried once)
+static std::atomic<int> g_chol_blocks{0};  // co-resident CTAs of k_chol_grid (queried once)
 
 cudaError_t dense_rr(double *M, double *Hs, int ns, double *ritz, double *Cf, double *work,
                      int *status, cudaStream_t st)
@@ -359,7 +361,7 @@ cudaError_t dense_rr(double *M, double *Hs, int ns, double *ritz, double *Cf, do
     GridBarrier *bar = (GridBarrier *)(status + 8);
     int *status32 = status + 13;  // FP32 phase: running out of sweeps only shortens its help
     cudaError_t e;
-    if (g_chol_blocks == 0) {
+    if (g_chol_blocks.load(std::memory_order_acquire) == 0) {
         int dev = 0, sms = 0, per = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
@@ -367,11 +369,12 @@ cudaError_t dense_rr(double *M, double *Hs, int ns, double *ritz, double *Cf, do
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_grid, CT, 0)) !=
             cudaSuccess)
             return e;
-        g_chol_blocks = sms * (per > 0 ? per : 1);
+        g_chol_blocks.store(sms * (per > 0 ? per : 1), std::memory_order_release);
     }
     long want = (nn / 2 + CT - 1) / CT;
     if (want < 1) want = 1;
-    int G0 = (int)(want < g_chol_blocks ? want : g_chol_blocks);
+    const int cb = g_chol_blocks.load(std::memory_order_acquire);
+    int G0 = (int)(want < cb ? want : cb);
     if (G0 > 152) G0 = 152;
     if ((e = cudaMemsetAsync(status, 0, sizeof(int), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return e;

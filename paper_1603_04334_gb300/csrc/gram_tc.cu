@@ -36,6 +36,8 @@
 // kernel raises *err, drains its copies and MMAs (bounded), frees its tensor memory and
 // returns.
 #include "internal.cuh"
+
+#include <atomic>
 #include "tma.cuh"
 
 #include <cstdint>
@@ -639,13 +641,13 @@ static cudaError_t tc_digits(const T *X, long ld, long nd, int ns, const TcPlan 
 template <class C>
 static cudaError_t tc_prepare(const TcPlan &p, bool sym, int2 *tiles, cudaStream_t st)
 {
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};  // set once (several host threads may launch)
     cudaError_t e;
-    if (!attr_set) {
+    if (!attr_set.load(std::memory_order_acquire)) {
         e = cudaFuncSetAttribute(k_gram_tc<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TcDims<C>::kSmemBytes);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set.store(true, std::memory_order_release);
     }
     static thread_local int2 host_tiles[64 * 65 / 2 + 64 * 64];
     if (p.ntiles > (int)(sizeof(host_tiles) / sizeof(int2))) return cudaErrorInvalidValue;
@@ -814,13 +816,13 @@ cudaError_t rotate_tc(const double *Y, long ldy, long nd, int ns, const double *
     int *EA = (int *)take(p.ea_bytes);
     __nv_bfloat16 *DB = (__nv_bfloat16 *)take(p.db_bytes);
     int *EB = (int *)take(p.eb_bytes);
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};  // set once (several host threads may launch)
     cudaError_t e;
-    if (!attr_set) {
+    if (!attr_set.load(std::memory_order_acquire)) {
         e = cudaFuncSetAttribute(k_gram_tc<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TcDims<C>::kSmemBytes);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set.store(true, std::memory_order_release);
     }
     {   // A = C: K = Ns rows, M = Ns columns
         dim3 grid(p.ns_pad / 8, (unsigned)p.nchunk);

@@ -23,6 +23,8 @@
 #include "grid.cuh"
 #include "internal.cuh"
 
+#include <atomic>
+
 namespace sparc {
 
 namespace {
@@ -162,9 +164,9 @@ static cudaError_t jacobi_grid_t(T *A0, T *A1, T *V, T *diag, int n, GridBarrier
                                  int *status, int *sweeps_out, double eps, int max_sweeps,
                                  cudaStream_t st)
 {
-    static int coop_blocks = 0;  // co-resident CTAs of this instance (queried once)
+    static std::atomic<int> coop_blocks{0};  // co-resident CTAs of this instance (queried once)
     if (n <= 0 || n > kMaxDense) return cudaErrorInvalidValue;
-    if (coop_blocks == 0) {
+    if (coop_blocks.load(std::memory_order_acquire) == 0) {
         int dev = 0, sms = 0, per = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
@@ -172,7 +174,7 @@ static cudaError_t jacobi_grid_t(T *A0, T *A1, T *V, T *diag, int n, GridBarrier
         if (e != cudaSuccess) return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_jacobi_grid<T>, NT, 0);
         if (e != cudaSuccess) return e;
-        coop_blocks = sms * (per > 0 ? per : 1);
+        coop_blocks.store(sms * (per > 0 ? per : 1), std::memory_order_release);
     }
     const long half = (n + 1) / 2;
     // a round's FP64 work (the 2 x 2 blocks and the columns of V) spread over four times
@@ -180,7 +182,8 @@ static cudaError_t jacobi_grid_t(T *A0, T *A1, T *V, T *diag, int n, GridBarrier
     // cost of a barrier over more CTAs
     long want = 4 * ((half * half + NT - 1) / NT);
     if (want < 1) want = 1;
-    int G = (int)(want < coop_blocks ? want : coop_blocks);
+    const int cb = coop_blocks.load(std::memory_order_acquire);
+    int G = (int)(want < cb ? want : cb);
     if (G > 152) G = 152;
     cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;

@@ -30,6 +30,8 @@
 // Requirements (checked on the host, else the plain kernel of stencil.cu runs): n0 and ld
 // multiples of 4 and 16-byte aligned block pointers (TMA strides and float4 accesses).
 #include "internal.cuh"
+
+#include <atomic>
 #include "tma.cuh"
 
 #include <cudaTypedefs.h>
@@ -440,18 +442,18 @@ k_batch_stencil_tma(const BatchItem *__restrict__ items, int nitems, const Batch
     }
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::atomic<PFN_cuTensorMapEncodeTiled_v12000> g_encode{nullptr};
 
 static cudaError_t get_encoder()
 {
-    if (g_encode) return cudaSuccess;
+    if (g_encode.load(std::memory_order_acquire)) return cudaSuccess;
     cudaDriverEntryPointQueryResult q;
     void *fn = nullptr;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
                                                      cudaEnableDefault, &q);
     if (e != cudaSuccess) return e;
     if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    g_encode.store((PFN_cuTensorMapEncodeTiled_v12000)fn, std::memory_order_release);
     return cudaSuccess;
 }
 
@@ -468,10 +470,11 @@ cudaError_t encode_f32_maps(const DevHam &H, const float *base, int ncols, long 
     cuuint32_t estr[4] = {1, 1, 1, 1};
     cuuint32_t boxY[4] = {(cuuint32_t)kW, (cuuint32_t)kH, 1, 1};
     cuuint32_t boxP[4] = {(cuuint32_t)kBX, (cuuint32_t)kTY, 1, 1};
-    if (g_encode(&m[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)base, dims, strides, boxY,
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = g_encode.load(std::memory_order_acquire);
+    if (enc(&m[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)base, dims, strides, boxY,
                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
-        g_encode(&m[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)base, dims, strides, boxP,
+        enc(&m[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)base, dims, strides, boxP,
                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
@@ -489,13 +492,13 @@ cudaError_t batch_stencil_tma(const BatchItem *items, int nitems, const BatchTma
                               int *err, cudaStream_t st)
 {
     if (nitems <= 0) return cudaSuccess;
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};  // set once (several host threads may launch)
     const int smem = kStages * kStageFloats * 4;
-    if (!attr_set) {
+    if (!attr_set.load(std::memory_order_acquire)) {
         cudaError_t e = cudaFuncSetAttribute(k_batch_stencil_tma,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set.store(true, std::memory_order_release);
     }
     k_batch_stencil_tma<<<grid, dim3(kTX, kTY), smem, st>>>(items, nitems, cs, err);
     note_launch();
@@ -515,13 +518,13 @@ cudaError_t stencil_f32_tma(const DevHam &H, const float *Y, const float *Yprev,
 {
     cudaError_t e = get_encoder();
     if (e != cudaSuccess) return e;
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};  // set once (several host threads may launch)
     const int smem = kStages * kStageFloats * 4;
-    if (!attr_set) {
+    if (!attr_set.load(std::memory_order_acquire)) {
         e = cudaFuncSetAttribute(k_stencil_f32_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set.store(true, std::memory_order_release);
     }
     // both maps view a block as (x, y, z, column); they differ in base and box
     auto encode = [&](CUtensorMap *m, const float *base, cuuint32_t bx, cuuint32_t by) {
@@ -531,7 +534,7 @@ cudaError_t stencil_f32_tma(const DevHam &H, const float *Y, const float *Yprev,
                                  (cuuint64_t)ld * 4};
         cuuint32_t box[4] = {bx, by, 1, 1};
         cuuint32_t estr[4] = {1, 1, 1, 1};
-        return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)base, dims, strides, box,
+        return g_encode.load(std::memory_order_acquire)(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)base, dims, strides, box,
                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     };
