@@ -97,3 +97,13 @@ def test_oversize_request_is_rejected_and_shutdown_cancels_queue():
     srv.submit(_spec(48, 32, 0.3))
     srv.submit(_spec(48, 32, 0.3))
     srv.close()  # returns after the running request; the queued one is cancelled
+
+
+def test_fp64_estimate_caps_the_digit_workspace():
+    # 160^3 x 1024 FP64: the whole block's 47-bit digits would be about 100 GB; the Gram and
+    # rotation run in row slabs whose workspace stays within 24 GiB, so the estimate is the
+    # request's blocks and FP64 work arrays plus at most that
+    n, ns = 160, 1024
+    block = 8 * n ** 3 * ns
+    est = serve.request_bytes(_spec(n, ns, 0, dtype="f64"))
+    assert 4 * block < est < 4 * block + 1.1 * (24 << 30) + (1 << 30) + 4 * block // 16
