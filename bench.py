@@ -322,6 +322,10 @@ def run_ours(args, rank, world, local_rank):
         roof["traffic"] = tr["dram_bytes"]
         roof["traffic_launch"] = tr["launch"]
         roof["traffic_algorithmic_bytes"] = tr["algorithmic_bytes"]
+        if "issue_active" in tr:
+            # what bounds the kernel when DRAM does not: instruction issue in the same capture
+            roof["issue"] = {"issue_active": tr["issue_active"],
+                             "thread_inst_per_ptorb": tr["thread_inst_per_ptorb"]}
     if dtype == "f64":
         # The FP64 step runs on the integer and FP32 pipes (exact integer neighbour sums,
         # FP32-pair scaling); its FP64-equivalent flop rate is compared with the FP64
