@@ -16,8 +16,15 @@ Under torchrun (N > 1) each rank solves its own replica on its own GPU (replicas
 the path has no data exchange), times are max-reduced over ranks and `value` sums the
 ranks' work.
 
+Two more objects follow on one GPU (N = 1): `mixed160`, the large cluster (160^3, 400 atoms,
+Ns = 1024, degree 24) solved in the mixed-precision form and in the FP64 form on the same
+GPU from the same start (times, speed-up, Ritz-value differences of the converged states),
+and `serving`, the request loop under Poisson arrivals (p50/p99 latency and throughput at
+the configured and at sub-saturation rates, beside serial FP64 solves). Together they take
+about 15-20 minutes; --no-mixed160 and --serving-requests 0 skip them.
+
 --impl reference times the FP64 CPU oracle instead (on the host cores, rank 0 only),
-each step a bounded sample of the same workload.
+each step one CheFSI iteration of the same workload on a column slice, set up once.
 """
 from __future__ import annotations
 
@@ -238,8 +245,7 @@ def run_ours(args, rank, world, local_rank):
 
     def solve(Xsrc):
         X.copy_(Xsrc, non_blocking=True)
-        lo, hi = ctx.lanczos_bounds(w.lanczos_k, args.seed)
-        b = sparc.first_bounds(lo, hi)
+        b = ctx.first_bounds(w.lanczos_k, args.seed)
         ritz = resid = None
         for it in range(w.iters):
             last = it == w.iters - 1 and not mixed
@@ -285,23 +291,35 @@ def run_ours(args, rank, world, local_rank):
     work = work_per_step(w, dtype) * args.steps * world
     value = job_value(work_per_step(w, dtype), args.steps, world, ms)
 
-    # ---- end-to-end: host block in pinned memory -> device each step ------------------
+    # ---- end-to-end: the start block from pinned host memory to the device and the
+    # solved orbitals (and Ritz values, residuals, bounds) back to the host, every step ---
     e2e = None
+    Xpin = Xout = Xres = None
     if not args.no_e2e:
         Xpin = torch.from_numpy(X0h).to(dtype=tdt).pin_memory()
-        solve(Xpin)
-        torch.cuda.synchronize()
+        Xres = X64 if mixed else X                  # the solve's result block
+        Xout = torch.empty(Xres.shape, dtype=Xres.dtype).pin_memory()
+
+        def e2e_step():
+            r = solve(Xpin)
+            Xout.copy_(Xres, non_blocking=True)
+            torch.cuda.current_stream(dev).synchronize()
+            return r
+
+        e2e_step()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            r_host, _ = solve(Xpin)
+            e2e_step()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         e_ms = reduce_max((t1 - t0) * 1e3, world, dev)
-        es = 8 if dtype == "f64" else 4
+        n_rr = w.iters + (1 if mixed else 0)        # Rayleigh-Ritz steps per solve
         e2e = {"value": work / (e_ms / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(w.nd * w.ns * es),
-               "d2h_bytes_per_step": int(w.iters * (2 * w.ns * 8 + 4) + 2 * 8 + 4),
+               "h2d_bytes_per_step": int(Xpin.numel() * Xpin.element_size()),
+               # result block + per iteration Ritz values, residuals and flags + bounds
+               "d2h_bytes_per_step": int(Xout.numel() * Xout.element_size()
+                                         + n_rr * (2 * w.ns * 8 + 4) + 2 * 8 + 4),
                "ms_per_step": e_ms / args.steps}
 
     alg = stencil_algorithmic(w, dtype, prof, args.steps)
@@ -352,7 +370,165 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(w, args.seed, budget_s=args.cpu_budget)
     ctx.close()
+    del X, W, X0, X64, W64, Xpin, Xout, Xres
+    torch.cuda.empty_cache()
+    if world == 1 and not args.no_mixed160:
+        out["mixed160"] = mixed_vs_fp64(args.seed)
+        torch.cuda.empty_cache()
+    if world == 1 and args.serving_requests > 0:
+        out["serving"] = serving_study(args.seed, args.serving_requests)
     return out
+
+
+def mixed_vs_fp64(seed: int, resid_cut: float = 1e-4) -> dict:
+    """The large cluster (160^3 grid, h = 0.25 bohr, 400 atoms, Ns = 1024, degree 24, 20
+    iterations) solved in both forms on this GPU from the same start block: the mixed form
+    (Lanczos bounds, 20 FP32-filter iterations, one FP64 refinement iteration) and the FP64
+    form (Lanczos bounds, 20 FP64 iterations). Each solve is timed once with CUDA events on
+    the context stream, after one warm-up iteration of each form (workspaces, kernel
+    loading); the start block is drawn on the device (torch's seeded generator) before the
+    timing starts. Ritz values of the states the FP64 run has converged (residual <=
+    resid_cut) are compared with the mixed run's."""
+    import torch
+    from paper_1603_04334_gb300 import sparc
+
+    w = synth.preset("cluster160")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    cl = synth.make_cluster(w, seed)
+    ctx = sparc.Context(cl.n, cl.h, cl.R, cl.Z, cl.gamma, veff=None, sigma=cl.sigma,
+                        rcut=cl.rcut, rc_erf=cl.rc_erf, stream=stream)
+    X32 = torch.empty((w.ns, w.nd), dtype=torch.float32, device=dev)
+    W32 = torch.empty_like(X32)
+    X64 = torch.empty((w.ns, w.nd), dtype=torch.float64, device=dev)
+    W64 = torch.empty_like(X64)
+
+    def start():
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed + 1)
+        X64.uniform_(-0.5, 0.5, generator=g)
+
+    b0 = ctx.first_bounds(w.lanczos_k, seed)
+    # warm-up: one iteration of each form
+    start()
+    X32.copy_(X64)
+    ctx.chefsi_step(X32, W32, w.degree, b0, want_resid=False)
+    start()
+    ctx.chefsi_step(X64, W64, w.degree, b0, want_resid=True)
+    torch.cuda.synchronize()
+
+    def timed(run):
+        ck = ClockSampler(torch.cuda.current_device())
+        ctx.profile_reset()
+        ctx.profile_enable(True)
+        torch.cuda.synchronize()
+        ck.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = ck.stop()
+        ctx.profile_enable(False)
+        ph = {k: round(v[1], 1) for k, v in ctx.profile_read().items()}
+        return r, e0.elapsed_time(e1) / 1e3, ph, clocks
+
+    def mixed():
+        b = ctx.first_bounds(w.lanczos_k, seed)
+        for _ in range(w.iters):
+            _, _, b = ctx.chefsi_step(X32, W32, w.degree, b, want_resid=False)
+        X64.copy_(X32)
+        return ctx.chefsi_step(X64, W64, w.degree, b, want_resid=True)
+
+    def fp64():
+        b = ctx.first_bounds(w.lanczos_k, seed)
+        r = None
+        for it in range(w.iters):
+            r = ctx.chefsi_step(X64, W64, w.degree, b, want_resid=it == w.iters - 1)
+            b = r[2]
+        return r
+
+    start()
+    X32.copy_(X64)
+    (rm, resm, _), t_m, ph_m, ck_m = timed(mixed)
+    start()
+    (r64, res64, _), t_64, ph_64, ck_64 = timed(fp64)
+    ctx.close()
+    del X32, W32, X64, W64
+    conv = res64 <= resid_cut
+    d = np.abs(rm - r64)
+    work_m = work_per_step(w, "f32")
+    work_64 = work_per_step(w, "f64")
+    return {"workload": workload_config(w, "f32")["workload"],
+            "mixed_s": t_m, "fp64_s": t_64, "speedup": t_64 / t_m,
+            "mixed_ptorb_per_s": work_m / t_m, "fp64_ptorb_per_s": work_64 / t_64,
+            "resid_cut": resid_cut, "converged_fp64": int(conv.sum()),
+            "converged_both": int((conv & (resm <= resid_cut)).sum()),
+            "max_abs_dritz_converged": float(d[conv].max()) if conv.any() else None,
+            "within_1e-5": bool(conv.any() and d[conv].max() <= 1e-5),
+            "max_abs_dritz_all": float(d.max()),
+            "dritz_converged_quantiles": ([float(q) for q in np.quantile(d[conv], [0.5, 0.9, 1.0])]
+                                          if conv.any() else None),
+            "ritz_lowest": [float(x) for x in r64[:3]],
+            "mixed_phases_ms": ph_m, "fp64_phases_ms": ph_64,
+            "clocks": {"mixed": ck_m, "fp64": ck_64},
+            "timing": "one timed solve of each form (CUDA events), after one warm-up iteration "
+                      "of each; start block drawn on the device before the timing"}
+
+
+def serving_study(seed: int, requests: int, rates=(400.0, 20.0), below=(0.5,),
+                  slots: int = 4, budget_gb: float = 150.0, serial_sample: int = 24) -> dict:
+    """The serving loop under Poisson arrivals: `requests` requests per rate, drawn from
+    seed (edge in {48..128}, h = 0.3, 4-200 atoms, Ns 32-512, degree 20, <= 15 iterations to
+    max residual 1e-4, mixed form), 4 slots, 150 GB budget. The configured rates (20 and
+    400 req/s) come first; they saturate the server and measure its capacity. Then rates
+    below saturation (the given fractions of that capacity). Beside them, the first
+    `serial_sample` requests solved one at a time in FP64 (one slot): their service times
+    and the serial throughput."""
+    from paper_1603_04334_gb300 import serve
+
+    specs = serve.draw_requests(requests, seed)
+    budget = int(budget_gb * 2 ** 30)
+
+    def point(rate):
+        t0 = time.perf_counter()
+        m = serve.run_arrivals(specs, rate, budget, slots, seed + 1)
+        lat = m["latency_s"]
+        res = m["results"]
+        return {"rate_req_per_s": rate, "requests": len(specs),
+                "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "mean_s": float(lat.mean()), "max_s": float(lat.max()),
+                "throughput_req_per_s": len(specs) / m["span_s"],
+                "max_running": m["stats"]["max_running"],
+                "peak_reserved_gb": m["stats"]["peak_reserved"] / 2 ** 30,
+                "converged": int(sum(r["converged"] for r in res)),
+                "failed": int(sum(r["status"] != 0 for r in res)),
+                "wall_s": time.perf_counter() - t0}
+
+    pts = [point(r) for r in rates]
+    cap = max(p["throughput_req_per_s"] for p in pts)
+    pts += [point(f * cap) for f in below]
+    base = []
+    srv = serve.Server(budget, 1)
+    try:
+        for s in specs[:serial_sample]:
+            f64 = serve.Spec(s.n, s.h, s.R, s.Z, s.gamma, s.ns, s.degree, s.max_iters, s.tol,
+                             s.seed, "f64")
+            r = srv.wait(srv.submit(f64))
+            base.append(r["t_done"] - r["t_admit"])
+    finally:
+        srv.close()
+    base = np.array(base)
+    return {"workload": "edge in {48,...,128}, h=0.3, atoms 4-200, Ns 32-512, degree 20, "
+                        "<= 15 CheFSI iterations to max residual 1e-4, mixed form",
+            "slots": slots, "budget_gb": budget_gb, "capacity_req_per_s": cap,
+            "points": pts,
+            "serial_fp64": {"requests": len(base),
+                            "throughput_req_per_s": len(base) / float(base.sum()),
+                            "service_p50_s": float(np.percentile(base, 50)),
+                            "service_p99_s": float(np.percentile(base, 99)),
+                            "sample": f"the first {len(base)} requests of the same list, one "
+                                      f"at a time in FP64 on one slot"}}
 
 
 def after_rotation(ctx, X, ritz, w, stream, fp64_peak_tflops: float, reps: int = 10) -> dict:
@@ -412,46 +588,109 @@ def after_rotation(ctx, X, ritz, w, stream, fp64_peak_tflops: float, reps: int =
 # ----------------------------------------------------------------------------------
 # the oracle (CPU baseline and the reference arm)
 # ----------------------------------------------------------------------------------
-def oracle_sample(w, seed: int, budget_s: float = 12.0, max_iters: int = 64) -> dict:
-    """Times the FP64 CPU oracle, as it stands, on a bounded sample of the workload:
-    CheFSI iterations (filter of degree m + Rayleigh-Ritz) on a 16-column slice of the
-    start block, repeated until `budget_s` seconds have passed."""
-    import oracle
+def host_cores() -> int:
+    """Host cores this process may run on (nproc)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
-    cl = synth.make_cluster(w, seed)
-    H = oracle.Hamiltonian.from_cluster(cl)
-    X = synth.initial_block(seed + 1, w.nd, w.ns)[:ORACLE_COLS].copy()
-    lo, hi, _ = H.lanczos_bounds(w.lanczos_k, seed)
-    b = oracle.chefsi_first_bounds(lo, hi)
-    t0 = time.perf_counter()
-    n = 0
-    while True:
-        X, ritz, res, b = oracle.chefsi_step(H, X, w.degree, b)
-        n += 1
-        if time.perf_counter() - t0 >= budget_s or n >= max_iters:
-            break
-    t = time.perf_counter() - t0
-    work = n * (w.degree + 1) * w.nd * X.shape[0]
-    cores = min(os.cpu_count() or 1, X.shape[0], int(os.environ.get("OMP_NUM_THREADS", "9999")))
-    return {"value": work / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} CheFSI iteration(s) (degree {w.degree} filter + RR) on a "
-                      f"{X.shape[0]}-column slice of {w.name}, {t:.1f} s, OpenMP over columns"}
+
+class OracleRun:
+    """The FP64 CPU oracle, as it stands, set up once on a column slice of a workload:
+    the Hamiltonian (V_eff, projector tables), the Lanczos bounds and the first filter
+    interval are built here, outside any timing; step() runs one CheFSI iteration (the
+    degree-m filter and the Rayleigh-Ritz step) on the slice."""
+
+    def __init__(self, w, seed: int, cols: int):
+        import oracle
+        self.oracle = oracle
+        self.w = w
+        cl = synth.make_cluster(w, seed)
+        self.H = oracle.Hamiltonian.from_cluster(cl)
+        self.X0 = synth.initial_block(seed + 1, w.nd, w.ns)[:cols].copy()
+        lo, hi, _ = self.H.lanczos_bounds(w.lanczos_k, seed)
+        self.b0 = oracle.chefsi_first_bounds(lo, hi)
+        self.reset()
+
+    @property
+    def cols(self) -> int:
+        return self.X0.shape[0]
+
+    def reset(self):
+        self.X, self.b = self.X0.copy(), list(self.b0)
+
+    def step(self):
+        self.X, _, _, self.b = self.oracle.chefsi_step(self.H, self.X, self.w.degree, self.b)
+
+    def work_per_step(self) -> int:
+        return (self.w.degree + 1) * self.w.nd * self.cols
+
+    def timed(self, budget_s: float, max_steps: int = 64, threads: int = 0):
+        """Iterations until budget_s has passed (at least one): (iterations, seconds)."""
+        from oracle import oracle as O
+        O.threads(threads)
+        self.reset()
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            self.step()
+            n += 1
+            if time.perf_counter() - t0 >= budget_s or n >= max_steps:
+                break
+        return n, time.perf_counter() - t0
+
+
+def oracle_sample(w, seed: int, budget_s: float = 12.0, single_budget_s: float = 6.0) -> dict:
+    """Times the FP64 CPU oracle, as it stands, on a bounded sample of the workload: CheFSI
+    iterations (filter of degree m + Rayleigh-Ritz) on a slice of the start block as wide as
+    the host has cores (at least 16 columns, at most Ns), with OpenMP over the slice's
+    columns on all cores; then one thread on a 4-column slice. Set-up (Hamiltonian, bounds)
+    is outside the timing."""
+    from oracle import oracle as O
+    nproc = host_cores()
+    cols = min(w.ns, max(ORACLE_COLS, nproc))
+    run = OracleRun(w, seed, cols)
+    n_all, t_all = run.timed(budget_s, threads=nproc)
+    one = OracleRun(w, seed, min(w.ns, 4))
+    n_one, t_one = one.timed(single_budget_s, threads=1)
+    O.threads(nproc)
+    per = run.work_per_step()
+    return {"value": n_all * per / t_all, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "nproc": nproc,
+            "sample": f"{n_all} CheFSI iteration(s) (degree {w.degree} filter + Rayleigh-Ritz) "
+                      f"on a {cols}-column slice of {w.name}, {t_all:.1f} s, OpenMP over the "
+                      f"slice's columns on all {nproc} host cores; set-up outside the timing",
+            "single_thread": {"value": n_one * one.work_per_step() / t_one, "unit": UNIT,
+                              "cores": 1,
+                              "sample": f"{n_one} iteration(s) on a {one.cols}-column slice, one "
+                                        f"thread, {t_one:.1f} s"}}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle as it stands on the host cores. The Hamiltonian, the
+    bounds and the slice are set up once outside the timing; W untimed and K timed steps,
+    each one CheFSI iteration (degree-m filter + Rayleigh-Ritz) on the slice."""
     if rank != 0:
         return None
+    from oracle import oracle as O
     w = synth.preset(args.workload)
     dtype = "f64"
+    nproc = host_cores()
+    cols = min(w.ns, max(ORACLE_COLS, nproc))
+    run = OracleRun(w, args.seed, cols)
+    O.threads(nproc)
     for _ in range(args.warmup):
-        oracle_sample(w, args.seed, budget_s=0.0, max_iters=1)
+        run.step()
     t0 = time.perf_counter()
-    samples = [oracle_sample(w, args.seed, budget_s=0.0, max_iters=1) for _ in range(args.steps)]
+    for _ in range(args.steps):
+        run.step()
     t = time.perf_counter() - t0
-    work = args.steps * (w.degree + 1) * w.nd * ORACLE_COLS
-    value = work / t
-    cb = dict(samples[-1])
-    cb["value"] = value
+    value = args.steps * run.work_per_step() / t
+    cb = {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle", "nproc": nproc,
+          "sample": f"{args.steps} CheFSI iteration(s) (degree {w.degree} filter + "
+                    f"Rayleigh-Ritz) on a {cols}-column slice of {w.name}, OpenMP over the "
+                    f"slice's columns on all {nproc} host cores; set-up outside the timing"}
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
@@ -472,6 +711,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-mixed160", action="store_true",
+                    help="skip the 160^3 mixed-vs-FP64 comparison")
+    ap.add_argument("--serving-requests", type=int, default=200,
+                    help="requests per arrival rate of the serving study (0: skip it)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not os.environ.get("SPARC_BENCH_ALLOW_SHORT"):
         args.warmup = 3

@@ -110,6 +110,18 @@ sparc_status sparc_apply_H(sparc_ctx *ctx, sparc_dtype dtype, const void *X, voi
 sparc_status sparc_lanczos_bounds(sparc_ctx *ctx, int ksteps, unsigned long long seed,
                                   double *lo, double *hi);
 
+/* Filter interval of the first CheFSI iteration (Sec. 4: the bounds of the spectrum from
+ * a few Lanczos steps, and a cutoff lambda_c below which the filter passes the spectrum).
+ * Runs sparc_lanczos_bounds(ctx, ksteps, seed, &lo, &hi) and writes
+ *     bounds_out[3] = [a, b, a0] = [lo + (hi - lo) / 4, hi, lo]   (host memory),
+ * the bounds_inout argument of the first sparc_chefsi_step. The paper's cutoff is
+ * lambda_c = E_F + 0.1 Ha, which a fixed Hamiltonian without electrons does not have; the
+ * quarter point is this library's choice. Later iterations take a and a0 from the Ritz
+ * values (sparc_chefsi_step updates bounds_inout). Errors: those of sparc_lanczos_bounds;
+ * SPARC_ERR_ARG for a NULL bounds_out or when lo == hi (no interval). Synchronises. */
+sparc_status sparc_first_bounds(sparc_ctx *ctx, int ksteps, unsigned long long seed,
+                                double *bounds_out);
+
 /* Chebyshev filter, Algorithm ChebychevFilter with Eq. (ChebFilter), Sec. 3.4:
  * X <- p_m(H) X with p_m(t) = C_m((t - c)/e) / C_m((a0 - c)/e), e = (b - a)/2,
  * c = (b + a)/2, m = degree (number of applications of H), using the scaled
@@ -131,10 +143,13 @@ sparc_status sparc_cheb_filter(sparc_ctx *ctx, sparc_dtype dtype, void *X, void 
  * Each column of Q is signed so that its largest-magnitude entry is positive.
  * On return Xf holds Euclidean-orthonormal Ritz vectors (ascending Ritz values),
  * ritz_host[ncols] the Ritz values, and resid_host[ncols] (if not NULL) the residual
- * norms ||H x_n - ritz_n x_n||_2. For dtype F32 the block stays FP32, H Xf is applied
- * in FP64, M_s and H_s come from the tensor-core contraction (see sparc_gram_tc) and the
- * eigensolve is FP64; the rotated H X of the residuals is then formed in FP32 arithmetic
- * (residuals good to about 1e-7 of ||H x_n||). HXf_or_null: optional FP64 device
+ * norms ||H x_n - ritz_n x_n||_2. M_s and H_s are formed on the tensor cores from the
+ * operands' 47-bit digits (each entry rounded to 2^-48 of the largest in its 128-row chunk,
+ * the digit products summed exactly): FP64-level for both dtypes. For dtype F32 the block
+ * stays FP32, H Xf is applied in FP64 and M_s, H_s and the eigensolve are FP64; the rotation
+ * and the rotated H X of the residuals run on the tensor cores in the 23-bit digit form with
+ * FP32 results (the block's own precision; residuals good to about 1e-7 of ||H x_n||).
+ * HXf_or_null: optional FP64 device
  * block (ncols x ld) used as the H Xf workspace; when NULL the context allocates one.
  * Fails with SPARC_ERR_NOT_SPD if M_s is not numerically positive definite and with
  * SPARC_ERR_NONFINITE on NaN/Inf, leaving Xf unrotated. ncols <= 1024. Synchronises. */
@@ -290,21 +305,24 @@ sparc_status sparc_selftest_timeout(sparc_ctx *ctx, int which);
 
 /* ---- allocation-free variant ---------------------------------------------------- */
 
-/* G = A^T B in FP64 without allocating any memory (the paper has no counterpart; it is
- * a service for callers that cannot call cudaMalloc where they call this: code inside a
- * CUDA stream capture, loops that forbid allocation after start-up, or hosts that hand
- * in buffers from their own pool). Same result as sparc_gram for FP64 inputs, up to the
- * order of the row-slice sums. A, B: device, nd rows x ncols columns, column-major,
- * leading dimension ld >= nd. G: device, ncols x ncols, column-major, overwritten.
- * Enqueued on `cuda_stream` (a cudaStream_t; NULL = legacy default stream); needs no
- * context. The row-slice partial sums live in a fixed 16 MiB __device__ array that every
- * GPU loading the library keeps until exit: ncols^2 must not exceed 2^21 (any
- * ncols <= 1024 fits), else SPARC_ERR_ARG. The first call on a device looks up that
- * array's address (cudaGetSymbolAddress) with the device current; make it before any
- * stream capture. All calls share the array: calls that overlap on the GPU race on it
- * and must be serialised. Each call overwrites every partial it reads, so no clearing is
- * needed. Returns SPARC_ERR_ARG for NULL pointers or bad sizes, SPARC_ERR_CUDA if the
- * lookup or the launch fails. */
+/* G = A^T B in FP64 without allocating any memory. The paper has no counterpart: this is a
+ * service for callers that cannot let the library call cudaMalloc where they call it --
+ * real-time loops that forbid allocation after start-up (an allocation can block and
+ * synchronise the device), hosts that carve all device memory out of their own pool, or
+ * processes that have already reserved nearly all of it. Same result as sparc_gram for FP64
+ * inputs, up to the order of the row-slice sums. A, B: device, nd rows x ncols columns,
+ * column-major, leading dimension ld >= nd. G: device, ncols x ncols, column-major,
+ * overwritten. Enqueued on `cuda_stream` (a cudaStream_t; NULL = legacy default stream);
+ * needs no context. The row-slice partial sums live in a fixed 16 MiB __device__ array that
+ * every GPU loading the library keeps until exit: ncols^2 must not exceed 2^21 (any
+ * ncols <= 1024 fits), else SPARC_ERR_ARG. The first call on a device looks up that array's
+ * address (cudaGetSymbolAddress) with the device current and keeps it for the life of the
+ * process; make that first call before any stream capture begins. The kept address belongs
+ * to the device's primary context: a process that resets the device (cudaDeviceReset) must
+ * not call this entry point on it afterwards. All calls share the array: calls that overlap
+ * on the GPU race on it and must be serialised. Each call overwrites every partial it reads,
+ * so no clearing is needed. Returns SPARC_ERR_ARG for NULL pointers or bad sizes,
+ * SPARC_ERR_CUDA if the lookup or the launch fails. */
 sparc_status sparc_gram_noalloc(const double *A, const double *B, long nd, int ncols, long ld,
                                 double *G, void *cuda_stream);
 

@@ -82,8 +82,16 @@ def lib():
         L.orc_lanczos_start.argtypes = [C.c_long, C.c_uint64, dp]
         L.orc_lanczos.argtypes = [C.POINTER(_Ham), C.c_int, C.c_uint64, dp, dp]
         L.orc_lanczos.restype = C.c_int
+        L.orc_threads.argtypes = [C.c_int]
+        L.orc_threads.restype = C.c_int
         _lib = L
     return _lib
+
+
+def threads(n: int = 0) -> int:
+    """Sets the OpenMP thread count of the C loops (n > 0) and returns the count in effect.
+    Results do not depend on it."""
+    return int(lib().orc_threads(int(n)))
 
 
 def _dp(a: np.ndarray):

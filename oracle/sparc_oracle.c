@@ -17,9 +17,20 @@
  * orbitals is column-major: column c starts at X + c*ld, ld >= Nd.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* Thread count of the OpenMP loops (for timing the oracle on 1 or all host cores; the
+ * results do not depend on it). n <= 0 leaves the count unchanged. Returns the count in
+ * effect. */
+int orc_threads(int n)
+{
+    if (n > 0)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+}
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846

@@ -139,9 +139,8 @@ def main(argv=None):
     ctxs, X, W, bounds = [], [], [], []
     for i, (n, R, Z, gamma, ns) in enumerate(spec):
         ctx = sparc.Context(n, h, R, Z, gamma)
-        lo, hi = ctx.lanczos_bounds(10, i)
         ctxs.append(ctx)
-        bounds.append(sparc.first_bounds(lo, hi))
+        bounds.append(ctx.first_bounds(10, i))
         x0 = torch.from_numpy(synth.initial_block(a.seed + i, n ** 3, ns)).to("cuda",
                                                                            torch.float32)
         X.append(x0)

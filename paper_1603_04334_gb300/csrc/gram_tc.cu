@@ -1,6 +1,10 @@
-// gram_tc.cu -- the subspace contractions of the mixed-precision form on the tensor cores:
+// gram_tc.cu -- the subspace contractions on the tensor cores (tcgen05):
 //   M_s = Y^T Y  and  H_s = Y^T (H Y)   (projection onto the filtered block, Sec. 3.4),
-// Y the FP32 filtered block and H Y its FP64 image, G = A^T B over the Nd grid rows.
+// G = A^T B over the Nd grid rows, and the rotation X = Y (L^-T Q) (Eq.
+// OrbitalTransformation). Two digit representations share one kernel: 47 bits (six digits;
+// the Gram pair of both forms, FP64 or FP32 Y, and the FP64 form's rotation) and 23 bits
+// (three digits; sparc_gram_tc and the mixed form's FP32 rotation). The description below
+// is of the 23-bit form; the 47-bit form differs as stated at struct Tc47.
 //
 // Representation. The rows are cut into chunks of kChunk = 256. For chunk c and column j
 // of an operand, e = e(c, j) is the smallest integer with max_{k in c} |x_kj| < 2^e, and
@@ -228,13 +232,13 @@ __device__ __forceinline__ double widen_int(float f)
 // writes its 8 values of a digit as one 16-byte store (the 8 K-adjacent elements of a core
 // matrix row are contiguous, and the 32 rows of a warp fill 512 contiguous bytes). Rows past
 // nd and columns past ns are zero.
-template <class C>
+template <class C, typename T>
 __global__ void __launch_bounds__(32 * (C::kChunk / 8))
-k_tc_digits_t(const double *__restrict__ Y, long ld, long nd, int ns, long nstep,
+k_tc_digits_t(const T *__restrict__ Y, long ld, long nd, int ns, long nstep,
               __nv_bfloat16 *__restrict__ D, int *__restrict__ E, long nd_pad)
 {
-    using B = FBits<double>;
-    using U = B::U;
+    using B = FBits<T>;
+    using U = typename B::U;
     constexpr int G = C::kChunk / 8;  // column groups (warps)
     __shared__ U red[G][32];
     __shared__ int bad_s[G][32];
@@ -243,13 +247,13 @@ k_tc_digits_t(const double *__restrict__ Y, long ld, long nd, int ns, long nstep
     const long chunk = blockIdx.y;
     const int kb = (int)(chunk * C::kChunk) + g * 8;  // first column of this thread's group
     const bool live = row < nd;
-    double x[8];
+    T x[8];
     U mx = 0;
     int bad = 0;
     const U inf = (U)B::kExpMask << B::kMant;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-        x[t] = (live && kb + t < ns) ? Y[row + (long)(kb + t) * ld] : 0.0;
+        x[t] = (live && kb + t < ns) ? Y[row + (long)(kb + t) * ld] : (T)0;
         const U m = B::mag(x[t]);
         bad |= m >= inf;
         mx = m > mx ? m : mx;
@@ -278,7 +282,7 @@ k_tc_digits_t(const double *__restrict__ Y, long ld, long nd, int ns, long nstep
             const int sh = e + B::kBias + B::kMant - C::kBits - ebx;
             if (sh <= 0)
                 N = (long)m << (-sh);
-            else if (sh < 64)
+            else if (sh < 8 * (int)sizeof(U))
                 N = (long)((m + ((U)1 << (sh - 1))) >> sh);
         }
         const int sg = B::neg(x[t]) ? -1 : 1;
@@ -314,12 +318,12 @@ k_tc_digits_t(const double *__restrict__ Y, long ld, long nd, int ns, long nstep
 // running on across units; A's and B's exponents have the row strides ea_ld and eb_ld, and
 // the epilogue writes out[i + j ldo] (i: A column, j: B column) for i < nrow, j < ncol, a
 // warp's lanes covering 32 consecutive i (coalesced).
-template <class C, bool ROT>
+template <class C, bool ROT, typename TO = double>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
           const __nv_bfloat16 *__restrict__ DB, const int *__restrict__ EB, int ns_pad, long nstep,
           const int2 *__restrict__ tiles, int ntiles, int nsplit, double *__restrict__ part,
-          int *err, int eb_ld = 0, int mblk = 1, double *__restrict__ out = nullptr, long ldo = 0,
+          int *err, int eb_ld = 0, int mblk = 1, TO *__restrict__ out = nullptr, long ldo = 0,
           long nrow = 0, int ncol = 0, long ea_ld = 0)
 {
     using Dm = TcDims<C>;
@@ -537,10 +541,15 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                 const long i = (long)w.tb.x * kTile + r;
                 const long j0 = (long)w.tb.y * kTile + w.hf * C::kN + hw * kEpiCols;
                 if (i < nrow) {
-                    double *o = out + i + j0 * ldo;
+                    TO *o = out + i + j0 * ldo;
 #pragma unroll
-                    for (int x = 0; x < kEpiCols; ++x)
-                        if (j0 + x < ncol) o[(long)x * ldo] = widen_int(H[x]) + widen_int(Lw[x * 32]);
+                    for (int x = 0; x < kEpiCols; ++x) {
+                        if (j0 + x >= ncol) continue;
+                        if constexpr (sizeof(TO) == 4)
+                            o[(long)x * ldo] = H[x] + Lw[x * 32];  // the pair rounded to FP32
+                        else
+                            o[(long)x * ldo] = widen_int(H[x]) + widen_int(Lw[x * 32]);
+                    }
                 }
             } else {
                 double *o = part + ((long)w.split * ntiles + w.tile) * kTile * kTile +
@@ -743,37 +752,41 @@ cudaError_t gram_tc(const TA *A, long lda, const TB *B, long ldb, long nd, int n
     return gram_tc_impl<Tc23, TA, TB>(A, lda, B, ldb, nd, ns, G, ws, ws_bytes, sym, err, st);
 }
 
-template <typename TA, typename TB>
-cudaError_t gram_tc_pair(const TA *A, long lda, const TB *B, long ldb, long nd, int ns,
-                         double *M, double *Hm, void *ws, size_t ws_bytes, int *err,
-                         cudaStream_t st)
-{
-    return gram_tc_pair_impl<Tc23, TA, TB>(A, lda, B, ldb, nd, ns, M, Hm, ws, ws_bytes, err, st);
-}
 
-cudaError_t gram_tc47_pair(const double *A, long lda, const double *B, long ldb, long nd, int ns,
+template <typename TA>
+cudaError_t gram_tc47_pair(const TA *A, long lda, const double *B, long ldb, long nd, int ns,
                            double *M, double *Hm, void *ws, size_t ws_bytes, int *err,
                            cudaStream_t st)
 {
-    return gram_tc_pair_impl<Tc47, double, double>(A, lda, B, ldb, nd, ns, M, Hm, ws, ws_bytes,
-                                                   err, st);
+    return gram_tc_pair_impl<Tc47, TA, double>(A, lda, B, ldb, nd, ns, M, Hm, ws, ws_bytes, err,
+                                               st);
 }
+template cudaError_t gram_tc47_pair<double>(const double *, long, const double *, long, long, int,
+                                            double *, double *, void *, size_t, int *,
+                                            cudaStream_t);
+template cudaError_t gram_tc47_pair<float>(const float *, long, const double *, long, long, int,
+                                           double *, double *, void *, size_t, int *,
+                                           cudaStream_t);
 
-// ---- rotation out = Y C on the tensor cores (47-bit digits) ------------------------------
+// ---- rotation out = Y C on the tensor cores -----------------------------------------------
 // Written as the contraction G = A^T B with A = Y^T (K = Ns: Y's columns, M = Nd: Y's rows)
 // and B = C (N = Ns): G(i, j) = sum_k Y_ik C_kj = out(i, j). Y gets exponents per (K chunk,
 // row), C per (K chunk, column), so every product in a class accumulator shares one scale.
-// K = Ns is short, so a unit is one 128 x 64 tile over all of K; the tensor-memory lanes
-// hold Y's rows, so each store of the epilogue covers 32 consecutive rows of a column.
+// K = Ns is short, so a unit is one tile (Tc47: a 128 x 64 half tile) over all of K; the
+// tensor-memory lanes hold Y's rows, so each store of the epilogue covers 32 consecutive rows
+// of a column. The FP64 form uses the 47-bit digits (FP64 blocks, FP64 output); the mixed
+// form the 23-bit digits (FP32 block or the FP64 H Y of its residuals, FP32 output): each
+// entry of Y and C is rounded to 2^-24 of its chunk's largest, the rounding an FP32 result
+// carries anyway, for 6 digit MMAs per 16 K instead of 21.
 namespace {
 struct RotPlan {
     int ns_pad, mblk;
     long nblk, nd_pad, nchunk, nstep;
     size_t da_bytes, ea_bytes, db_bytes, eb_bytes;
 };
+template <class C>
 RotPlan rot_plan(long nd, int ns)
 {
-    using C = Tc47;
     RotPlan p;
     p.mblk = (ns + kTile - 1) / kTile;
     p.ns_pad = p.mblk * kTile;
@@ -787,22 +800,21 @@ RotPlan rot_plan(long nd, int ns)
     p.eb_bytes = (size_t)p.nchunk * p.nd_pad * sizeof(int);
     return p;
 }
-}  // namespace
-
-size_t rotate_tc_workspace(long nd, int ns)
+template <class C>
+size_t rot_workspace(long nd, int ns)
 {
-    const RotPlan p = rot_plan(nd, ns);
+    const RotPlan p = rot_plan<C>(nd, ns);
     return align256(p.da_bytes) + align256(p.ea_bytes) + align256(p.db_bytes) +
            align256(p.eb_bytes);
 }
 
-cudaError_t rotate_tc(const double *Y, long ldy, long nd, int ns, const double *Cm, double *out,
-                      long ldo, void *ws, size_t ws_bytes, int *err, cudaStream_t st)
+template <class C, typename TY, typename TO>
+cudaError_t rotate_tc_impl(const TY *Y, long ldy, long nd, int ns, const double *Cm, TO *out,
+                           long ldo, void *ws, size_t ws_bytes, int *err, cudaStream_t st)
 {
-    using C = Tc47;
     if (ns <= 0 || nd <= 0) return cudaSuccess;
-    const RotPlan p = rot_plan(nd, ns);
-    if (ws_bytes < rotate_tc_workspace(nd, ns)) return cudaErrorInvalidValue;
+    const RotPlan p = rot_plan<C>(nd, ns);
+    if (ws_bytes < rot_workspace<C>(nd, ns)) return cudaErrorInvalidValue;
     const long ctas = (long)p.mblk * p.nblk * TcDims<C>::kHalves;
     if (p.nchunk > 65535 || ctas > 0x7fffffffL || p.nd_pad / 32 > 0x7fffffffL)
         return cudaErrorInvalidValue;
@@ -819,7 +831,8 @@ cudaError_t rotate_tc(const double *Y, long ldy, long nd, int ns, const double *
     static std::atomic<bool> attr_set{false};  // set once (several host threads may launch)
     cudaError_t e;
     if (!attr_set.load(std::memory_order_acquire)) {
-        e = cudaFuncSetAttribute(k_gram_tc<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_gram_tc<C, true, TO>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TcDims<C>::kSmemBytes);
         if (e != cudaSuccess) return e;
         attr_set.store(true, std::memory_order_release);
@@ -831,19 +844,41 @@ cudaError_t rotate_tc(const double *Y, long ldy, long nd, int ns, const double *
     }
     {   // B = Y^T: K = Ns (Y's columns), N = Nd (Y's rows)
         dim3 grid((unsigned)(p.nd_pad / 32), (unsigned)p.nchunk);
-        k_tc_digits_t<C><<<grid, 32 * (C::kChunk / 8), 0, st>>>(Y, ldy, nd, ns, p.nstep, DB, EB,
-                                                               p.nd_pad);
+        k_tc_digits_t<C, TY><<<grid, 32 * (C::kChunk / 8), 0, st>>>(Y, ldy, nd, ns, p.nstep, DB,
+                                                                    EB, p.nd_pad);
         note_launch();
     }
     const unsigned grid = (unsigned)(ctas < 152 ? ctas : 152);  // persistent, one per SM
     // A: Y's digits (nblk row blocks, exponent stride nd_pad); B: C's (mblk column blocks,
     // the fastest tile index)
-    k_gram_tc<C, true><<<grid, kThreads, TcDims<C>::kSmemBytes, st>>>(
+    k_gram_tc<C, true, TO><<<grid, kThreads, TcDims<C>::kSmemBytes, st>>>(
         DB, EB, DA, EA, p.ns_pad, p.nstep, nullptr, (int)(p.mblk * p.nblk), 1, nullptr, err,
         p.ns_pad, p.mblk, out, ldo, nd, ns, p.nd_pad);
     note_launch();
     return cudaGetLastError();
 }
+}  // namespace
+
+size_t rotate_tc_workspace(long nd, int ns) { return rot_workspace<Tc47>(nd, ns); }
+size_t rotate_tc23_workspace(long nd, int ns) { return rot_workspace<Tc23>(nd, ns); }
+
+cudaError_t rotate_tc(const double *Y, long ldy, long nd, int ns, const double *Cm, double *out,
+                      long ldo, void *ws, size_t ws_bytes, int *err, cudaStream_t st)
+{
+    return rotate_tc_impl<Tc47, double, double>(Y, ldy, nd, ns, Cm, out, ldo, ws, ws_bytes, err,
+                                                st);
+}
+
+template <typename TY>
+cudaError_t rotate_tc23(const TY *Y, long ldy, long nd, int ns, const double *Cm, float *out,
+                        long ldo, void *ws, size_t ws_bytes, int *err, cudaStream_t st)
+{
+    return rotate_tc_impl<Tc23, TY, float>(Y, ldy, nd, ns, Cm, out, ldo, ws, ws_bytes, err, st);
+}
+template cudaError_t rotate_tc23<float>(const float *, long, long, int, const double *, float *,
+                                        long, void *, size_t, int *, cudaStream_t);
+template cudaError_t rotate_tc23<double>(const double *, long, long, int, const double *, float *,
+                                         long, void *, size_t, int *, cudaStream_t);
 
 __global__ void k_add_into(double *__restrict__ dst, const double *__restrict__ src, long n)
 {
@@ -861,9 +896,6 @@ cudaError_t add_into(double *dst, const double *src, long n, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template cudaError_t gram_tc_pair<float, double>(const float *, long, const double *, long, long,
-                                                 int, double *, double *, void *, size_t, int *,
-                                                 cudaStream_t);
 template cudaError_t gram_tc<float, float>(const float *, long, const float *, long, long, int,
                                            double *, void *, size_t, bool, int *, cudaStream_t);
 template cudaError_t gram_tc<float, double>(const float *, long, const double *, long, long, int,

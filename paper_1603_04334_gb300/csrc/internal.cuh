@@ -12,6 +12,8 @@ constexpr int kRadius = 6;  // stencil radius the kernels are written for (n_o <
 
 // Counts kernel launches made by this library (process-wide, read by sparc_launch_count).
 void note_launch(int n = 1);
+// [a, b, a0] of the first CheFSI iteration from the Lanczos bounds (sparc.cu)
+void first_iteration_bounds(double lo, double hi, double *bounds);
 
 // Device copy of the discrete Hamiltonian (Sec. 3.1) and of its projector tables.
 struct DevHam {
@@ -237,47 +239,52 @@ size_t gram_tc47_workspace(long nd, int ns);
 // out = Y C (C: ns x ns FP64, column-major) on the tensor cores in the 47-bit digit form;
 // ws: rotate_tc_workspace(nd, ns) bytes.
 size_t rotate_tc_workspace(long nd, int ns);
-// Rows per slab of the FP64 form's tensor-core Gram and rotation: the whole block when the
-// digit workspace (12 bytes per element of both operands) stays within 24 GB, else the
-// largest multiple of 256 rows, halving from nd, that does. Larger blocks are processed
-// slab by slab: the Grams of the slabs are summed (slabs start on 128-row chunk boundaries,
-// so every slab's digits are those the whole-block call would form) and the rotation's rows
-// are independent.
-inline long fp64_tc_slab_rows(long nd, int ns)
+// The same in the 23-bit digit form with FP32 output (the mixed-precision form: Y its FP32
+// block, or the FP64 H Y of its residuals); ws: rotate_tc23_workspace(nd, ns) bytes.
+size_t rotate_tc23_workspace(long nd, int ns);
+// Rows per slab of the tensor-core Gram (47-bit digits in both forms) and rotation (47-bit
+// digits in the FP64 form, 23-bit in the mixed form): the whole block when the digit
+// workspace stays within 24 GB, else the largest multiple of 256 rows, halving from nd,
+// that does. Larger blocks are processed slab by slab: the Grams of the slabs are summed
+// (slabs start on 128-row chunk boundaries, so every slab's digits are those the
+// whole-block call would form) and the rotation's rows are independent.
+inline long tc_slab_rows(long nd, int ns, bool mixed)
 {
     const size_t cap = (size_t)24 << 30;
+    auto rot = [&](long r) { return mixed ? rotate_tc23_workspace(r, ns) : rotate_tc_workspace(r, ns); };
     long rows = nd;
-    while (rows > 256 &&
-           (gram_tc47_workspace(rows, ns) > cap || rotate_tc_workspace(rows, ns) > cap))
+    while (rows > 256 && (gram_tc47_workspace(rows, ns) > cap || rot(rows) > cap))
         rows = (rows / 2 + 255) / 256 * 256;
     return rows;
+}
+// Bytes of the tensor-core workspace one slab of tc_slab_rows(nd, ns, mixed) rows needs.
+inline size_t tc_slab_workspace(long nd, int ns, bool mixed)
+{
+    const long slab = tc_slab_rows(nd, ns, mixed);
+    const size_t wg = gram_tc47_workspace(slab, ns);
+    const size_t wr = mixed ? rotate_tc23_workspace(slab, ns) : rotate_tc_workspace(slab, ns);
+    return wg > wr ? wg : wr;
 }
 // dst[i] += src[i], i < n
 cudaError_t add_into(double *dst, const double *src, long n, cudaStream_t st);
 cudaError_t rotate_tc(const double *Y, long ldy, long nd, int ns, const double *C, double *out,
                       long ldo, void *ws, size_t ws_bytes, int *err, cudaStream_t st);
-cudaError_t gram_tc47_pair(const double *A, long lda, const double *B, long ldb, long nd, int ns,
+template <typename TY>
+cudaError_t rotate_tc23(const TY *Y, long ldy, long nd, int ns, const double *C, float *out,
+                        long ldo, void *ws, size_t ws_bytes, int *err, cudaStream_t st);
+// M = A^T A and Hm = A^T B in the 47-bit digit form (A FP64 or FP32, B FP64).
+template <typename TA>
+cudaError_t gram_tc47_pair(const TA *A, long lda, const double *B, long ldb, long nd, int ns,
                            double *M, double *Hm, void *ws, size_t ws_bytes, int *err,
                            cudaStream_t st);
 template <typename TA, typename TB>
 cudaError_t gram_tc(const TA *A, long lda, const TB *B, long ldb, long nd, int ns, double *G,
                     void *ws, size_t ws_bytes, bool sym, int *err, cudaStream_t st);
-// M = A^T A and Hm = A^T B (both symmetric-tiled and mirrored) with one digit pass of A;
-// ws: gram_tc_workspace(nd, ns, false, true) bytes.
-template <typename TA, typename TB>
-cudaError_t gram_tc_pair(const TA *A, long lda, const TB *B, long ldb, long nd, int ns,
-                         double *M, double *Hm, void *ws, size_t ws_bytes, int *err,
-                         cudaStream_t st);
 cudaError_t gram_f64_nsplit(const double *A, long lda, const double *B, long ldb, long nd, int ns,
                             double *G, double *part, int nsplit, cudaStream_t st);
 // out (nd x ns, ldo) = A (nd x ns, lda) Q (ns x ns, column-major FP64)
 cudaError_t rotate_f64(const double *A, long lda, long nd, int ns, const double *Q,
                        double *out, long ldo, cudaStream_t st);
-cudaError_t rotate_f32(const float *A, long lda, long nd, int ns, const double *Q, float *out,
-                       long ldo, cudaStream_t st);
-// out = A Q in FP32 arithmetic from an FP64 block (the FP32 form's residuals)
-cudaError_t rotate_f64in_f32(const double *A, long lda, long nd, int ns, const double *Q,
-                             float *out, long ldo, cudaStream_t st);
 
 // ---- dense.cu -------------------------------------------------------------------
 // Small dense Rayleigh-Ritz on the device (single CTA kernels), ns <= kMaxDense.

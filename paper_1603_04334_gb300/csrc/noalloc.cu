@@ -1,9 +1,10 @@
 // noalloc.cu -- an FP64 Gram contraction G = A^T B that allocates no memory.
 //
 // Who needs it: callers that must not allocate device memory at the point of use --
-// code running inside a CUDA stream capture, real-time or embedded loops that forbid
-// cudaMalloc after start-up, or hosts that hand this library pre-allocated buffers from
-// their own pool and cannot let it grow one. sparc_gram keeps its row-slice partial
+// real-time or embedded loops that forbid cudaMalloc after start-up (an allocation can
+// block and synchronise the whole device), hosts that hand this library pre-allocated
+// buffers from their own pool and cannot let it grow one, or processes that have reserved
+// nearly all device memory already. sparc_gram keeps its row-slice partial
 // sums in context workspace that it may (re)allocate; this variant keeps them in one
 // file-scope __device__ array instead, so the caller only supplies A, B and G.
 //
@@ -18,7 +19,9 @@
 //     the contents left by an earlier call do not matter.
 //   * Host code cannot use the array's name as a device address. The first call on each
 //     device looks the address up with cudaGetSymbolAddress (with that device current)
-//     and caches it; make that first call before any stream capture begins.
+//     and caches it; make that first call before any stream capture begins. The cached
+//     address belongs to the device's primary context, so a process that resets the device
+//     (cudaDeviceReset) must not call this entry point on it again.
 #include "sparc.h"
 #include "internal.cuh"
 

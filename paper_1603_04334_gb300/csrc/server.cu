@@ -154,10 +154,9 @@ sparc_status solve(const Request &r, cudaStream_t st, sparc_result_info &info,
         k_start_block<double><<<152 * 8, 256, 0, st>>>((double *)X, nd, q.ns, nd, key);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) return finish(SPARC_ERR_CUDA);
-    double lo = 0, hi = 0;
-    s = sparc_lanczos_bounds(ctx, kLanczosSteps, q.seed, &lo, &hi);
+    double b[3];  // [a, b, a0] of the first iteration
+    s = sparc_first_bounds(ctx, kLanczosSteps, q.seed, b);
     if (s != SPARC_OK) return finish(s);
-    double b[3] = {lo + 0.25 * (hi - lo), hi, lo};  // first iteration: a = a0 + (b - a0) / 4
     ritz.assign(q.ns, 0.0);
     resid.assign(q.ns, 0.0);
     for (int it = 0; it < q.max_iters; ++it) {
@@ -249,15 +248,13 @@ size_t sparc_request_bytes(const sparc_request *q)
     b += sizeof(double) * 4 * na * ns;
     b += sizeof(double) * (size_t)nd * ns;
     b += es * (size_t)nd * ns;
-    if (q->dtype == SPARC_F32) {
-        b += gram_tc_workspace(nd, ns, false, true);
-    } else {
-        // 47-bit tensor-core Gram and rotation (one workspace, sized for a slab of rows, and
-        // the slab Grams' sums); column bounds of the filter's blocks, V_eff - shift pairs
-        const long slab = fp64_tc_slab_rows(nd, ns);
-        const size_t wg = gram_tc47_workspace(slab, ns), wr = rotate_tc_workspace(slab, ns);
-        b += wg > wr ? wg : wr;
-        if (slab < nd) b += sizeof(double) * 2 * (size_t)ns * ns;
+    // tensor-core Gram and rotation (one workspace, sized for a slab of rows, and the slab
+    // Grams' sums)
+    const bool mixed = q->dtype == SPARC_F32;
+    b += tc_slab_workspace(nd, ns, mixed);
+    if (tc_slab_rows(nd, ns, mixed) < nd) b += sizeof(double) * 2 * (size_t)ns * ns;
+    if (!mixed) {
+        // column bounds of the filter's blocks, V_eff - shift pairs
         b += sizeof(unsigned) * ((size_t)(q->degree + 1) * ns + (size_t)ns);
         b += 8 * (size_t)nd;
     }

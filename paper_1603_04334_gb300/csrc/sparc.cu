@@ -25,6 +25,18 @@ using namespace sparc;
 namespace sparc {
 static std::atomic<long long> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Filter interval of the first CheFSI iteration from the Lanczos bounds [lo, hi] (Sec. 4
+// gives the lower end as lambda_c = E_F + 0.1 Ha, which a fixed Hamiltonian without
+// electrons lacks): a0 = lo, b = hi and the cutoff a a quarter of the way up,
+// a = a0 + (b - a0) / 4. Later iterations take a and a0 from the Ritz values
+// (sparc_chefsi_step).
+void first_iteration_bounds(double lo, double hi, double *bounds)
+{
+    bounds[0] = lo + 0.25 * (hi - lo);
+    bounds[1] = hi;
+    bounds[2] = lo;
+}
 }  // namespace sparc
 
 // Per-phase CUDA-event timing on the context stream.
@@ -421,30 +433,26 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
     // M_s = Yf^T Yf, H_s = Yf^T (H Yf)
     DenseBufs d;
     TRY(dense_bufs(ctx, ns, d));
-    // FP64 form: both contractions on the tensor cores in the 47-bit digit form (gram_tc.cu),
-    // slab by slab where the whole block's digits would exceed the workspace cap; the
-    // rotations below reuse the workspace
-    const bool tc64 = sizeof(T) == 8;
-    const long slab = tc64 ? fp64_tc_slab_rows(nd, ns) : nd;
-    if (tc64) {
-        const size_t wg = gram_tc47_workspace(slab, ns), wr = rotate_tc_workspace(slab, ns);
-        TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, wg > wr ? wg : wr));
+    // Both forms: the two contractions on the tensor cores in the 47-bit digit form
+    // (gram_tc.cu; an FP32 block's entries are represented exactly, H Yf to 2^-48 of each
+    // chunk's largest: FP64-level M_s and H_s), slab by slab where the whole block's digits
+    // would exceed the workspace cap; the rotations below reuse the workspace.
+    const bool mixed = sizeof(T) == 4;
+    const long slab = tc_slab_rows(nd, ns, mixed);
+    {
+        TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, tc_slab_workspace(nd, ns, mixed)));
         const size_t nn = (size_t)ns * ns;
         if (slab < nd) TRY(ensure(ctx, ctx->part, ctx->part_bytes, sizeof(double) * 2 * nn));
         PHASE(SPARC_PHASE_GRAM);
         for (long r0 = 0; r0 < nd; r0 += slab) {
             const long rows = nd - r0 < slab ? nd - r0 : slab;
             double *Mo = r0 ? (double *)ctx->part : d.M, *Ho = r0 ? (double *)ctx->part + nn : d.Hs;
-            CK(gram_tc47_pair((const double *)Yf + r0, ld, HX + r0, ld, rows, ns, Mo, Ho, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st));
+            CK(gram_tc47_pair<T>(Yf + r0, ld, HX + r0, ld, rows, ns, Mo, Ho, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st));
             if (r0) {
                 CK(add_into(d.M, Mo, (long)nn, ctx->st));
                 CK(add_into(d.Hs, Ho, (long)nn, ctx->st));
             }
         }
-    } else {
-        // mixed-precision form: both contractions on the tensor cores (gram_tc.cu)
-        TRY(ensure(ctx, ctx->tcws, ctx->tcws_bytes, gram_tc_workspace(nd, ns, false, true)));
-        { PHASE(SPARC_PHASE_GRAM); CK((gram_tc_pair<float, double>((const float *)Yf, ld, HX, ld, nd, ns, d.M, d.Hs, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st))); }
     }
     { PHASE(SPARC_PHASE_DENSE); CK(dense_rr(d.M, d.Hs, ns, d.ritz, d.Cf, d.work, ctx->flags, ctx->st)); }
     CK(cudaMemcpyAsync(ctx->pin_i, ctx->flags, sizeof(int) * 16, cudaMemcpyDeviceToHost, ctx->st));
@@ -470,11 +478,15 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
         PHASE(SPARC_PHASE_ROTATE);
         for (long r0 = 0; r0 < nd; r0 += slab)
             CK(rotate_tc((const double *)Yf + r0, ld, nd - r0 < slab ? nd - r0 : slab, ns, d.Cf, (double *)xout + r0, ld, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st));
-    } else
-        { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f32((const float *)Yf, ld, nd, ns, d.Cf, (float *)xout, ld, ctx->st)); }
+    } else {
+        PHASE(SPARC_PHASE_ROTATE);
+        for (long r0 = 0; r0 < nd; r0 += slab)
+            CK(rotate_tc23<float>((const float *)Yf + r0, ld, nd - r0 < slab ? nd - r0 : slab, ns, d.Cf, (float *)xout + r0, ld, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st));
+    }
     if (resid_host) {
-        // H X = (H Y_f) (L^-T Q); residuals against the rotated block. The FP32 form rotates
-        // in FP32 arithmetic (the block itself is FP32; about 1e-7 relative of |H X|).
+        // H X = (H Y_f) (L^-T Q); residuals against the rotated block. The mixed form rotates
+        // H Y_f in the 23-bit digit form to FP32 (the block itself is FP32; about 1e-7
+        // relative of |H X|).
         TRY(ensure(ctx, ctx->roth, ctx->roth_bytes, sizeof(T) * (size_t)ns * ld));
         if (sizeof(T) == 8) {
             double *hxr = (double *)ctx->roth;
@@ -486,7 +498,11 @@ sparc_status rr_core(sparc_ctx *ctx, T *Yf, T *dst, double *HX, int ns, long ld,
             { PHASE(SPARC_PHASE_OTHER); CK(resid_f64((const double *)xout, hxr, ld, nd, ns, d.ritz, d.resid, ctx->st)); }
         } else {
             float *hxr = (float *)ctx->roth;
-            { PHASE(SPARC_PHASE_ROTATE); CK(rotate_f64in_f32(HX, ld, nd, ns, d.Cf, hxr, ld, ctx->st)); }
+            {
+                PHASE(SPARC_PHASE_ROTATE);
+                for (long r0 = 0; r0 < nd; r0 += slab)
+                    CK(rotate_tc23<double>(HX + r0, ld, nd - r0 < slab ? nd - r0 : slab, ns, d.Cf, hxr + r0, ld, ctx->tcws, ctx->tcws_bytes, ctx->H.err, ctx->st));
+            }
             { PHASE(SPARC_PHASE_OTHER); CK(resid_f32((const float *)xout, hxr, ld, nd, ns, d.ritz, d.resid, ctx->st)); }
         }
     }
@@ -990,6 +1006,21 @@ sparc_status sparc_lanczos_bounds(sparc_ctx *ctx, int ksteps, unsigned long long
         return fail(ctx, SPARC_ERR_TIMEOUT, "tridiagonal eigensolve failed (status %d)", ctx->pin_i[0]);
     *lo = ctx->pin[0];
     *hi = ctx->pin[1];
+    return SPARC_OK;
+}
+
+sparc_status sparc_first_bounds(sparc_ctx *ctx, int ksteps, unsigned long long seed,
+                                double *bounds_out)
+{
+    if (!ctx) return SPARC_ERR_ARG;
+    ctx->err.clear();
+    if (!bounds_out) return fail(ctx, SPARC_ERR_ARG, "bounds_out is NULL");
+    double lo = 0.0, hi = 0.0;
+    TRY(sparc_lanczos_bounds(ctx, ksteps, seed, &lo, &hi));
+    first_iteration_bounds(lo, hi, bounds_out);
+    if (!(bounds_out[2] < bounds_out[0] && bounds_out[0] < bounds_out[1]))
+        return fail(ctx, SPARC_ERR_ARG,
+                    "Lanczos bounds lo = %g, hi = %g leave no filter interval (a0 < a < b)", lo, hi);
     return SPARC_OK;
 }
 

@@ -34,7 +34,8 @@ _STATUS = {SPARC_ERR_ARG: "SPARC_ERR_ARG", SPARC_ERR_OOM: "SPARC_ERR_OOM",
 # Entry points of include/sparc.h (checked by the test suite against the header).
 EXPORTS = ("sparc_create", "sparc_destroy", "sparc_last_error", "sparc_get_veff", "sparc_info",
            "sparc_set_kinetic_scale", "sparc_apply_H", "sparc_lanczos_bounds",
-           "sparc_cheb_filter", "sparc_orth_rr", "sparc_gram", "sparc_chefsi_step",
+           "sparc_first_bounds", "sparc_cheb_filter", "sparc_orth_rr", "sparc_gram",
+           "sparc_chefsi_step",
            "sparc_profile_enable",
            "sparc_profile_read", "sparc_profile_reset", "sparc_launch_count",
            "sparc_gram_noalloc", "sparc_sync", "sparc_selftest_timeout",
@@ -88,6 +89,7 @@ def load(build_if_missing: bool = True):
     L.sparc_set_kinetic_scale.argtypes = [vp, C.c_double]
     L.sparc_apply_H.argtypes = [vp, ip, vp, vp, ip, C.c_long]
     L.sparc_lanczos_bounds.argtypes = [vp, ip, C.c_ulonglong, dp, dp]
+    L.sparc_first_bounds.argtypes = [vp, ip, C.c_ulonglong, dp]
     L.sparc_cheb_filter.argtypes = [vp, ip, vp, vp, ip, C.c_long, ip, C.c_double, C.c_double,
                                     C.c_double]
     L.sparc_orth_rr.argtypes = [vp, ip, vp, vp, ip, C.c_long, dp, dp]
@@ -251,6 +253,14 @@ class Context:
                                                  C.byref(lo), C.byref(hi)))
         return lo.value, hi.value
 
+    def first_bounds(self, k: int = 10, seed: int = 0) -> list:
+        """[a, b, a0] for the first CheFSI iteration (sparc_first_bounds: k Lanczos steps,
+        then the library's cutoff rule)."""
+        out = np.zeros(3)
+        self._check(self._L.sparc_first_bounds(self._h, int(k), int(seed) & (2 ** 64 - 1),
+                                               out.ctypes.data_as(C.POINTER(C.c_double))))
+        return [float(v) for v in out]
+
     def cheb_filter(self, X, work, degree: int, a: float, b: float, a0: float):
         ncols, ld = _block(X, "X")
         if work.shape != X.shape or work.dtype != X.dtype:
@@ -383,8 +393,3 @@ def launch_count() -> int:
     if st != SPARC_OK:
         raise SparcError(st, "sparc_launch_count")
     return n.value
-
-
-def first_bounds(lo: float, hi: float):
-    """[a, b, a0] for the first CheFSI iteration from Lanczos bounds: a = a0 + 0.25 (b - a0)."""
-    return [lo + 0.25 * (hi - lo), hi, lo]

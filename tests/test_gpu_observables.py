@@ -47,8 +47,7 @@ def solved24():
     ctx = make_ctx(cl, V=H.V)
     X = to_dev(synth.initial_block(1, w.nd, w.ns))
     W = torch.empty_like(X)
-    lo, hi = ctx.lanczos_bounds(w.lanczos_k, 0)
-    bounds = sparc.first_bounds(lo, hi)
+    bounds = ctx.first_bounds(w.lanczos_k, 0)
     for _ in range(3):
         ritz, _, bounds = ctx.chefsi_step(X, W, w.degree, bounds)
     yield w, cl, H, ctx, X, ritz

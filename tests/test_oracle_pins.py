@@ -424,3 +424,39 @@ def test_chefsi_free_box_shells():
     X0 = synth.initial_block(9, n ** 3, ns)
     X, ritz, res, hist, _ = oracle.chefsi_solve(H, X0, 14, 60, tol=1e-10)
     assert np.max(np.abs(ritz[:10] - sums[:10])) < 1e-10
+
+
+# --------------------------------------------------------------------------------------
+# eigenvector sign convention (largest-magnitude entry positive, lowest index on ties)
+# --------------------------------------------------------------------------------------
+def test_fix_signs_hand_built():
+    # column 0: largest |.| is -0.8 -> flipped; column 1: largest is +0.9 -> kept;
+    # column 2: exact tie 0.5 / -0.5, the first (+0.5) decides -> kept; column 3: exact tie
+    # -0.5 / 0.5, the first (-0.5) decides -> flipped; column 4: all zero -> kept.
+    Q = np.array([[0.6, -0.3, 0.5, -0.5, 0.0],
+                  [-0.8, 0.9, -0.5, 0.5, 0.0],
+                  [0.0, -0.3, 0.1, 0.2, 0.0]])
+    want = np.array([[-0.6, -0.3, 0.5, 0.5, 0.0],
+                     [0.8, 0.9, -0.5, -0.5, 0.0],
+                     [-0.0, -0.3, 0.1, -0.2, 0.0]])
+    got = O.fix_signs(Q)
+    assert np.array_equal(got, want)
+    assert np.array_equal(Q[:, 1], got[:, 1])        # the input is not modified in place
+    assert Q[1, 0] == -0.8
+
+
+def test_rr_keeps_signs_of_an_exact_eigenbasis(dense12):
+    # Rows of Y: exact eigenvectors of H, shuffled and with chosen signs. Then M_s = I, the
+    # projected matrix is diagonal, Q is a permutation whose +-1 entries the convention turns
+    # to +1, and X must be Y's rows sorted by eigenvalue with the signs Y gave them.
+    w, cl, H, D, ev, EV = dense12
+    ns = 6
+    order = np.array([3, 0, 5, 1, 4, 2])
+    sgn = np.array([-1.0, 1.0, -1.0, -1.0, 1.0, 1.0])
+    Y = sgn[:, None] * EV[:, order].T
+    X, HX, lam, res, Cf = oracle.orth_rr(Y, H.apply(Y))
+    assert np.max(np.abs(lam - ev[:ns])) < 1e-11
+    want = Y[np.argsort(order)]
+    assert np.max(np.abs(X - want)) < 1e-10
+    # the coefficient matrix is the permutation itself, every nonzero entry +1
+    assert np.max(np.abs(Cf - np.eye(ns)[:, np.argsort(order)])) < 1e-10
