@@ -477,22 +477,25 @@ def mixed_vs_fp64(seed: int, resid_cut: float = 1e-4) -> dict:
 
 
 def serving_study(seed: int, requests: int, rates=(400.0, 20.0), below=(0.5,),
-                  slots: int = 4, budget_gb: float = 150.0, serial_sample: int = 24) -> dict:
+                  slots: int = 8, workers: int = 4, budget_gb: float = 150.0,
+                  serial_sample: int = 24) -> dict:
     """The serving loop under Poisson arrivals: `requests` requests per rate, drawn from
     seed (edge in {48..128}, h = 0.3, 4-200 atoms, Ns 32-512, degree 20, <= 15 iterations to
-    max residual 1e-4, mixed form), 4 slots, 150 GB budget. The configured rates (20 and
-    400 req/s) come first; they saturate the server and measure its capacity. Then rates
-    below saturation (the given fractions of that capacity). Beside them, the first
-    `serial_sample` requests solved one at a time in FP64 (one slot): their service times
-    and the serial throughput."""
+    max residual 1e-4, mixed form), 150 GB budget. The continuous-batching server (at most
+    `slots` active requests whose filters share launches, requests joining between rounds)
+    runs the configured rates (20 and 400 req/s) first; they saturate it and measure its
+    capacity; then rates below saturation (the given fractions of that capacity). Beside
+    them: the worker server (`workers` threads, one stream each, a whole solve per request)
+    at 400 req/s, and the first `serial_sample` requests solved one at a time in FP64 (one
+    worker): their service times and the serial throughput."""
     from paper_1603_04334_gb300 import serve
 
     specs = serve.draw_requests(requests, seed)
     budget = int(budget_gb * 2 ** 30)
 
-    def point(rate):
+    def point(rate, batched, nslots):
         t0 = time.perf_counter()
-        m = serve.run_arrivals(specs, rate, budget, slots, seed + 1)
+        m = serve.run_arrivals(specs, rate, budget, nslots, seed + 1, batched=batched)
         lat = m["latency_s"]
         res = m["results"]
         return {"rate_req_per_s": rate, "requests": len(specs),
@@ -505,9 +508,10 @@ def serving_study(seed: int, requests: int, rates=(400.0, 20.0), below=(0.5,),
                 "failed": int(sum(r["status"] != 0 for r in res)),
                 "wall_s": time.perf_counter() - t0}
 
-    pts = [point(r) for r in rates]
+    pts = [point(r, True, slots) for r in rates]
     cap = max(p["throughput_req_per_s"] for p in pts)
-    pts += [point(f * cap) for f in below]
+    pts += [point(f * cap, True, slots) for f in below]
+    wk = point(max(rates), False, workers)
     base = []
     srv = serve.Server(budget, 1)
     try:
@@ -521,14 +525,18 @@ def serving_study(seed: int, requests: int, rates=(400.0, 20.0), below=(0.5,),
     base = np.array(base)
     return {"workload": "edge in {48,...,128}, h=0.3, atoms 4-200, Ns 32-512, degree 20, "
                         "<= 15 CheFSI iterations to max residual 1e-4, mixed form",
-            "slots": slots, "budget_gb": budget_gb, "capacity_req_per_s": cap,
+            "server": f"continuous batching: at most {slots} active requests, their FP32 "
+                      f"filters in shared launches, joining between CheFSI iterations",
+            "budget_gb": budget_gb, "capacity_req_per_s": cap,
             "points": pts,
+            "worker_server": dict(wk, server=f"{workers} worker threads, one stream each, "
+                                             f"whole solves"),
             "serial_fp64": {"requests": len(base),
                             "throughput_req_per_s": len(base) / float(base.sum()),
                             "service_p50_s": float(np.percentile(base, 50)),
                             "service_p99_s": float(np.percentile(base, 99)),
                             "sample": f"the first {len(base)} requests of the same list, one "
-                                      f"at a time in FP64 on one slot"}}
+                                      f"at a time in FP64 on one worker"}}
 
 
 def after_rotation(ctx, X, ritz, w, stream, fp64_peak_tflops: float, reps: int = 10) -> dict:

@@ -66,6 +66,20 @@ typedef struct {
 sparc_status sparc_server_create(size_t hbm_budget_bytes, int slots, int simulate,
                                  sparc_server **out);
 
+/* Creates a server in continuous-batching mode: one scheduler thread and one CUDA stream
+ * run rounds, each one CheFSI iteration of every active request. The Chebyshev filters of
+ * the active FP32-filter requests that share a degree run together through one
+ * sparc_batch (each filter step's three kernels walk one work list spanning all of them,
+ * include/sparc_batch.h); other requests are filtered on their own; then each request's
+ * Rayleigh-Ritz step (sparc_orth_rr) runs. After a round, requests that converged or ran
+ * out of iterations leave and their memory returns to the budget, and waiting requests
+ * join (same admission rule as above) while fewer than max_active (1..1024) are active.
+ * The batch uses one fixed kernel variant, so a request's results do not depend on which
+ * other requests share its launches. Same solve per request as above; the rest of the API
+ * is shared. */
+sparc_status sparc_server_create_batched(size_t hbm_budget_bytes, int max_active,
+                                         sparc_server **out);
+
 /* Device memory a request will hold while it runs (context tables and workspaces plus its
  * two orbital blocks); the budget is charged this much on admission. */
 size_t sparc_request_bytes(const sparc_request *req);

@@ -65,21 +65,6 @@ cudaError_t colmax_f32(const float *Y, int ncols, long ld, long nd, unsigned *b,
     return colmax_launch<float>(Y, ncols, ld, nd, b, st);
 }
 
-// (V_eff - shift) as FP32 pairs: the FP64 difference, then split.
-__global__ void k_vshift(const double *__restrict__ V, double shift, float2 *out, long n)
-{
-    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (long)gridDim.x * blockDim.x)
-        out[q] = split_double(V[q] - shift);
-}
-
-cudaError_t vshift_pairs(const double *V, double shift, float2 *out, long n, cudaStream_t st)
-{
-    k_vshift<<<152 * 4, 256, 0, st>>>(V, shift, out, n);
-    note_launch();
-    return cudaGetLastError();
-}
-
 __global__ void k_to_float_pair(const double *in, float2 *out, long n)
 {
     for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n;

@@ -72,13 +72,20 @@ struct Tc23 {
 };
 struct Tc47 {
     static constexpr int kDigits = 6, kClasses = 6, kBits = 47, kChunk = 128, kStep = 16,
-                         kN = 64, kStages = 3;
+                         kN = 64, kStages = 4;
 };
+// A stage holds A's blobs (all 128 columns of each digit) and the kN columns of B's blobs
+// this CTA multiplies: per digit and 8-row K group, kN / 8 core matrices of 128 B (copied
+// as one contiguous piece of each blob's K group), so B's K-adjacent cores sit kN * 16 B
+// apart in shared memory.
 template <class C> struct TcDims {
     static constexpr int kStepsPerChunk = C::kChunk / C::kStep;
     static constexpr int kBlobElems = kTile * C::kStep;                    // BF16 per blob
     static constexpr unsigned kOperandBytes = C::kDigits * kBlobElems * 2;
-    static constexpr unsigned kStageBytes = 2 * kOperandBytes;
+    static constexpr unsigned kBLbo = C::kN * 16;                          // B K-group stride
+    static constexpr unsigned kBDigitBytes = C::kN * C::kStep * 2;
+    static constexpr unsigned kBOperandBytes = C::kDigits * kBDigitBytes;
+    static constexpr unsigned kStageBytes = kOperandBytes + kBOperandBytes;
     static constexpr int kHalves = kTile / C::kN;                          // CTAs per tile
     static constexpr int kEpiCols = C::kN / 2;                             // per epilogue warp
     // ring, then the low parts of the epilogue's running pair sums ([warp][column][lane])
@@ -329,6 +336,8 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
     using Dm = TcDims<C>;
     constexpr int kStages = C::kStages, kStepsPerChunk = Dm::kStepsPerChunk;
     constexpr unsigned kStageBytes = Dm::kStageBytes, kOperandBytes = Dm::kOperandBytes;
+    constexpr unsigned kBLbo = Dm::kBLbo, kBDigitBytes = Dm::kBDigitBytes;
+    constexpr int kGroups = C::kStep / 8;  // 8-row K groups of a step
     constexpr int kEpiCols = Dm::kEpiCols;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full, acc_empty, drain;
@@ -400,9 +409,23 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                     mbar_arrive_expect_tx(&full[s], w.one ? kOperandBytes : kStageBytes);
                     bulk_load(dst, DA + blob_offset<C>(w.tb.x, st, 0, nstep), kOperandBytes,
                               &full[s]);
-                    if (!w.one)
-                        bulk_load(dst + kOperandBytes, DB + blob_offset<C>(w.tb.y, st, 0, nstep),
-                                  kOperandBytes, &full[s]);
+                    if (!w.one) {
+                        if (Dm::kHalves == 1) {
+                            bulk_load(dst + kOperandBytes,
+                                      DB + blob_offset<C>(w.tb.y, st, 0, nstep), kOperandBytes,
+                                      &full[s]);
+                        } else {
+                            // this unit's kN columns of every digit and K group of B
+#pragma unroll
+                            for (int d = 0; d < C::kDigits; ++d)
+#pragma unroll
+                                for (int g = 0; g < kGroups; ++g)
+                                    bulk_load(dst + kOperandBytes + d * kBDigitBytes + g * kBLbo,
+                                              DB + blob_offset<C>(w.tb.y, st, d, nstep) +
+                                                  g * (kTile * 8) + w.hf * (C::kN * 8),
+                                              kBLbo, &full[s]);
+                        }
+                    }
                     issued = j + 1;
                 }
             }
@@ -442,7 +465,7 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                     }
                     tc_fence_after();
                     const unsigned char *a = smem + (size_t)s * kStageBytes;
-                    const unsigned char *b = w.one ? a : a + kOperandBytes;
+                    const unsigned char *b = a + kOperandBytes;
 #pragma unroll
                     for (int ks = 0; ks < C::kStep / 16; ++ks) {
 #pragma unroll
@@ -456,8 +479,13 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                                 const bool first = kin == 0 && ks == 0 && sa == 0;
                                 const uint64_t ad = smem_desc(
                                     a + sa * Dm::kBlobElems * 2 + ks * 2 * kLbo, kLbo, kSbo);
-                                const uint64_t bd = smem_desc(
-                                    b + sb * Dm::kBlobElems * 2 + ks * 2 * kLbo + boff, kLbo, kSbo);
+                                // B: its own compact kN columns, or (a diagonal tile of
+                                // A^T A) the unit's columns inside A's blobs
+                                const uint64_t bd =
+                                    w.one ? smem_desc(a + sb * Dm::kBlobElems * 2 + ks * 2 * kLbo +
+                                                          boff, kLbo, kSbo)
+                                          : smem_desc(b + sb * kBDigitBytes + ks * 2 * kBLbo,
+                                                      kBLbo, kSbo);
                                 tc_mma_bf16(tmem + (uint32_t)(cl * C::kN), ad, bd, idesc, !first);
                             }
                         }

@@ -31,7 +31,6 @@ struct DevHam {
 
     const double *V = nullptr;   // V_eff, Nd
     const float *Vf = nullptr;   // V_eff rounded to float (FP32 filter)
-    const float2 *Vdf = nullptr; // V_eff as FP32 pairs (hi, lo) for the pair-arithmetic stencil
 
     int natoms = 0;
     long nsup = 0;                   // support entries over all atoms
@@ -76,12 +75,13 @@ StepCoef<double> make_coef(const DevHam &H, double alpha, double shift, double b
 // scaled by a power of two per column, so each column needs a bound of its magnitude:
 // bY[c] = the largest high word (bits 32..62) of |y| over the column, as written by
 // colmax_f64 or by the launch that produced the block. bOut, if not null, is raised
-// (atomicMax) to the bound of the output's columns. Vc: V_eff - shift as FP32 pairs
-// (H.Vdf for shift 0, else from vshift_pairs).
+// (atomicMax) to the bound of the output's columns. u: alpha (V_eff - shift), Nd values
+// (from scaled_v; H.V itself when alpha = 1 and shift = 0).
 cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, double *out,
-                        int ncols, long ld, double alpha, const float2 *Vc, double beta,
+                        int ncols, long ld, double alpha, const double *u, double beta,
                         const unsigned *bY, unsigned *bOut, cudaStream_t st);
-cudaError_t vshift_pairs(const double *V, double shift, float2 *out, long n, cudaStream_t st);
+cudaError_t scaled_v(const double *V, double alpha, double shift, double *u, long n,
+                     cudaStream_t st);
 // out += V_nl part from Cs = alpha chi^T Y (pairs), for FP64 blocks (stencil_df.cu); bOut
 // as for stencil_f64 (raised to the bound of the updated values)
 cudaError_t scatter_f64_df(const DevHam &H, const float2 *Cs, double *out, int ncols, long ld,

@@ -10,6 +10,7 @@
 // reports an upper bound of what it actually held next to it.
 #include "internal.cuh"
 #include "sparc.h"
+#include "sparc_batch.h"
 #include "sparc_server.h"
 
 #include <algorithm>
@@ -89,6 +90,7 @@ struct sparc_server {
     size_t budget = 0, reserved = 0, peak_reserved = 0;
     int slots = 0;
     bool simulate = false;
+    bool batched = false;  // one scheduler thread, filters of all active requests batched
     int running = 0, max_running = 0;
     int device = 0;  // CUDA device of the creating thread; every worker uses it
     long long completed = 0, next_id = 1;
@@ -225,6 +227,215 @@ void worker(sparc_server *S)
     if (st) cudaStreamDestroy(st);
 }
 
+// ---- continuous batching: one scheduler thread, one stream -------------------------------
+// Each round runs one CheFSI iteration of every active request: the Chebyshev filters of
+// the FP32-filter requests that share the round's degree go through one sparc_batch (the
+// three filter kernels of each step walk one work list over all of them), any other
+// request is filtered on its own, then every request's Rayleigh-Ritz step runs. Between
+// rounds, finished requests leave (their memory returns to the budget) and waiting
+// requests join as the budget and the `slots` limit allow; the batch is rebuilt whenever
+// the set of batched requests changes. The batch keeps its default kernel variant (no
+// autotuning), so a request's arithmetic does not depend on which others share its
+// launches.
+struct Active {
+    Request *r = nullptr;
+    sparc_ctx *ctx = nullptr;
+    void *X = nullptr, *W = nullptr;
+    long nd = 0;
+    double b[3] = {0, 0, 0};
+    sparc_result_info info{};
+    std::vector<double> ritz, resid;
+    bool done = false;
+    sparc_status status = SPARC_OK;
+};
+
+// Context, blocks, start block and first-iteration bounds of an admitted request.
+sparc_status start_active(Active &a, cudaStream_t st)
+{
+    const sparc_request &q = a.r->spec;
+    a.nd = (long)q.n[0] * q.n[1] * q.n[2];
+    const size_t es = q.dtype == SPARC_F32 ? 4 : 8;
+    sparc_grid g{{q.n[0], q.n[1], q.n[2]}, q.h, kRadius};
+    sparc_atoms at{q.natoms, a.r->R.data(), a.r->Z.data(), a.r->gamma.data(), 0.8, 3.0, 1.0};
+    sparc_status s = sparc_create(&g, nullptr, &at, st, &a.ctx);
+    if (s != SPARC_OK) return s;
+    const size_t bb = es * (size_t)a.nd * q.ns;
+    if (cudaMalloc(&a.X, bb) != cudaSuccess || cudaMalloc(&a.W, bb) != cudaSuccess) {
+        cudaGetLastError();
+        return SPARC_ERR_OOM;
+    }
+    const unsigned long long key = host_mix64(q.seed);
+    if (q.dtype == SPARC_F32)
+        k_start_block<float><<<152 * 8, 256, 0, st>>>((float *)a.X, a.nd, q.ns, a.nd, key);
+    else
+        k_start_block<double><<<152 * 8, 256, 0, st>>>((double *)a.X, a.nd, q.ns, a.nd, key);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) return SPARC_ERR_CUDA;
+    a.ritz.assign(q.ns, 0.0);
+    a.resid.assign(q.ns, 0.0);
+    return sparc_first_bounds(a.ctx, kLanczosSteps, q.seed, a.b);
+}
+
+void release_active(Active &a)
+{
+    const sparc_request &q = a.r->spec;
+    const size_t bb = (q.dtype == SPARC_F32 ? 4 : 8) * (size_t)a.nd * q.ns;
+    size_t peak = 0;
+    if (a.ctx) sparc_device_bytes(a.ctx, &peak);
+    a.info.used_bytes = peak + (a.X ? bb : 0) + (a.W ? bb : 0);
+    if (a.X) cudaFree(a.X);
+    if (a.W) cudaFree(a.W);
+    if (a.ctx) sparc_destroy(a.ctx);
+    a.X = a.W = nullptr;
+    a.ctx = nullptr;
+}
+
+// Rayleigh-Ritz of one request after its filter; bounds for the next round as
+// sparc_chefsi_step sets them (a = largest, a0 = smallest Ritz value).
+void rr_active(Active &a)
+{
+    const sparc_request &q = a.r->spec;
+    sparc_status s = sparc_orth_rr(a.ctx, q.dtype, a.X, nullptr, q.ns, a.nd, a.ritz.data(),
+                                   a.resid.data());
+    a.info.iters++;
+    if (s != SPARC_OK) {
+        a.status = s;
+        a.done = true;
+        return;
+    }
+    a.b[0] = *std::max_element(a.ritz.begin(), a.ritz.end());
+    a.b[2] = *std::min_element(a.ritz.begin(), a.ritz.end());
+    if (*std::max_element(a.resid.begin(), a.resid.end()) <= q.tol) {
+        a.info.converged = 1;
+        a.done = true;
+    } else if (a.info.iters >= q.max_iters) {
+        a.done = true;
+    }
+}
+
+void scheduler(sparc_server *S)
+{
+    cudaStream_t st = nullptr;
+    const bool gpu_ok = cudaSetDevice(S->device) == cudaSuccess &&
+                        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+    std::vector<std::unique_ptr<Active>> act;
+    sparc_batch *batch = nullptr;
+    std::vector<sparc_ctx *> batch_ctxs;
+    for (;;) {
+        // admit waiting requests while slots and budget allow (block when nothing runs)
+        std::vector<Request *> joined;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (act.empty())
+                S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+            if (S->stop && act.empty()) break;
+            Request *r;
+            while (!S->stop && (int)act.size() + (int)joined.size() < S->slots &&
+                   (r = pick(S)) != nullptr) {
+                S->reserved += r->est;
+                S->peak_reserved = std::max(S->peak_reserved, S->reserved);
+                S->running++;
+                S->max_running = std::max(S->max_running, S->running);
+                r->info.t_admit = now_since(S->t0);
+                joined.push_back(r);
+            }
+        }
+        for (Request *r : joined) {
+            auto a = std::make_unique<Active>();
+            a->r = r;
+            a->info = r->info;
+            a->status = gpu_ok ? start_active(*a, st) : SPARC_ERR_CUDA;
+            if (a->status != SPARC_OK) a->done = true;
+            act.push_back(std::move(a));
+        }
+        if (act.empty()) continue;
+        // the round: batched filters, then the other filters, then every Rayleigh-Ritz
+        int degree = -1;
+        std::vector<Active *> bat;
+        for (auto &a : act) {
+            if (a->done || a->r->spec.dtype != SPARC_F32) continue;
+            if (degree < 0) degree = a->r->spec.degree;
+            if (a->r->spec.degree == degree) bat.push_back(a.get());
+        }
+        std::vector<sparc_ctx *> want;
+        for (Active *a : bat) want.push_back(a->ctx);
+        if (want != batch_ctxs) {
+            sparc_batch_destroy(batch);
+            batch = nullptr;
+            batch_ctxs.clear();
+            if (!want.empty() && sparc_batch_create(want.data(), (int)want.size(), st, &batch) ==
+                                     SPARC_OK)
+                batch_ctxs = want;
+        }
+        if (!bat.empty()) {
+            std::vector<float *> X, W;
+            std::vector<int> nc;
+            std::vector<long> ld;
+            std::vector<double> bounds;
+            for (Active *a : bat) {
+                X.push_back((float *)a->X);
+                W.push_back((float *)a->W);
+                nc.push_back(a->r->spec.ns);
+                ld.push_back(a->nd);
+                bounds.insert(bounds.end(), a->b, a->b + 3);
+            }
+            const sparc_status s =
+                batch ? sparc_batch_filter(batch, X.data(), W.data(), nc.data(), ld.data(), degree,
+                                           bounds.data())
+                      : SPARC_ERR_OOM;
+            if (s != SPARC_OK)
+                for (Active *a : bat) a->status = s, a->done = true;
+        }
+        for (auto &a : act) {
+            if (a->done) continue;
+            const bool batched = std::find(bat.begin(), bat.end(), a.get()) != bat.end();
+            if (!batched) {
+                const sparc_request &q = a->r->spec;
+                const sparc_status s = sparc_cheb_filter(a->ctx, q.dtype, a->X, a->W, q.ns, a->nd,
+                                                         q.degree, a->b[0], a->b[1], a->b[2]);
+                if (s != SPARC_OK) {
+                    a->status = s;
+                    a->done = true;
+                    continue;
+                }
+            }
+            rr_active(*a);
+        }
+        // finished requests leave; the batch over them goes first (it uses their contexts)
+        bool left = false;
+        for (auto &a : act) left = left || a->done;
+        if (!left) continue;
+        sparc_batch_destroy(batch);
+        batch = nullptr;
+        batch_ctxs.clear();
+        for (auto it = act.begin(); it != act.end();) {
+            Active &a = **it;
+            if (!a.done) {
+                ++it;
+                continue;
+            }
+            release_active(a);
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                Request *r = a.r;
+                a.info.status = a.status;
+                a.info.t_done = now_since(S->t0);
+                r->info = a.info;
+                r->ritz = std::move(a.ritz);
+                r->resid = std::move(a.resid);
+                r->done = true;
+                S->reserved -= r->est;
+                S->running--;
+                S->completed++;
+            }
+            S->cv_done.notify_all();
+            it = act.erase(it);
+        }
+    }
+    sparc_batch_destroy(batch);
+    if (st) cudaStreamDestroy(st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -236,10 +447,10 @@ size_t sparc_request_bytes(const sparc_request *q)
     const int ns = q->ns;
     const size_t es = q->dtype == SPARC_F32 ? 4 : 8;
     const size_t na = q->natoms > 0 ? (size_t)q->natoms : 1;
-    // context: V_eff (FP64, FP32, FP32 pair) and set-up scratch per node, projector entries
-    // (index, chi and gamma chi in FP64 / FP32 / pairs, inverse map), bounded by the cube
-    // around each support sphere
-    const size_t per_node = 8 + 4 + 8 + 4 * 8 + 8;
+    // context: V_eff (FP64, FP32) and set-up scratch per node, projector entries (index,
+    // chi and gamma chi in FP64 / FP32 / pairs, inverse map), bounded by the cube around
+    // each support sphere
+    const size_t per_node = 8 + 4 + 4 * 8 + 8;
     const size_t per_entry = 4 + 4 + 32 + 32 + 16 + 16 + 32 + 4 + 4 + 16 + 32 + 16;
     const size_t entries = na * (size_t)nodes_in_support_box(q->h, 3.0);
     size_t b = per_node * (size_t)nd + per_entry * entries + 4096 * 64;
@@ -254,7 +465,7 @@ size_t sparc_request_bytes(const sparc_request *q)
     b += tc_slab_workspace(nd, ns, mixed);
     if (tc_slab_rows(nd, ns, mixed) < nd) b += sizeof(double) * 2 * (size_t)ns * ns;
     if (!mixed) {
-        // column bounds of the filter's blocks, V_eff - shift pairs
+        // column bounds of the filter's blocks, alpha (V_eff - shift) of a step
         b += sizeof(unsigned) * ((size_t)(q->degree + 1) * ns + (size_t)ns);
         b += 8 * (size_t)nd;
     }
@@ -279,6 +490,25 @@ sparc_status sparc_server_create(size_t hbm_budget_bytes, int slots, int simulat
         return SPARC_ERR_CUDA;
     }
     for (int i = 0; i < slots; ++i) S->workers.emplace_back(worker, S);
+    *out = S;
+    return SPARC_OK;
+}
+
+sparc_status sparc_server_create_batched(size_t hbm_budget_bytes, int max_active,
+                                         sparc_server **out)
+{
+    if (!out || max_active < 1 || max_active > 1024 || hbm_budget_bytes == 0)
+        return SPARC_ERR_ARG;
+    sparc_server *S = new (std::nothrow) sparc_server();
+    if (!S) return SPARC_ERR_OOM;
+    S->budget = hbm_budget_bytes;
+    S->slots = max_active;
+    S->batched = true;
+    if (cudaGetDevice(&S->device) != cudaSuccess) {
+        delete S;
+        return SPARC_ERR_CUDA;
+    }
+    S->workers.emplace_back(scheduler, S);
     *out = S;
     return SPARC_OK;
 }

@@ -57,7 +57,6 @@ struct sparc_ctx {
     // owned tables
     double *V = nullptr;
     float *Vf = nullptr;
-    float2 *Vdf = nullptr;
     int *atom_ptr = nullptr, *idx = nullptr, *ent_atom = nullptr;
     double *chi = nullptr, *gchi = nullptr;
     float *chi_f = nullptr, *gchi_f = nullptr;
@@ -78,8 +77,7 @@ struct sparc_ctx {
     void *lz = nullptr;      size_t lz_bytes = 0;    // Lanczos vectors and scalars
     void *bnd = nullptr;     size_t bnd_bytes = 0;   // column bounds of the FP64 filter's blocks
     void *bsc = nullptr;     size_t bsc_bytes = 0;   // column bounds of other FP64 H applications
-    void *vc = nullptr;      size_t vc_bytes = 0;    // V_eff - vc_shift as FP32 pairs
-    double vc_shift = 0.0;   bool vc_valid = false;
+    void *vc = nullptr;      size_t vc_bytes = 0;    // alpha (V_eff - shift) of an FP64 step
     int *flags = nullptr;                            // device status words
     void *obs = nullptr;     size_t obs_bytes = 0;   // occupations, density and force data
     std::vector<double> gamma;                       // KB coefficients, 4 per atom (host)
@@ -247,20 +245,17 @@ sparc_status scratch_bounds(sparc_ctx *ctx, const T *Y, int ncols, long ld, unsi
     return SPARC_OK;
 }
 
-// V_eff - shift as FP32 pairs for the FP64 stencil (kept until the shift changes).
-sparc_status shifted_v(sparc_ctx *ctx, double shift, const float2 **Vc)
+// alpha (V_eff - shift) for one FP64 step (formed on the context stream before the step;
+// V_eff itself for alpha = 1, shift = 0).
+sparc_status scaled_potential(sparc_ctx *ctx, double alpha, double shift, const double **u)
 {
-    if (shift == 0.0) {
-        *Vc = ctx->H.Vdf;
+    if (alpha == 1.0 && shift == 0.0) {
+        *u = ctx->H.V;
         return SPARC_OK;
     }
-    if (!ctx->vc_valid || ctx->vc_shift != shift) {
-        TRY(ensure(ctx, ctx->vc, ctx->vc_bytes, sizeof(float2) * (size_t)ctx->H.nd));
-        CK(vshift_pairs(ctx->H.V, shift, (float2 *)ctx->vc, ctx->H.nd, ctx->st));
-        ctx->vc_shift = shift;
-        ctx->vc_valid = true;
-    }
-    *Vc = (const float2 *)ctx->vc;
+    TRY(ensure(ctx, ctx->vc, ctx->vc_bytes, sizeof(double) * (size_t)ctx->H.nd));
+    CK(scaled_v(ctx->H.V, alpha, shift, (double *)ctx->vc, ctx->H.nd, ctx->st));
+    *u = (const double *)ctx->vc;
     return SPARC_OK;
 }
 
@@ -277,13 +272,13 @@ sparc_status step_f64(sparc_ctx *ctx, const double *Y, const double *Yprev, doub
         TRY(scratch_bounds(ctx, Y, ncols, ld, &b));
         bY = b;
     }
-    const float2 *Vc = nullptr;
-    TRY(shifted_v(ctx, shift, &Vc));
+    const double *u = nullptr;
+    { PHASE(SPARC_PHASE_STENCIL); TRY(scaled_potential(ctx, alpha, shift, &u)); }
     if (H.natoms > 0) {
         TRY(ensure_C(ctx, ncols));
         { PHASE(SPARC_PHASE_PROJECT); CK(project_f64_df(H, Y, ncols, ld, alpha, (float2 *)ctx->C, ctx->st)); }
     }
-    { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f64(H, Y, Yprev, out, ncols, ld, alpha, Vc, beta, bY, bOut, ctx->st)); }
+    { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f64(H, Y, Yprev, out, ncols, ld, alpha, u, beta, bY, bOut, ctx->st)); }
     if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f64_df(H, (const float2 *)ctx->C, out, ncols, ld, bOut, ctx->st)); }
     return SPARC_OK;
 }
@@ -592,7 +587,7 @@ bool lap_weights_int(int no, double h, int *wint, double &wunit)
 void free_ctx(sparc_ctx *c)
 {
     if (!c) return;
-    void *ps[] = {c->V, c->Vf, c->Vdf, c->atom_ptr, c->idx, c->ent_atom, c->chi, c->gchi, c->chi_f,
+    void *ps[] = {c->V, c->Vf, c->atom_ptr, c->idx, c->ent_atom, c->chi, c->gchi, c->chi_f,
                   c->gchi_f, c->chi_df, c->uniq_node, c->uniq_ptr, c->ent_list, c->nl_atom, c->nl_gf, c->nl_gdf, c->C, c->hx, c->rotx, c->roth, c->part,
                   c->tcws, c->dm, c->lz, c->bnd, c->bsc, c->vc, c->flags, c->obs, c->pois};
     for (void *p : ps) dfree(p);
@@ -743,7 +738,6 @@ sparc_status sparc_create(const sparc_grid *grid, const double *veff_host,
         H.err = ctx->flags + 14;
         TRY(dmalloc(ctx, ctx->V, nd));
         TRY(dmalloc(ctx, ctx->Vf, nd));
-        TRY(dmalloc(ctx, ctx->Vdf, nd));
         if (veff_host) {
             CK(cudaMemcpyAsync(ctx->V, veff_host, sizeof(double) * nd, cudaMemcpyHostToDevice,
                                ctx->st));
@@ -764,8 +758,6 @@ sparc_status sparc_create(const sparc_grid *grid, const double *veff_host,
             CK(cudaFree(Z));
         }
         CK(to_float(ctx->V, ctx->Vf, nd, ctx->st));
-        CK(to_float_pair(ctx->V, ctx->Vdf, nd, ctx->st));
-        H.Vdf = ctx->Vdf;
         H.V = ctx->V;
         H.Vf = ctx->Vf;
         TRY(build_tables(ctx, atoms));

@@ -23,8 +23,9 @@ import numpy as np
 from . import sparc, synth
 
 F32, F64 = 1, 0
-EXPORTS = ("sparc_request_bytes", "sparc_server_create", "sparc_server_destroy",
-           "sparc_server_stats", "sparc_server_submit", "sparc_server_wait")
+EXPORTS = ("sparc_request_bytes", "sparc_server_create", "sparc_server_create_batched",
+           "sparc_server_destroy", "sparc_server_stats", "sparc_server_submit",
+           "sparc_server_wait")
 
 
 class _Request(C.Structure):
@@ -46,6 +47,7 @@ def _bind(L):
         return L
     vp = C.c_void_p
     L.sparc_server_create.argtypes = [C.c_size_t, C.c_int, C.c_int, C.POINTER(vp)]
+    L.sparc_server_create_batched.argtypes = [C.c_size_t, C.c_int, C.POINTER(vp)]
     L.sparc_request_bytes.argtypes = [C.POINTER(_Request)]
     L.sparc_request_bytes.restype = C.c_size_t
     L.sparc_server_submit.argtypes = [vp, C.POINTER(_Request), C.POINTER(C.c_longlong)]
@@ -54,8 +56,8 @@ def _bind(L):
     L.sparc_server_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int),
                                      C.POINTER(C.c_size_t)]
     L.sparc_server_destroy.argtypes = [vp]
-    for name in ("sparc_server_create", "sparc_server_submit", "sparc_server_wait",
-                 "sparc_server_stats", "sparc_server_destroy"):
+    for name in ("sparc_server_create", "sparc_server_create_batched", "sparc_server_submit",
+                 "sparc_server_wait", "sparc_server_stats", "sparc_server_destroy"):
         getattr(L, name).restype = C.c_int
     L._server_bound = True
     return L
@@ -98,14 +100,21 @@ def request_bytes(spec: Spec) -> int:
 
 
 class Server:
-    """A sparc_server: `slots` workers, an HBM budget in bytes; simulate=True runs no GPU
-    work (each solve sleeps spec.sim_seconds)."""
+    """A sparc_server: `slots` workers (or, batched=True, one scheduler running rounds over
+    at most `slots` active requests whose filters share launches), an HBM budget in bytes;
+    simulate=True runs no GPU work (each solve sleeps spec.sim_seconds; worker mode only)."""
 
-    def __init__(self, budget_bytes: int, slots: int = 4, simulate: bool = False):
+    def __init__(self, budget_bytes: int, slots: int = 4, simulate: bool = False,
+                 batched: bool = False):
         self._L = _bind(sparc.load())
         h = C.c_void_p()
-        st = self._L.sparc_server_create(int(budget_bytes), int(slots), int(bool(simulate)),
-                                         C.byref(h))
+        if batched:
+            if simulate:
+                raise ValueError("the batched server has no simulated mode")
+            st = self._L.sparc_server_create_batched(int(budget_bytes), int(slots), C.byref(h))
+        else:
+            st = self._L.sparc_server_create(int(budget_bytes), int(slots),
+                                             int(bool(simulate)), C.byref(h))
         if st != 0:
             raise sparc.SparcError(st, "sparc_server_create")
         self._h = h
@@ -179,12 +188,13 @@ def draw_requests(count: int, seed: int, edges=EDGES, atoms=(4, 200), states=(32
     return out
 
 
-def run_arrivals(specs: list, rate: float, budget: int, slots: int, seed: int) -> dict:
+def run_arrivals(specs: list, rate: float, budget: int, slots: int, seed: int,
+                 batched: bool = False) -> dict:
     """Submits `specs` at Poisson arrival times of the given rate (requests/s) and waits for
     all; latency = completion - arrival (steady-clock seconds in the library)."""
     gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=len(specs))
     arrive = np.cumsum(gaps) - gaps[0]
-    srv = Server(budget, slots)
+    srv = Server(budget, slots, batched=batched)
     try:
         t0 = time.perf_counter()
         ids = []

@@ -65,3 +65,52 @@ def test_converged_request_matches_dense_eigenvalues():
     k = w.ns - 2
     assert np.max(np.abs(r["ritz"][:k] - ev[:k])) <= 1e-10
     assert np.max(r["resid"][:k]) <= 1e-6
+
+
+def test_batched_server_requests_join_mid_flight_and_match_their_solo_runs():
+    # 18 requests, at most 6 active: the filters of the active requests share launches
+    # (one work list per kernel per filter step), requests leave after 3 to 6 iterations
+    # and waiting ones join the running batch. Each result must be bitwise the one the same
+    # request gives alone (the batch's per-point arithmetic does not depend on the other
+    # requests in it).
+    specs = serve.draw_requests(18, seed=5, edges=(32, 40, 48), atoms=(2, 8), states=(16, 48),
+                                degree=10, iters=6, tol=1e-12)
+    for i, s in enumerate(specs):
+        s.max_iters = 3 + i % 4
+    budget = sum(serve.request_bytes(s) for s in specs)
+    srv = serve.Server(budget, slots=6, batched=True)
+    ids = [srv.submit(s) for s in specs]
+    mix = [srv.wait(i, timeout=600) for i in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(specs) and st["max_running"] == 6
+    # some requests were admitted only after others had finished
+    admits = sorted(r["t_admit"] for r in mix)
+    first_done = min(r["t_done"] for r in mix)
+    assert sum(t > first_done for t in admits) >= 6
+    srv = serve.Server(budget, slots=1, batched=True)
+    alone = [srv.wait(srv.submit(s), timeout=600) for s in specs]
+    srv.close()
+    for s, a, b in zip(specs, mix, alone):
+        assert a["status"] == 0 and b["status"] == 0
+        assert a["iters"] == b["iters"] == s.max_iters
+        assert np.array_equal(a["ritz"], b["ritz"])
+        assert np.array_equal(a["resid"], b["resid"])
+        assert np.all(np.diff(a["ritz"]) >= 0)
+        assert 0 < a["used_bytes"] <= a["est_bytes"]
+
+
+def test_batched_server_result_matches_the_worker_server():
+    # the same request through the batched filter and through sparc_chefsi_step on a
+    # worker: the same mixed-precision solve, within the form's 1e-5 Ha contract
+    specs = serve.draw_requests(3, seed=8, edges=(40, 48), atoms=(2, 6), states=(16, 32),
+                                degree=10, iters=4, tol=1e-12)
+    budget = sum(serve.request_bytes(s) for s in specs)
+    out = []
+    for batched in (True, False):
+        srv = serve.Server(budget, slots=3, batched=batched)
+        out.append([srv.wait(srv.submit(s), timeout=600) for s in specs])
+        srv.close()
+    for a, b in zip(*out):
+        assert a["status"] == 0 and b["status"] == 0
+        assert np.max(np.abs(a["ritz"] - b["ritz"])) <= 1e-5
