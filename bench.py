@@ -190,8 +190,8 @@ def stencil_algorithmic(w, dtype: str, prof: dict, steps: int) -> dict:
 
     Per point-orbital a filter step reads Y_j and Y_{j-1} and writes Y_{j+1} (3 elements);
     the first step of a filter and an H X read one block and write one (2 elements); each
-    launch also reads V_eff once per node (8 B as an FP32 pair in the FP64 kernels, 4 B in
-    the FP32 kernel). Flops per point-orbital: 6 radii x (5 adds + 1 FMA) + centre
+    launch also reads the potential once per node (8 B: alpha (V_eff - shift) in FP64 in the
+    FP64 kernel, 4 B in the FP32 kernel). Flops per point-orbital: 6 radii x (5 adds + 1 FMA) + centre
     (1 FMA + 1 multiply) + recurrence (1 FMA) = 47 (45 without the recurrence term).
     FP64 form per iteration: 2-stream first step, m - 1 3-stream steps, 2-stream H Y_f, all
     FP64. Mixed form per FP32 iteration: FP32 steps (4-byte elements) and the FP64 H Y_f of
@@ -345,12 +345,12 @@ def run_ours(args, rank, world, local_rank):
             roof["issue"] = {"issue_active": tr["issue_active"],
                              "thread_inst_per_ptorb": tr["thread_inst_per_ptorb"]}
     if dtype == "f64":
-        # The FP64 step runs on the integer and FP32 pipes (exact integer neighbour sums,
-        # FP32-pair scaling); its FP64-equivalent flop rate is compared with the FP64
-        # pipe's issue limit as context.
+        # The FP64 step runs its neighbour sums on the integer and FP32 pipes (exact integer
+        # sums) and spends four FP64 operations per point; its FP64-equivalent flop rate is
+        # compared with the FP64 pipe's issue limit as context.
         fl = alg["flops"] / (alg["ms"] / 1e3) / 1e12 if alg["ms"] > 0 else None
         roof["kernel"] = ("k_stencil_df (fused stencil + V_eff + recurrence; exact integer "
-                          "neighbour sums, FP32-pair scaling)")
+                          "neighbour sums, four FP64 operations per point)")
         roof["fp64_equiv_tflops"] = fl
         roof["fp64_pipe_peak_tflops"] = fp64_alu_peak_tflops(sm_max)
     else:

@@ -61,18 +61,21 @@ constexpr int kNonFinite = INT32_MIN;          // exponent sentinel of a chunk w
 constexpr unsigned kLbo = 2048, kSbo = 128;
 }  // namespace
 
-// The two representations. Tc23 (mixed form): entries rounded to 23 bits of the chunk's
-// largest, three digits, classes 0..2, 256-row chunks, 128 x 128 tiles. Tc47 (FP64 form):
-// 47 bits, six digits, classes 0..5 (21 digit MMAs per 16 rows; a class sums at most six
-// digit products, so 128-row chunks keep it below 2^24), 128 x 64 half tiles (six class
-// accumulators of 64 columns fit the 512 tensor-memory columns).
+// The representations. Tc23: entries rounded to 23 bits of the chunk's largest, three
+// base-256 digits, classes 0..2, 256-row chunks, 128 x 128 tiles (sparc_gram_tc, the mixed
+// form's rotation). Tc47: 47 bits, six base-256 digits, classes 0..5 (21 digit MMAs per 16
+// rows; a class sums at most six digit products, so 128-row chunks keep it below 2^24),
+// 128 x 64 half tiles (six class accumulators of 64 columns fit the 512 tensor-memory
+// columns): the Gram pairs of both forms and the FP64 form's rotation. The digit base is a
+// parameter (kBase bits); kScale = kBits - kBase (kDigits - 1), so that
+// x = 2^(e - kScale) sum_s d_s 2^(-kBase s).
 struct Tc23 {
     static constexpr int kDigits = 3, kClasses = 3, kBits = 23, kChunk = 256, kStep = 32,
-                         kN = 128, kStages = 3;
+                         kN = 128, kStages = 3, kBase = 8;
 };
 struct Tc47 {
     static constexpr int kDigits = 6, kClasses = 6, kBits = 47, kChunk = 128, kStep = 16,
-                         kN = 64, kStages = 4;
+                         kN = 64, kStages = 4, kBase = 8;
 };
 // A stage holds A's blobs (all 128 columns of each digit) and the kN columns of B's blobs
 // this CTA multiplies: per digit and 8-row K group, kN / 8 core matrices of 128 B (copied
@@ -92,7 +95,13 @@ template <class C> struct TcDims {
     static constexpr unsigned kLowBytes = kEpiWarps * kEpiCols * 32 * 4;
     static constexpr unsigned kSmemBytes = C::kStages * kStageBytes + kLowBytes + 1024;
     static_assert(C::kClasses * C::kN <= kTmemCols, "class accumulators exceed tensor memory");
-    static_assert(C::kBits == 8 * (C::kDigits - 1) + 7, "top digit must stay within [0, 128]");
+    static_assert(C::kBits <= C::kBase * C::kDigits - 1,
+                  "top digit must stay within [0, 2^(kBase - 1)]");
+    // a class sums at most kClasses digit products of magnitude <= 2^(2 kBase - 2) per row:
+    // exact in the FP32 accumulator over a chunk
+    static_assert(((long)C::kClasses << (2 * C::kBase - 2)) * C::kChunk < (1L << 24),
+                  "class sums of a chunk must stay exact in FP32");
+    static constexpr int kScale = C::kBits - C::kBase * (C::kDigits - 1);
 };
 
 namespace {
@@ -180,12 +189,14 @@ k_tc_digits(const T *__restrict__ X, long ld, long nd, int ns, long nstep,
             else if (sh < 8 * (int)sizeof(U))
                 N = (long)((m + ((U)1 << (sh - 1))) >> sh);
         }
-        // balanced base-256 digits from the bottom; the top one lies in [0, 128]
+        // balanced base-2^kBase digits from the bottom; the top one lies in
+        // [0, 2^(kBase - 1)]
+        constexpr long kHalf = 1L << (C::kBase - 1), kMask = (1L << C::kBase) - 1;
         int d[C::kDigits];
 #pragma unroll
         for (int s = C::kDigits - 1; s > 0; --s) {
-            d[s] = (int)(((N + 128) & 255) - 128);
-            N = (N - d[s]) >> 8;
+            d[s] = (int)(((N + kHalf) & kMask) - kHalf);
+            N = (N - d[s]) >> C::kBase;
         }
         d[0] = (int)N;
         const int sg = ng[u] ? -1 : 1;
@@ -200,13 +211,13 @@ k_tc_digits(const T *__restrict__ X, long ld, long nd, int ns, long nstep,
     }
 }
 
-// 2^(e - 7) as an FP32 factor (the chunk scale 2^(e_i + e_j - 14) is applied as two such
-// factors, each exact); 0 below the FP32 normal range, NaN for a non-finite chunk. The
-// scale is the same for both forms: 2 kBits - 2 * 8 (kDigits - 1) = 14.
+// 2^(e - kScale) as an FP32 factor (the chunk scale 2^(e_i + e_j - 2 kScale) is applied as
+// two such factors, each exact); 0 below the FP32 normal range, NaN for a non-finite chunk.
+template <class C>
 __device__ __forceinline__ float pow2_factor(int e)
 {
     if (e == kNonFinite) return __int_as_float(0x7FC00000);
-    const int b = e - 7 + 127;
+    const int b = e - TcDims<C>::kScale + 127;
     if (b <= 0) return 0.0f;
     if (b >= 255) return __int_as_float(0x7F800000);
     return __int_as_float(b << 23);
@@ -293,11 +304,12 @@ k_tc_digits_t(const T *__restrict__ Y, long ld, long nd, int ns, long nstep,
                 N = (long)((m + ((U)1 << (sh - 1))) >> sh);
         }
         const int sg = B::neg(x[t]) ? -1 : 1;
+        constexpr long kHalf = 1L << (C::kBase - 1), kMask = (1L << C::kBase) - 1;
 #pragma unroll
         for (int s2 = C::kDigits - 1; s2 > 0; --s2) {
-            const int v = (int)(((N + 128) & 255) - 128);
+            const int v = (int)(((N + kHalf) & kMask) - kHalf);
             d[s2][t] = sg * v;
-            N = (N - v) >> 8;
+            N = (N - v) >> C::kBase;
         }
         d[0][t] = sg * (int)N;
     }
@@ -527,7 +539,7 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                     break;
                 }
                 tc_fence_after();
-                const float fA = pow2_factor(EA[c * ea_stride + colA]);
+                const float fA = pow2_factor<C>(EA[c * ea_stride + colA]);
                 const int *eb = EB + c * (ROT ? eb_ld : ns_pad) + (long)w.tb.y * kTile +
                                 w.hf * C::kN + hw * kEpiCols;
 #pragma unroll
@@ -546,13 +558,13 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                         float wt = 1.0f;
 #pragma unroll
                         for (int cl = 1; cl < C::kClasses; ++cl) {
-                            wt *= 0.00390625f;  // 2^-8
+                            wt *= 1.0f / (float)(1 << C::kBase);  // 2^-kBase
                             float t, e2;
                             two_sum_f(h, __uint_as_float(v[cl][x]) * wt, t, e2);
                             h = t;
                             l += e2;
                         }
-                        const float f = fA * pow2_factor(eb[g * 8 + x]);
+                        const float f = fA * pow2_factor<C>(eb[g * 8 + x]);
                         const float ph = h * f, pl = l * f;
                         float sh, se;
                         two_sum_f(H[g * 8 + x], ph, sh, se);

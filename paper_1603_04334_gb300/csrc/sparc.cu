@@ -273,7 +273,7 @@ sparc_status step_f64(sparc_ctx *ctx, const double *Y, const double *Yprev, doub
         bY = b;
     }
     const double *u = nullptr;
-    { PHASE(SPARC_PHASE_STENCIL); TRY(scaled_potential(ctx, alpha, shift, &u)); }
+    { PHASE(SPARC_PHASE_OTHER); TRY(scaled_potential(ctx, alpha, shift, &u)); }
     if (H.natoms > 0) {
         TRY(ensure_C(ctx, ncols));
         { PHASE(SPARC_PHASE_PROJECT); CK(project_f64_df(H, Y, ncols, ld, alpha, (float2 *)ctx->C, ctx->st)); }

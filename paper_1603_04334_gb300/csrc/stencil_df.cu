@@ -88,113 +88,44 @@ __device__ __forceinline__ double int51_to_double(long long t)
 }
 
 // TI is the input block's type: FP64, or FP32 (the mixed-precision Rayleigh-Ritz step
-// applies H in FP64 to the FP32 filtered block). A CTA owns a BX x BY tile of (x, y) of one
-// column and walks its z range, one plane per CTA barrier, with two kinds of warps:
-//   * sum threads (one per (x, y) node, BX * BY of them) keep the 13 planes around the
-//     current one in registers on the column's grid, stage the current plane's tile with
-//     its x and y halos in shared memory (the halo strips, 2 R (BX + BY) nodes, loaded and
-//     converted by all sum threads together, at most two each), form the exact integer sum
-//     T of every node of plane k and leave it in shared memory;
-//   * finish threads (kFinish of them, BX * BY / kFinish nodes each) take plane k - 1's T
-//     in the same period and spend the step's four FP64 operations per node on it
-//     (out = alpha g 2^(E-26) T + alpha (V - shift) y - beta Y_{j-1}), with their loads of
-//     y, alpha (V - shift) and Y_{j-1} issued one plane ahead.
-// GB300 issues FP64 at 1/64 of the FP32 rate; kept apart, the finish warps feed the FP64
-// unit through the whole plane while the sum warps keep the integer and FP32 pipes busy,
-// instead of every warp reaching the FP64 tail together before each barrier. u: the
-// launch's alpha (V_eff - shift), Nd values.
-constexpr int kFinish = 128;
-
-// The two roles meet at the CTA barrier from different code paths; every warp belongs
-// wholly to one role (BX * BY is a multiple of 32), and each role passes the barrier the
-// same number of times per launch.
-__device__ __forceinline__ void role_barrier() { __syncthreads(); }
-
+// applies H in FP64 to the FP32 filtered block). One thread per (x, y) node of a BX x BY
+// tile walks the tile's z range of one column; the 13 planes around it stay in registers
+// on the column's grid, the current plane's tile with its x and y halos in shared memory.
+// The halo strips (2 R (BX + BY) nodes) are loaded and converted by all threads together,
+// at most two nodes each, so no warp runs them as a divergent side branch. The next
+// plane's halo values, queue entry, alpha (V - shift) and Y_{j-1} are loaded during the
+// current plane's compute. u: the launch's alpha (V_eff - shift), Nd values.
 template <typename TI, int BX, int BY>
-__global__ void __launch_bounds__(BX * BY + kFinish, 2)
+__global__ void __launch_bounds__(BX *BY, 2)
 k_stencil_df(const TI *__restrict__ Y, const double *Yprev, double *out,
              const double *__restrict__ u, int n0, int n1, int n2, long ld, int nzc, int zchunk,
              FxCoef cf, const unsigned *__restrict__ bY, unsigned *bOut)
 {
-    constexpr int R = kRadius, SX = BX + 2 * R, SY = BY + 2 * R, NS = BX * BY;
+    constexpr int R = kRadius, SX = BX + 2 * R, SY = BY + 2 * R, NT = BX * BY;
     constexpr int NH = 2 * R * (BX + BY);  // halo nodes of a plane
-    constexpr int PF = NS / kFinish;       // nodes per finish thread
-    static_assert(NH <= 2 * NS, "at most two halo nodes per sum thread");
-    static_assert(NS % kFinish == 0, "finish threads split the tile evenly");
-    static_assert(NS % 32 == 0, "each warp holds one role");
-    // plane k is read from buffer b while plane k+1 is staged into buffer b ^ 1; the sums of
-    // plane k go to Ts[b] while the finish threads read plane k-1's from Ts[b ^ 1]: one
-    // barrier per plane
+    static_assert(NH <= 2 * NT, "at most two halo nodes per thread");
+    // plane k is read from buffer b while plane k+1 is staged into buffer b ^ 1: one barrier
+    // per plane, and the global loads of plane k+1 are in flight while plane k is computed
     __shared__ int2 s[2 * SY * SX];
-    __shared__ long long Ts[2][NS];
-    const int tid = threadIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+    const int i = i0 + tx, j = j0 + ty;
     const int col = blockIdx.z / nzc;
     const int k0 = (blockIdx.z % nzc) * zchunk;
     const int k1 = min(n2, k0 + zchunk);
     const unsigned plane = (unsigned)n0 * (unsigned)n1;  // offsets in a column fit 32 bits
-    const long cb = (long)col * ld;  // the column's offset in Y, Y_{j-1} and out
-    const unsigned uy = bY[col];
-    const int EY = bound_exponent(uy);  // grid values in units of 2^(EY-26)
-
-    if (tid >= NS) {
-        // ---- finish threads: FP64 tail of plane k - 1 during the period of plane k -------
-        const int f = tid - NS;
-        const bool hasP = Yprev != nullptr;
-        const bool nonfinite = ((uy >> 20) & 0x7ffu) == 0x7ffu;
-        const double gs = ldexp(cf.ag, EY - 26);  // alpha g 2^(EY-26)
-        unsigned pij[PF];
-        bool act[PF];
-#pragma unroll
-        for (int t = 0; t < PF; ++t) {
-            const int nn = f + t * kFinish, i = i0 + nn % BX, j = j0 + nn / BX;
-            act[t] = i < n0 && j < n1;
-            pij[t] = act[t] ? (unsigned)i + (unsigned)n0 * (unsigned)j : 0u;
-        }
-        double yv[PF], uv[PF], pv[PF];
-        auto load = [&](int k) {
-            const unsigned pk = (unsigned)k * plane;
-#pragma unroll
-            for (int t = 0; t < PF; ++t) {
-                yv[t] = act[t] ? as_f64(Y[cb + pij[t] + pk]) : 0.0;
-                uv[t] = act[t] ? u[pij[t] + pk] : 0.0;
-                pv[t] = act[t] && hasP ? cf.mbeta * Yprev[cb + pij[t] + pk] : 0.0;
-            }
-        };
-        unsigned omax = 0u;
-        if (k0 < k1) load(k0);
-        for (int k = k0; k <= k1; ++k) {
-            role_barrier();  // plane k - 1's sums are in Ts[(k - 1 - k0) & 1]
-            if (k == k0) continue;
-            const long long *T = Ts[(k - 1 - k0) & 1];
-            double o[PF];
-#pragma unroll
-            for (int t = 0; t < PF; ++t)
-                o[t] = fma(gs, int51_to_double(T[f + t * kFinish]), fma(uv[t], yv[t], pv[t]));
-            const unsigned pk = (unsigned)(k - 1) * plane;
-            if (k < k1) load(k);  // the next plane's operands, in flight during this one
-#pragma unroll
-            for (int t = 0; t < PF; ++t) {
-                if (!act[t]) continue;
-                if (nonfinite) o[t] = __longlong_as_double(0x7ff8000000000000ll);
-                omax = max(omax, abs_hi_word(o[t]));
-                out[cb + pij[t] + pk] = o[t];
-            }
-        }
-        if (bOut) {
-            omax = __reduce_max_sync(0xffffffffu, omax);
-            if ((tid & 31) == 0 && omax) raise_bound(bOut + col, omax);
-        }
-        return;
-    }
-
-    // ---- sum threads ---------------------------------------------------------------------
-    const int tx = tid % BX, ty = tid / BX;
-    const int i = i0 + tx, j = j0 + ty;
+    // the column's offset in Y, Y_{j-1} and out (the base pointers stay kernel parameters)
+    const long cb = (long)col * ld;
+    const bool hasP = Yprev != nullptr;
     const bool act = (i < n0) && (j < n1);
     const unsigned pij = act ? (unsigned)i + (unsigned)n0 * (unsigned)j : 0u;
     const int2 zero = make_int2(0, 0);
-    // halo duties: nodes tid and tid + NS of the strips (left, right: R x BY each; top,
+    // the column's scale: grid values in units of 2^(EY-26)
+    const unsigned uy = bY[col];
+    const bool nonfinite = ((uy >> 20) & 0x7ffu) == 0x7ffu;
+    const int EY = bound_exponent(uy);
+    const double gs = ldexp(cf.ag, EY - 26);  // alpha g 2^(EY-26)
+    // halo duties: nodes tid and tid + NT of the strips (left, right: R x BY each; top,
     // bottom: BX x R each); hs = shared-memory index (-1: none), hg = offset in the plane
     // (kNoNode: the node lies outside the grid and stays zero)
     constexpr unsigned kNoNode = 0xffffffffu;
@@ -202,7 +133,7 @@ k_stencil_df(const TI *__restrict__ Y, const double *Yprev, double *out,
     unsigned hg[2];
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
-        const int h = tid + v * NS;
+        const int h = tid + v * NT;
         int sx, sy;
         if (h < 2 * R * BY) {
             const int side = h / (R * BY), rr = h % (R * BY);
@@ -234,7 +165,10 @@ k_stencil_df(const TI *__restrict__ Y, const double *Yprev, double *out,
         for (int v = 0; v < 2; ++v)
             if (hs[v] >= 0) s[hs[v]] = hg[v] != kNoNode ? to_grid(Y[cb + hg[v] + pk], EY) : zero;
     }
-    role_barrier();
+    double ucur = act && k0 < k1 ? u[pij + (unsigned)k0 * plane] : 0.0;
+    double pcur = act && hasP && k0 < k1 ? Yprev[cb + pij + (unsigned)k0 * plane] : 0.0;
+    unsigned omax = 0u;
+    __syncthreads();
     // The plane loop is unrolled 13 times, one copy per rotation of the z queue: in the
     // copy of phase PH, logical queue entry t (plane k - R + t) sits in q[(PH + t) % 13], so
     // the queue is never shifted.
@@ -248,33 +182,47 @@ k_stencil_df(const TI *__restrict__ Y, const double *Yprev, double *out,
         const bool more = k + 1 < k1;
         const unsigned pk1 = pk + plane;
         TI g[2] = {0, 0}, gq = 0;
+        double unext = 0.0, pnext = 0.0;
         if (more) {
 #pragma unroll
             for (int v = 0; v < 2; ++v)
                 if (hg[v] != kNoNode) g[v] = Y[cb + hg[v] + pk1];
+            if (act) {
+                unext = u[pij + pk1];
+                if (hasP) pnext = Yprev[cb + pij + pk1];
+            }
         }
         const int kn = k + R + 1;
         if (act && kn < n2) gq = Y[cb + pij + (unsigned)kn * plane];
-        // h^2 D L_h y in units of 2^(EY-26): exact integer sums of d, FP32 sums of r
-        const int2 c = q[(PH + R) % Q];
-        const int2 *row = s + b * (SY * SX) + me;
-        long long A = (long long)cf.W[0] * c.x;
-        float Rs = cf.Wf[0] * __int_as_float(c.y);
+        if (act) {
+            const double yc = as_f64(Y[cb + pij + pk]);  // the point's own value (cached)
+            // h^2 D L_h y in units of 2^(EY-26): exact integer sums of d, FP32 sums of r
+            const int2 c = q[(PH + R) % Q];
+            const int2 *row = s + b * (SY * SX) + me;
+            long long A = (long long)cf.W[0] * c.x;
+            float Rs = cf.Wf[0] * __int_as_float(c.y);
 #pragma unroll
-        for (int r = 1; r <= R; ++r) {
-            const int2 xa = row[r], xb = row[-r], ya = row[r * SX], yb = row[-r * SX];
-            const int2 za = q[(PH + R + r) % Q], zb = q[(PH + R - r) % Q];
-            const int sd = (xa.x + xb.x + ya.x) + (yb.x + za.x + zb.x);
-            const float sr = ((__int_as_float(xa.y) + __int_as_float(xb.y)) +
-                              (__int_as_float(ya.y) + __int_as_float(yb.y))) +
-                             (__int_as_float(za.y) + __int_as_float(zb.y));
-            A += (long long)cf.W[r] * sd;
-            Rs = fmaf(cf.Wf[r], sr, Rs);
+            for (int r = 1; r <= R; ++r) {
+                const int2 xa = row[r], xb = row[-r], ya = row[r * SX], yb = row[-r * SX];
+                const int2 za = q[(PH + R + r) % Q], zb = q[(PH + R - r) % Q];
+                const int sd = (xa.x + xb.x + ya.x) + (yb.x + za.x + zb.x);
+                const float sr = ((__int_as_float(xa.y) + __int_as_float(xb.y)) +
+                                  (__int_as_float(ya.y) + __int_as_float(yb.y))) +
+                                 (__int_as_float(za.y) + __int_as_float(zb.y));
+                A += (long long)cf.W[r] * sd;
+                Rs = fmaf(cf.Wf[r], sr, Rs);
+            }
+            const double T = int51_to_double(A + (long long)__float2int_rn(Rs));
+            double o = fma(gs, T, fma(ucur, yc, hasP ? cf.mbeta * pcur : 0.0));
+            if (nonfinite) o = __longlong_as_double(0x7ff8000000000000ll);
+            omax = max(omax, abs_hi_word(o));
+            out[cb + pij + pk] = o;
         }
-        Ts[b][tid] = A + (long long)__float2int_rn(Rs);
         // plane k - R leaves the queue; its slot takes plane k + R + 1 (logical entry 2R
         // of the next phase), and the next phase's centre is plane k + 1
         q[PH % Q] = (act && kn < n2) ? to_grid(gq, EY) : zero;
+        ucur = unext;
+        pcur = pnext;
         if (more) {
             int2 *nb = s + (b ^ 1) * (SY * SX);
             nb[me] = q[(PH + 1 + R) % Q];
@@ -282,7 +230,7 @@ k_stencil_df(const TI *__restrict__ Y, const double *Yprev, double *out,
             for (int v = 0; v < 2; ++v)
                 if (hs[v] >= 0) nb[hs[v]] = hg[v] != kNoNode ? to_grid(g[v], EY) : zero;
         }
-        role_barrier();
+        __syncthreads();
         ++k;
     };
 #define SPARC_DF_STEP(P)                                                                 \
@@ -294,7 +242,10 @@ k_stencil_df(const TI *__restrict__ Y, const double *Yprev, double *out,
         SPARC_DF_STEP(10) SPARC_DF_STEP(11) SPARC_DF_STEP(12)
     }
 #undef SPARC_DF_STEP
-    // the finish threads take the last plane's sums after the barrier that ended it
+    if (bOut) {
+        omax = __reduce_max_sync(0xffffffffu, omax);
+        if ((tid & 31) == 0 && omax) raise_bound(bOut + col, omax);
+    }
 }
 
 // u = alpha (V - shift): the per-launch potential factor of the FP64 step.
@@ -321,7 +272,7 @@ static cudaError_t stencil_df_launch(const DevHam &H, const TI *Y, const double 
                                      const double *u, double beta, const unsigned *bY,
                                      unsigned *bOut, cudaStream_t st)
 {
-    constexpr int BX = 32, BY = 12;
+    constexpr int BX = 32, BY = 16;
     if (ncols <= 0) return cudaSuccess;
     if (ncols > 65535 || !bY || !u) return cudaErrorInvalidValue;
     FxCoef cf;
@@ -334,10 +285,9 @@ static cudaError_t stencil_df_launch(const DevHam &H, const TI *Y, const double 
     const int gx = (H.n0 + BX - 1) / BX, gy = (H.n1 + BY - 1) / BY;
     int nzc, zchunk;
     stencil_z_split(H.n2, (long)gx * gy, ncols, nzc, zchunk);
-    dim3 grid(gx, gy, ncols * nzc);
-    k_stencil_df<TI, BX, BY><<<grid, BX * BY + kFinish, 0, st>>>(Y, Yprev, out, u, H.n0, H.n1,
-                                                                 H.n2, ld, nzc, zchunk, cf, bY,
-                                                                 bOut);
+    dim3 grid(gx, gy, ncols * nzc), block(BX, BY);
+    k_stencil_df<TI, BX, BY><<<grid, block, 0, st>>>(Y, Yprev, out, u, H.n0, H.n1, H.n2, ld,
+                                                     nzc, zchunk, cf, bY, bOut);
     note_launch();
     return cudaGetLastError();
 }

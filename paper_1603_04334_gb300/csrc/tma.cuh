@@ -56,14 +56,29 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned parity)
     return ok != 0;
 }
 
+// One potentially suspending probe: the thread may wait in the barrier for up to about
+// `hint_ns` nanoseconds and resumes as soon as the phase with the given parity completes.
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity, unsigned hint_ns)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait: false if the phase did not complete within `limit` probes. After the
-// first 64 probes each further probe sleeps ~64 ns, so limit = 2^22 bounds the wait to
-// about a quarter of a second.
+// first 64 plain probes each further probe may suspend the thread for up to ~64 ns (it
+// wakes when the phase completes), so limit = 2^22 bounds the wait to about a quarter of
+// a second.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned limit)
 {
     for (unsigned it = 0; it < limit; ++it) {
-        if (mbar_test(bar, parity)) return true;
-        if (it >= 64) __nanosleep(64);
+        if (it < 64 ? mbar_test(bar, parity) : mbar_try(bar, parity, 64u)) return true;
     }
     return false;
 }
