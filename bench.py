@@ -375,6 +375,14 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_mixed160:
         out["mixed160"] = mixed_vs_fp64(args.seed)
         torch.cuda.empty_cache()
+    if world == 1 and not args.no_batching:
+        from paper_1603_04334_gb300 import batching
+        # 64 uneven clusters in one batched filter against per-cluster launches: the
+        # configured mix (edges 32-96) and a mix of small clusters (edges 32-48) that each
+        # under-fill the GPU
+        out["batching"] = {"config_mix": batching.compare(64, args.seed),
+                           "small_mix": batching.compare(64, args.seed, edges=(32, 40, 48))}
+        torch.cuda.empty_cache()
     if world == 1 and args.serving_requests > 0:
         out["serving"] = serving_study(args.seed, args.serving_requests)
     return out
@@ -721,6 +729,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-mixed160", action="store_true",
                     help="skip the 160^3 mixed-vs-FP64 comparison")
+    ap.add_argument("--no-batching", action="store_true",
+                    help="skip the batched-filter comparison (64 clusters)")
     ap.add_argument("--serving-requests", type=int, default=200,
                     help="requests per arrival rate of the serving study (0: skip it)")
     args = ap.parse_args()

@@ -126,28 +126,26 @@ def draw_clusters(count: int, seed: int, edges=(32, 48, 64, 80, 96), atoms=(2, 6
     return out
 
 
-def main(argv=None):
+def compare(clusters: int = 64, seed: int = 0, degree: int = 16, reps: int = 5,
+            edges=(32, 48, 64, 80, 96)) -> dict:
+    """One batched filter of `clusters` seeded clusters (autotuned launch) against
+    sparc_cheb_filter on each cluster in turn: best of `reps` CUDA-event timings of each
+    after a warm-up (the warm-up captures the batch's graph)."""
     import torch
-    ap = argparse.ArgumentParser(description=__doc__)
-    ap.add_argument("--clusters", type=int, default=64)
-    ap.add_argument("--degree", type=int, default=16)
-    ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--reps", type=int, default=5)
-    a = ap.parse_args(argv)
     h = 0.3
-    spec = draw_clusters(a.clusters, a.seed)
+    spec = draw_clusters(clusters, seed, edges=edges)
     ctxs, X, W, bounds = [], [], [], []
     for i, (n, R, Z, gamma, ns) in enumerate(spec):
         ctx = sparc.Context(n, h, R, Z, gamma)
         ctxs.append(ctx)
         bounds.append(ctx.first_bounds(10, i))
-        x0 = torch.from_numpy(synth.initial_block(a.seed + i, n ** 3, ns)).to("cuda",
-                                                                           torch.float32)
+        x0 = torch.from_numpy(synth.initial_block(seed + i, n ** 3, ns)).to("cuda",
+                                                                         torch.float32)
         X.append(x0)
         W.append(torch.empty_like(x0))
     X0 = [x.clone() for x in X]
     batch = Batch(ctxs)
-    variant, tune_ms = batch.tune(X, W, a.degree, bounds)
+    variant, tune_ms = batch.tune(X, W, degree, bounds)
     st = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -157,7 +155,7 @@ def main(argv=None):
         fn()  # warm-up (graph capture for the batch)
         torch.cuda.synchronize()
         best = None
-        for _ in range(a.reps):
+        for _ in range(reps):
             for x, x0 in zip(X, X0):
                 x.copy_(x0)
             torch.cuda.synchronize()
@@ -169,21 +167,34 @@ def main(argv=None):
             best = t if best is None else min(best, t)
         return best
 
-    t_batch = timed(lambda: batch.filter(X, W, a.degree, bounds))
-    t_each = timed(lambda: [c.cheb_filter(x, w, a.degree, *b)
+    t_batch = timed(lambda: batch.filter(X, W, degree, bounds))
+    t_each = timed(lambda: [c.cheb_filter(x, w, degree, *b)
                             for c, x, w, b in zip(ctxs, X, W, bounds)])
-    ptorb = sum(a.degree * n ** 3 * ns for (n, _, _, _, ns) in spec)
-    print(json.dumps({
-        "metric": "batched Chebyshev filter, many uneven clusters",
-        "clusters": a.clusters, "degree": a.degree, "variant": variant,
-        "batched_ms": t_batch, "per_cluster_ms": t_each, "speedup": t_each / t_batch,
-        "batched_ptorb_per_s": ptorb / (t_batch / 1e3),
-        "per_cluster_ptorb_per_s": ptorb / (t_each / 1e3),
-        "workload": "edge in {32,48,64,80,96}, h=0.3, atoms 2-60, Ns 16-160, FP32, degree 16",
-        "tune_ms": tune_ms}), flush=True)
+    ptorb = sum(degree * n ** 3 * ns for (n, _, _, _, ns) in spec)
     batch.close()
     for c in ctxs:
         c.close()
+    return {"clusters": clusters, "degree": degree, "variant": variant,
+            "batched_ms": t_batch, "per_cluster_ms": t_each, "speedup": t_each / t_batch,
+            "batched_ptorb_per_s": ptorb / (t_batch / 1e3),
+            "per_cluster_ptorb_per_s": ptorb / (t_each / 1e3),
+            "workload": f"edge in {{{','.join(str(e) for e in edges)}}}, h=0.3, atoms 2-60, "
+                        f"Ns 16-160, FP32, degree {degree}",
+            "tune_ms": tune_ms}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--clusters", type=int, default=64)
+    ap.add_argument("--degree", type=int, default=16)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--edges", default="32,48,64,80,96")
+    a = ap.parse_args(argv)
+    out = compare(a.clusters, a.seed, a.degree, a.reps,
+                  tuple(int(e) for e in a.edges.split(",")))
+    print(json.dumps(dict(out, metric="batched Chebyshev filter, many uneven clusters")),
+          flush=True)
 
 
 if __name__ == "__main__":

@@ -94,6 +94,7 @@ template <class C> struct TcDims {
     // ring, then the low parts of the epilogue's running pair sums ([warp][column][lane])
     static constexpr unsigned kLowBytes = kEpiWarps * kEpiCols * 32 * 4;
     static constexpr unsigned kSmemBytes = C::kStages * kStageBytes + kLowBytes + 1024;
+    static_assert(kSmemBytes <= 227 * 1024, "shared memory of one CTA");
     static_assert(C::kClasses * C::kN <= kTmemCols, "class accumulators exceed tensor memory");
     static_assert(C::kBits <= C::kBase * C::kDigits - 1,
                   "top digit must stay within [0, 2^(kBase - 1)]");

@@ -14,6 +14,7 @@
 #include "sparc_server.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -29,6 +30,7 @@ namespace {
 
 constexpr int kMaxPassOver = 8;
 constexpr int kLanczosSteps = 10;
+constexpr int kRrThreads = 8;  // host threads running the batched server's per-request steps
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
 {
@@ -236,9 +238,12 @@ void worker(sparc_server *S)
 // requests join as the budget and the `slots` limit allow; the batch is rebuilt whenever
 // the set of batched requests changes. The batch keeps its default kernel variant (no
 // autotuning), so a request's arithmetic does not depend on which others share its
-// launches.
+// launches. Each request has its own stream: once the batched filter is done, the
+// requests' Rayleigh-Ritz steps (and the filters that were not batched) run side by side
+// on a pool of host threads, one request per thread at a time.
 struct Active {
     Request *r = nullptr;
+    cudaStream_t st = nullptr;
     sparc_ctx *ctx = nullptr;
     void *X = nullptr, *W = nullptr;
     long nd = 0;
@@ -249,12 +254,17 @@ struct Active {
     sparc_status status = SPARC_OK;
 };
 
-// Context, blocks, start block and first-iteration bounds of an admitted request.
-sparc_status start_active(Active &a, cudaStream_t st)
+// Stream, context, blocks, start block and first-iteration bounds of an admitted request.
+sparc_status start_active(Active &a)
 {
     const sparc_request &q = a.r->spec;
     a.nd = (long)q.n[0] * q.n[1] * q.n[2];
     const size_t es = q.dtype == SPARC_F32 ? 4 : 8;
+    if (cudaStreamCreateWithFlags(&a.st, cudaStreamNonBlocking) != cudaSuccess) {
+        a.st = nullptr;
+        return SPARC_ERR_CUDA;
+    }
+    cudaStream_t st = a.st;
     sparc_grid g{{q.n[0], q.n[1], q.n[2]}, q.h, kRadius};
     sparc_atoms at{q.natoms, a.r->R.data(), a.r->Z.data(), a.r->gamma.data(), 0.8, 3.0, 1.0};
     sparc_status s = sparc_create(&g, nullptr, &at, st, &a.ctx);
@@ -286,8 +296,27 @@ void release_active(Active &a)
     if (a.X) cudaFree(a.X);
     if (a.W) cudaFree(a.W);
     if (a.ctx) sparc_destroy(a.ctx);
+    if (a.st) cudaStreamDestroy(a.st);
     a.X = a.W = nullptr;
     a.ctx = nullptr;
+    a.st = nullptr;
+}
+
+// Runs task(i) for i < n on `threads` host threads (the calling thread included), each
+// with `device` current; returns when all are done.
+template <typename F>
+void run_parallel(int n, int threads, int device, F task)
+{
+    std::atomic<int> next{0};
+    auto body = [&](bool set_device) {
+        if (set_device) cudaSetDevice(device);
+        for (int i; (i = next.fetch_add(1)) < n;) task(i);
+    };
+    const int extra = std::min(threads, n) - 1;
+    std::vector<std::thread> pool;
+    for (int t = 0; t < extra; ++t) pool.emplace_back(body, true);
+    body(false);
+    for (std::thread &t : pool) t.join();
 }
 
 // Rayleigh-Ritz of one request after its filter; bounds for the next round as
@@ -344,7 +373,7 @@ void scheduler(sparc_server *S)
             auto a = std::make_unique<Active>();
             a->r = r;
             a->info = r->info;
-            a->status = gpu_ok ? start_active(*a, st) : SPARC_ERR_CUDA;
+            a->status = gpu_ok ? start_active(*a) : SPARC_ERR_CUDA;
             if (a->status != SPARC_OK) a->done = true;
             act.push_back(std::move(a));
         }
@@ -379,28 +408,33 @@ void scheduler(sparc_server *S)
                 ld.push_back(a->nd);
                 bounds.insert(bounds.end(), a->b, a->b + 3);
             }
-            const sparc_status s =
+            sparc_status s =
                 batch ? sparc_batch_filter(batch, X.data(), W.data(), nc.data(), ld.data(), degree,
                                            bounds.data())
                       : SPARC_ERR_OOM;
+            // the batch ends on the scheduler's stream; the requests' own streams take over
+            if (s == SPARC_OK && cudaStreamSynchronize(st) != cudaSuccess) s = SPARC_ERR_CUDA;
             if (s != SPARC_OK)
                 for (Active *a : bat) a->status = s, a->done = true;
         }
-        for (auto &a : act) {
-            if (a->done) continue;
-            const bool batched = std::find(bat.begin(), bat.end(), a.get()) != bat.end();
+        std::vector<Active *> todo;
+        for (auto &a : act)
+            if (!a->done) todo.push_back(a.get());
+        run_parallel((int)todo.size(), kRrThreads, S->device, [&](int i) {
+            Active &a = *todo[i];
+            const bool batched = std::find(bat.begin(), bat.end(), &a) != bat.end();
             if (!batched) {
-                const sparc_request &q = a->r->spec;
-                const sparc_status s = sparc_cheb_filter(a->ctx, q.dtype, a->X, a->W, q.ns, a->nd,
-                                                         q.degree, a->b[0], a->b[1], a->b[2]);
+                const sparc_request &q = a.r->spec;
+                const sparc_status s = sparc_cheb_filter(a.ctx, q.dtype, a.X, a.W, q.ns, a.nd,
+                                                         q.degree, a.b[0], a.b[1], a.b[2]);
                 if (s != SPARC_OK) {
-                    a->status = s;
-                    a->done = true;
-                    continue;
+                    a.status = s;
+                    a.done = true;
+                    return;
                 }
             }
-            rr_active(*a);
-        }
+            rr_active(a);
+        });
         // finished requests leave; the batch over them goes first (it uses their contexts)
         bool left = false;
         for (auto &a : act) left = left || a->done;

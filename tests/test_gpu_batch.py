@@ -102,3 +102,36 @@ def test_every_variant_agrees_and_tuner_picks_one(shapes):
     batch.close()
     for _, c, _ in cl:
         c.close()
+
+
+def test_batched_filter_64_clusters_of_the_configured_mix():
+    # 64 clusters drawn as the batching workload draws them (edge in {32, ..., 96},
+    # h = 0.3, 2-60 atoms, Ns 16-160, degree 16): the batched filter of all of them against
+    # sparc_cheb_filter on each cluster, and against the oracle on two columns of the four
+    # smallest clusters
+    spec = batching.draw_clusters(64, 0)
+    m = 16
+    ctxs, X0, B = [], [], []
+    for i, (n, R, Z, gamma, ns) in enumerate(spec):
+        ctx = sparc.Context(n, 0.3, R, Z, gamma)
+        ctxs.append(ctx)
+        B.append(ctx.first_bounds(10, i))
+        X0.append(torch.from_numpy(synth.initial_block(i, n ** 3, ns)).to("cuda", torch.float32))
+    Xb = [x.clone() for x in X0]
+    batch = batching.Batch(ctxs)
+    batch.filter(Xb, [torch.empty_like(x) for x in Xb], m, B)
+    for ctx, x0, xb, b in zip(ctxs, X0, Xb, B):
+        xr = x0.clone()
+        ctx.cheb_filter(xr, torch.empty_like(xr), m, *b)
+        assert _nrm(xb.double().cpu().numpy(), xr.double().cpu().numpy()) <= 2e-6
+    small = sorted(range(64), key=lambda i: (spec[i][0], spec[i][4]))[:4]
+    for i in small:
+        n, R, Z, gamma, ns = spec[i]
+        cl = synth.Cluster(n=n, h=0.3, R=R, Z=Z, gamma=gamma)
+        H = oracle.Hamiltonian.from_cluster(cl)
+        cols = [0, ns - 1]
+        ref = H.cheb_filter(X0[i][cols].double().cpu().numpy(), m, *B[i])
+        assert _nrm(Xb[i][cols].double().cpu().numpy(), ref) <= 1e-5
+    batch.close()
+    for c in ctxs:
+        c.close()
