@@ -6,6 +6,15 @@
 // (three digits; sparc_gram_tc and the mixed form's FP32 rotation). The description below
 // is of the 23-bit form; the 47-bit form differs as stated at struct Tc47.
 //
+// The scheme is a fixed-point form of the error-free splitting of a matrix product into
+// slices whose products the hardware forms exactly (the Ozaki scheme: K. Ozaki, T. Ogita,
+// S. Oishi and S. M. Rump, "Error-free transformations of matrix multiplication by using
+// fast routines of matrix multiplication and its applicability", Numer. Algorithms 59,
+// 2012), with per-chunk scaling so that the slices are small integers and the tensor
+// core's FP32 accumulator sums them exactly, in the manner of the integer-unit emulations of
+// FP64 products (H. Ootomo, K. Ozaki and R. Yokota, "DGEMM on integer matrix
+// multiplication unit", IJHPCA 2024).
+//
 // Representation. The rows are cut into chunks of kChunk = 256. For chunk c and column j
 // of an operand, e = e(c, j) is the smallest integer with max_{k in c} |x_kj| < 2^e, and
 // each entry is rounded to N = round(|x| 2^(23 - e)), an integer in [0, 2^23], written in
