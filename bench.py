@@ -494,8 +494,8 @@ def serving_study(seed: int, requests: int, rates=(400.0, 20.0), below=(0.5,),
     runs the configured rates (20 and 400 req/s) first; they saturate it and measure its
     capacity; then rates below saturation (the given fractions of that capacity). Beside
     them: the worker server (`workers` threads, one stream each, a whole solve per request)
-    at 400 req/s, and the first `serial_sample` requests solved one at a time in FP64 (one
-    worker): their service times and the serial throughput."""
+    at 400 req/s, and `serial_sample` requests spread evenly over the list solved one at a
+    time in FP64 (one worker): their service times and the serial throughput."""
     from paper_1603_04334_gb300 import serve
 
     specs = serve.draw_requests(requests, seed)
@@ -522,8 +522,9 @@ def serving_study(seed: int, requests: int, rates=(400.0, 20.0), below=(0.5,),
     wk = point(max(rates), False, workers)
     base = []
     srv = serve.Server(budget, 1)
+    pick = specs[::max(1, len(specs) // serial_sample)][:serial_sample]
     try:
-        for s in specs[:serial_sample]:
+        for s in pick:
             f64 = serve.Spec(s.n, s.h, s.R, s.Z, s.gamma, s.ns, s.degree, s.max_iters, s.tol,
                              s.seed, "f64")
             r = srv.wait(srv.submit(f64))
@@ -543,8 +544,9 @@ def serving_study(seed: int, requests: int, rates=(400.0, 20.0), below=(0.5,),
                             "throughput_req_per_s": len(base) / float(base.sum()),
                             "service_p50_s": float(np.percentile(base, 50)),
                             "service_p99_s": float(np.percentile(base, 99)),
-                            "sample": f"the first {len(base)} requests of the same list, one "
-                                      f"at a time in FP64 on one worker"}}
+                            "sample": f"{len(base)} requests spread evenly over the same "
+                                      f"list (every {max(1, len(specs) // serial_sample)}th), "
+                                      f"one at a time in FP64 on one worker"}}
 
 
 def after_rotation(ctx, X, ritz, w, stream, fp64_peak_tflops: float, reps: int = 10) -> dict:
