@@ -655,11 +655,21 @@ TcPlan tc_plan(long nd, int ns, bool sym)
     p.nchunk = (nd + C::kChunk - 1) / C::kChunk;
     p.nstep = p.nchunk * TcDims<C>::kStepsPerChunk;
     p.ntiles = sym ? p.nblk * (p.nblk + 1) / 2 : p.nblk * p.nblk;
+    // K splits: one CTA per SM (the ring and the class accumulators fill an SM), so the
+    // kernel takes (waves of 152 CTAs) x (chunks per split). Pick the split count with the
+    // fewest chunk-times, counting about two chunks of fixed cost per CTA (set-up and the
+    // partial tile's store), and keep the partial tiles within 256 MB.
     const long ctas = (long)p.ntiles * TcDims<C>::kHalves;
-    long s = (152 + ctas - 1) / ctas;
-    if (s > p.nchunk) s = p.nchunk;
-    if (s < 1) s = 1;
-    p.nsplit = (int)s;
+    const long smax_mem = ((long)256 << 20) / ((long)p.ntiles * kTile * kTile * 8);
+    long smax = p.nchunk < smax_mem ? p.nchunk : smax_mem;
+    if (smax > 1024) smax = 1024;
+    long best_s = 1, best = -1;
+    for (long s = 1; s <= smax; ++s) {
+        const long waves = (ctas * s + 151) / 152;
+        const long cost = waves * ((p.nchunk + s - 1) / s + 2);
+        if (best < 0 || cost < best) best = cost, best_s = s;
+    }
+    p.nsplit = (int)best_s;
     p.digits_bytes = (size_t)C::kDigits * p.ns_pad * p.nstep * C::kStep * 2;
     p.exps_bytes = (size_t)p.nchunk * p.ns_pad * sizeof(int);
     p.part_bytes = (size_t)p.nsplit * p.ntiles * kTile * kTile * sizeof(double);

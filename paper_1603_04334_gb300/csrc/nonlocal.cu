@@ -101,6 +101,9 @@ __device__ __forceinline__ void project_block(const T *__restrict__ Y, long ld, 
     __syncthreads();
 }
 
+// Grid: x = atom (dispatched first: the CTAs resident at one time read the supports of
+// many atoms for the same columns, so the nodes that several supports share are read from
+// DRAM about once), y = column block.
 template <typename T, typename TC, int CB, int NT, bool ILV>
 __global__ void __launch_bounds__(NT)
 k_project(const T *__restrict__ Y, long ld, int ncols, const int *__restrict__ atom_ptr,
@@ -164,6 +167,7 @@ cudaError_t project_f32in_f64(const DevHam &H, const float *Y, int ncols, long l
 // Projection with compensated products; each thread's partial sums over its share of the
 // support are combined across the CTA with pair additions (TwoSum). The result is written
 // as FP32 pairs, scaled by `alpha` (the filter step's factor), for the pair scatter.
+// Grid as k_project: x = atom, y = column block.
 template <int CB, int NT>
 __global__ void __launch_bounds__(NT, 4)
 k_project_df(const double *__restrict__ Y, long ld, int ncols, const int *__restrict__ atom_ptr,
@@ -248,10 +252,10 @@ cudaError_t project_f64_df(const DevHam &H, const double *Y, int ncols, long ld,
 
 // Native FP64 scatter, used where H is applied in FP64 to an FP32 block (the H Y_f of the
 // mixed-precision Rayleigh-Ritz step). Same grid as the FP32 scatter below: one covered
-// node per thread, kScatCols columns per CTA, covered nodes along the grid's x dimension.
-constexpr int kScatRegs = 4;
+// node per thread, kScatCols columns per CTA, column groups along the grid's x dimension.
 constexpr int kScatNodes = 256;
 constexpr int kScatCols = 16;
+constexpr int kScatF32Cols = 8;  // columns per thread of the FP32 scatter
 
 __global__ void __launch_bounds__(kScatNodes)
 k_scatter_f64(double *out, long ld, int ncols, long nuniq, const int *__restrict__ uniq_node,
@@ -259,113 +263,94 @@ k_scatter_f64(double *out, long ld, int ncols, long nuniq, const int *__restrict
               const int *__restrict__ ent_atom, const double *__restrict__ gchi,
               const double *__restrict__ C, double alpha)
 {
-    const long u = (long)blockIdx.x * kScatNodes + threadIdx.x;
-    if (u >= nuniq) return;
-    const int c0 = blockIdx.y * kScatCols, c1 = min(ncols, c0 + kScatCols);
-    const long node = uniq_node[u];
-    const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
+    const int c0 = blockIdx.x * kScatCols, c1 = min(ncols, c0 + kScatCols);
+    for (long ub = blockIdx.y; ub * kScatNodes < nuniq; ub += gridDim.y) {
+        const long u = ub * kScatNodes + threadIdx.x;
+        if (u >= nuniq) continue;
+        const long node = uniq_node[u];
+        const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
 #pragma unroll 2
-    for (int c = c0; c < c1; ++c) {
-        double v = 0.0;
-        for (int q = q0; q < q1; ++q) {
-            const int e = ent_list[q];
-            const int J = ent_atom[e];
+        for (int c = c0; c < c1; ++c) {
+            double v = 0.0;
+            for (int q = q0; q < q1; ++q) {
+                const int e = ent_list[q];
+                const int J = ent_atom[e];
 #pragma unroll
-            for (int l = 0; l < 4; ++l)
-                v += gchi[4 * (long)e + l] * C[(long)(J * 4 + l) * ncols + c];
+                for (int l = 0; l < 4; ++l)
+                    v += gchi[4 * (long)e + l] * C[(long)(J * 4 + l) * ncols + c];
+            }
+            double *o = out + node + (long)c * ld;
+            *o = *o + alpha * v;
         }
-        double *o = out + node + (long)c * ld;
-        *o = *o + alpha * v;
     }
 }
 
 // FP32 blocks: Cs holds alpha chi^T Y as one float4 per (atom, column), Cs4[J * ncols + c],
 // and g4[q] the four h^3 gamma chi values of entry q. A thread owns one covered node and a
-// group of kScatCols columns; the grid's x dimension (dispatched first) runs over the
-// covered nodes, so the CTAs resident at one time sweep consecutive nodes of the same
-// columns (DRAM page locality for the read-modify-write of the output). A node's entries
-// (the atoms whose support holds it, ascending) are loaded into registers once; each
-// column then costs one 16-byte load per entry (L1/L2-resident) and one read-modify-write.
-// Nodes covered by more than kScatRegs atoms take the generic loop.
-
-// The sums of the thread's kScatCols columns are formed first (coefficient loads hit L1 /
-// L2), then all output loads are issued before any store, so a thread keeps kScatCols
-// independent DRAM reads in flight (the kernel is bound by that latency, not by bytes).
-template <int N>
-__device__ __forceinline__ void scatter_node_f32(float *o, long ld, int c0, int nc, int q0,
-                                                 int ncols, const int *__restrict__ nl_atom,
-                                                 const float4 *__restrict__ g4,
-                                                 const float4 *__restrict__ Cs4)
-{
-    float4 gq[N];
-    const float4 *cq[N];
-#pragma unroll
-    for (int t = 0; t < N; ++t) {
-        gq[t] = g4[q0 + t];
-        cq[t] = Cs4 + (long)nl_atom[q0 + t] * ncols + c0;
-    }
-    float v[kScatCols], x[kScatCols];
-#pragma unroll
-    for (int c = 0; c < kScatCols; ++c) {
-        v[c] = 0.0f;
-        if (c < nc) {
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                const float4 cc = cq[t][c];
-                v[c] += gq[t].x * cc.x;
-                v[c] += gq[t].y * cc.y;
-                v[c] += gq[t].z * cc.z;
-                v[c] += gq[t].w * cc.w;
-            }
-        }
-    }
-    float *oc = o + (long)c0 * ld;
-#pragma unroll
-    for (int c = 0; c < kScatCols; ++c) x[c] = c < nc ? oc[(long)c * ld] : 0.0f;
-#pragma unroll
-    for (int c = 0; c < kScatCols; ++c)
-        if (c < nc) oc[(long)c * ld] = x[c] + v[c];
-}
-
-// Covered node u (entries q0 .. q1-1), columns c0 .. c0+nc-1.
+// group of columns; the grid's x dimension (dispatched first) runs over the column groups,
+// so the CTAs resident at one time share their covered nodes and read the node's entry
+// tables from L1/L2 (with the nodes outermost, every column group read the tables again
+// from DRAM: about as many bytes as the output itself at 1024 columns). The thread first
+// issues its kScatCols output reads (independent DRAM loads in flight), then walks its
+// node's entries (the atoms whose support holds it, ascending): per entry one load of the
+// four coefficients and, per column, one 16-byte load of Cs (L1/L2-resident). The entry
+// loop runs to the largest entry count of the warp with the shorter lanes predicated off,
+// so a warp whose nodes are covered by different numbers of atoms stays on one path.
+// Per column the entries are summed in ascending order.
+template <int NC>
 __device__ __forceinline__ void scatter_f32_node(float *out, long ld, int ncols, long node, int q0,
-                                                 int q1, int c0, int nc,
+                                                 int q1, int c0, int nc, bool live,
                                                  const int *__restrict__ nl_atom,
                                                  const float4 *__restrict__ g4,
                                                  const float4 *__restrict__ Cs4)
 {
-    float *o = out + node;
-    switch (q1 - q0) {
-    case 1: scatter_node_f32<1>(o, ld, c0, nc, q0, ncols, nl_atom, g4, Cs4); return;
-    case 2: scatter_node_f32<2>(o, ld, c0, nc, q0, ncols, nl_atom, g4, Cs4); return;
-    case 3: scatter_node_f32<3>(o, ld, c0, nc, q0, ncols, nl_atom, g4, Cs4); return;
-    case 4: scatter_node_f32<kScatRegs>(o, ld, c0, nc, q0, ncols, nl_atom, g4, Cs4); return;
-    default: break;
+    float *oc = out + node + (long)c0 * ld;
+    float x[NC], v[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        x[c] = (live && c < nc) ? oc[(long)c * ld] : 0.0f;
+        v[c] = 0.0f;
     }
-    for (int c = c0; c < c0 + nc; ++c) {
-        float v = 0.0f;
-        for (int q = q0; q < q1; ++q) {
-            const float4 g = g4[q], cc = Cs4[(long)nl_atom[q] * ncols + c];
-            v += g.x * cc.x;
-            v += g.y * cc.y;
-            v += g.z * cc.z;
-            v += g.w * cc.w;
+    const int n = live ? q1 - q0 : 0;
+    const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
+    for (int t = 0; t < nmax; ++t) {
+        if (t < n) {
+            const float4 g = g4[q0 + t];
+            const float4 *cq = Cs4 + (long)nl_atom[q0 + t] * ncols + c0;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                if (c < nc) {
+                    const float4 cc = cq[c];
+                    v[c] += g.x * cc.x;
+                    v[c] += g.y * cc.y;
+                    v[c] += g.z * cc.z;
+                    v[c] += g.w * cc.w;
+                }
+            }
         }
-        float *oc = o + (long)c * ld;
-        *oc = *oc + v;
+    }
+    if (live) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            if (c < nc) oc[(long)c * ld] = x[c] + v[c];
     }
 }
 
+// One covered node per thread, NC columns; every lane of a warp reaches the entry loop's
+// warp-wide maximum (lanes past nuniq take part with no entries).
+template <int NC>
 __global__ void __launch_bounds__(kScatNodes)
 k_scatter_f32(float *out, long ld, int ncols, long nuniq, const int *__restrict__ uniq_node,
               const int *__restrict__ uniq_ptr, const int *__restrict__ nl_atom,
               const float4 *__restrict__ g4, const float4 *__restrict__ Cs4)
 {
-    const long u = (long)blockIdx.x * kScatNodes + threadIdx.x;
-    if (u >= nuniq) return;
-    const int c0 = blockIdx.y * kScatCols, nc = min(ncols - c0, kScatCols);
-    scatter_f32_node(out, ld, ncols, uniq_node[u], uniq_ptr[u], uniq_ptr[u + 1], c0, nc, nl_atom,
-                     g4, Cs4);
+    const int c0 = blockIdx.x * NC, nc = min(ncols - c0, NC);
+    for (long ub = blockIdx.y; ub * kScatNodes < nuniq; ub += gridDim.y) {
+        const long u = ub * kScatNodes + threadIdx.x;
+        const bool live = u < nuniq;
+        scatter_f32_node<NC>(out, ld, ncols, live ? uniq_node[u] : 0, live ? uniq_ptr[u] : 0,
+                             live ? uniq_ptr[u + 1] : 0, c0, nc, live, nl_atom, g4, Cs4);
+    }
 }
 
 // Work-list form for a batch of clusters (items: cluster, node chunk, first column).
@@ -376,13 +361,12 @@ k_batch_scatter(const BatchItem *__restrict__ items, int nitems, const BatchNonl
         const BatchItem w = items[it];
         const BatchNonlocal &P = cs[w.cluster];
         const long u = (long)w.a * kBatchNodes + threadIdx.x;
-        if (u < P.nuniq) {
-            const int nc = min(P.ncols - w.col, kScatCols);
-            scatter_f32_node(P.out, P.ld, P.ncols, P.uniq_node[u], P.uniq_ptr[u],
-                             P.uniq_ptr[u + 1], w.col, nc, P.nl_atom,
-                             reinterpret_cast<const float4 *>(P.nl_gf),
-                             reinterpret_cast<const float4 *>(P.C));
-        }
+        const bool live = u < P.nuniq;
+        const int nc = min(P.ncols - w.col, kBatchCols);
+        scatter_f32_node<kBatchCols>(P.out, P.ld, P.ncols, live ? P.uniq_node[u] : 0,
+                         live ? P.uniq_ptr[u] : 0, live ? P.uniq_ptr[u + 1] : 0, w.col, nc, live,
+                         P.nl_atom, reinterpret_cast<const float4 *>(P.nl_gf),
+                         reinterpret_cast<const float4 *>(P.C));
     }
 }
 
@@ -399,10 +383,10 @@ cudaError_t scatter_f32(const DevHam &H, const float *Cs, float *out, int ncols,
                         cudaStream_t st)
 {
     if (H.natoms == 0 || H.nuniq == 0 || ncols <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((H.nuniq + kScatNodes - 1) / kScatNodes),
-              (unsigned)((ncols + kScatCols - 1) / kScatCols));
-    if (grid.y > 65535) return cudaErrorInvalidValue;
-    k_scatter_f32<<<grid, kScatNodes, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node, H.uniq_ptr,
+    constexpr int NC = kScatF32Cols;
+    const long nb = (H.nuniq + kScatNodes - 1) / kScatNodes;
+    dim3 grid((unsigned)((ncols + NC - 1) / NC), (unsigned)(nb < 65535 ? nb : 65535));
+    k_scatter_f32<NC><<<grid, kScatNodes, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node, H.uniq_ptr,
                                                H.nl_atom, reinterpret_cast<const float4 *>(H.nl_gf),
                                                reinterpret_cast<const float4 *>(Cs));
     note_launch();
@@ -413,9 +397,9 @@ cudaError_t scatter_f64(const DevHam &H, const double *C, double *out, int ncols
                         double alpha, cudaStream_t st)
 {
     if (H.natoms == 0 || H.nuniq == 0 || ncols <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((H.nuniq + kScatNodes - 1) / kScatNodes),
-              (unsigned)((ncols + kScatCols - 1) / kScatCols));
-    if (grid.y > 65535) return cudaErrorInvalidValue;
+    const long nb = (H.nuniq + kScatNodes - 1) / kScatNodes;
+    dim3 grid((unsigned)((ncols + kScatCols - 1) / kScatCols),
+              (unsigned)(nb < 65535 ? nb : 65535));
     k_scatter_f64<<<grid, kScatNodes, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node,
                                                H.uniq_ptr, H.ent_list, H.ent_atom, H.gchi, C,
                                                alpha);
@@ -426,10 +410,11 @@ cudaError_t scatter_f64(const DevHam &H, const double *C, double *out, int ncols
 // Nonlocal scatter for FP64 blocks in pair arithmetic: out(p, c) += sum_{q at p} sum_l
 // g(q, l) Cs(atom(q), l, c), Cs = alpha chi^T Y as pairs (k_project_df). A thread owns one
 // covered node and a group of kScatDfCols columns; the grid's x dimension (dispatched first)
-// runs over the covered nodes, so the CTAs resident at one time sweep consecutive nodes of
-// the same columns (coalesced, DRAM-page-local read-modify-write of the output; the node's
-// entries stay in L1). The pair sum is added to the FP64 output with one FP64 add. With
-// bOut, the column bounds of the output are raised to cover the updated values.
+// runs over the column groups, so the CTAs resident at one time share their covered nodes
+// (the node's entry tables are read from L1/L2, not once per column group from DRAM), and
+// y over blocks of covered nodes (strided when there are more than the grid holds). The pair
+// sum is added to the FP64 output with one FP64 add. With bOut, the column bounds of the
+// output are raised to cover the updated values.
 namespace {
 constexpr int kScatDfNodes = 256;
 constexpr int kScatDfCols = 4;
@@ -440,17 +425,21 @@ k_scatter_df(double *out, long ld, int ncols, long nuniq, const int *__restrict_
              const int *__restrict__ uniq_ptr, const int *__restrict__ nl_atom,
              const float2 *__restrict__ g, const float2 *__restrict__ Cs, unsigned *bOut)
 {
-    const long u = (long)blockIdx.x * kScatDfNodes + threadIdx.x;
-    const bool live = u < nuniq;  // no early return: the warp reduces the bounds below
-    const int c0 = blockIdx.y * kScatDfCols, c1 = min(ncols, c0 + kScatDfCols);
-    double o[kScatDfCols];
-    if (live) {
+    const int c0 = blockIdx.x * kScatDfCols, c1 = min(ncols, c0 + kScatDfCols);
+    unsigned om[kScatDfCols];
+#pragma unroll
+    for (int k = 0; k < kScatDfCols; ++k) om[k] = 0u;
+    // the block loop is uniform over the CTA: every lane reaches the bound reduction below
+    for (long ub = blockIdx.y; ub * kScatDfNodes < nuniq; ub += gridDim.y) {
+        const long u = ub * kScatDfNodes + threadIdx.x;
+        if (u >= nuniq) continue;
         const long node = uniq_node[u];
         const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
         // the output reads go first (kScatDfCols DRAM reads in flight while the sums are
         // formed); each entry's atom and coefficients are loaded once for all columns, and
-        // per column the entries are summed in ascending order as before
+        // per column the entries are summed in ascending order
         double *op = out + node + (long)c0 * ld;
+        double o[kScatDfCols];
 #pragma unroll
         for (int k = 0; k < kScatDfCols; ++k) o[k] = c0 + k < c1 ? op[(long)k * ld] : 0.0;
         float vh[kScatDfCols], vl[kScatDfCols];
@@ -469,16 +458,16 @@ k_scatter_df(double *out, long ld, int ncols, long nuniq, const int *__restrict_
 #pragma unroll
         for (int k = 0; k < kScatDfCols; ++k) {
             o[k] += pair_to_double(vh[k], vl[k]);
-            if (c0 + k < c1) op[(long)k * ld] = o[k];
+            if (c0 + k < c1) {
+                op[(long)k * ld] = o[k];
+                om[k] = max(om[k], abs_hi_word(o[k]));
+            }
         }
-    } else {
-#pragma unroll
-        for (int k = 0; k < kScatDfCols; ++k) o[k] = 0.0;
     }
     if (bOut) {
 #pragma unroll
         for (int k = 0; k < kScatDfCols; ++k) {
-            const unsigned m = __reduce_max_sync(0xffffffffu, abs_hi_word(o[k]));
+            const unsigned m = __reduce_max_sync(0xffffffffu, om[k]);
             if ((threadIdx.x & 31) == 0 && m && c0 + k < c1) raise_bound(bOut + c0 + k, m);
         }
     }
@@ -488,9 +477,9 @@ cudaError_t scatter_f64_df(const DevHam &H, const float2 *Cs, double *out, int n
                            unsigned *bOut, cudaStream_t st)
 {
     if (H.natoms == 0 || H.nuniq == 0 || ncols <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((H.nuniq + kScatDfNodes - 1) / kScatDfNodes),
-              (unsigned)((ncols + kScatDfCols - 1) / kScatDfCols));
-    if (grid.y > 65535) return cudaErrorInvalidValue;
+    const long nb = (H.nuniq + kScatDfNodes - 1) / kScatDfNodes;
+    dim3 grid((unsigned)((ncols + kScatDfCols - 1) / kScatDfCols),
+              (unsigned)(nb < 65535 ? nb : 65535));
     k_scatter_df<<<grid, kScatDfNodes, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node, H.uniq_ptr,
                                               H.nl_atom, H.nl_gdf, Cs, bOut);
     note_launch();
