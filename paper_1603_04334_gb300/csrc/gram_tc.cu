@@ -26,8 +26,8 @@
 // Exact accumulation. A product of two digits is an integer below 2^14 in magnitude,
 // exact in the tensor core's FP32 accumulator. The digit pairs (s, t) are grouped by
 // class w = s + t (0-based digits), whose weight is 2^(-8 w) relative to class 0; classes
-// 0, 1, 2 are kept (6 MMAs per 16 rows, one tensor-memory accumulator per class) and
-// classes 3, 4 (products below 2^-22 of the leading term) are dropped. Per chunk a class
+// 0, 1, 2 are kept (6 digit products per 16 rows, one tensor-memory accumulator per class)
+// and classes 3, 4 (products below 2^-22 of the leading term) are dropped. Per chunk a class
 // accumulator holds at most 3 x 2^14 x 256 < 2^24 in magnitude, so its FP32 sums are
 // exact integers. After each chunk the epilogue warps read the three accumulators from
 // tensor memory, combine them exactly into an FP32 pair (TwoSum), scale the pair by the
@@ -40,9 +40,11 @@
 // as 8 KB blobs, one per (128-column block, 32-row step, digit), plus the exponents
 // e(c, j). A CTA owns one 128 x 128 tile of G over a range of chunks (split-K): warp 0
 // streams the blobs of A and B into a three-stage ring with untiled bulk copies (48 KB a
-// stage), one thread of warp 1 issues the tcgen05.mma (M = N = 128, K = 16) into the three
-// class accumulators (384 tensor-memory columns) and commits stage releases and chunk
-// completions to mbarriers, and eight epilogue warps (two per tensor-memory lane quarter,
+// stage; B's digits side by side along N), one thread of warp 1 issues the tcgen05.mma
+// (M = 128, K = 16): per A digit s one MMA over the B digits 0 .. 2 - s at once (N = 384 as
+// 256 + 128, then 256, then 128), which writes the class accumulators s .. 2 side by side
+// (384 tensor-memory columns) and reads the A digit once instead of once per product; it
+// commits stage releases and chunk completions to mbarriers, and eight epilogue warps (two per tensor-memory lane quarter,
 // 64 columns each; high parts of the running sums in registers, low parts in shared
 // memory) flush every chunk. Partial tiles of the K splits are summed by a
 // second kernel in a fixed order (deterministic). Every wait is bounded; on a timeout the
@@ -72,10 +74,11 @@ constexpr unsigned kLbo = 2048, kSbo = 128;
 
 // The representations. Tc23: entries rounded to 23 bits of the chunk's largest, three
 // base-256 digits, classes 0..2, 256-row chunks, 128 x 128 tiles (sparc_gram_tc, the mixed
-// form's rotation). Tc47: 47 bits, six base-256 digits, classes 0..5 (21 digit MMAs per 16
-// rows; a class sums at most six digit products, so 128-row chunks keep it below 2^24),
-// 128 x 64 half tiles (six class accumulators of 64 columns fit the 512 tensor-memory
-// columns): the Gram pairs of both forms and the FP64 form's rotation. The digit base is a
+// form's rotation). Tc47: 47 bits, six base-256 digits, classes 0..5 (21 digit products per
+// 16 rows, issued as 8 MMAs of N = 64 .. 256 over the digit-concatenated B; a class sums at
+// most six digit products, so 128-row chunks keep it below 2^24), 128 x 64 half tiles (six
+// class accumulators of 64 columns fit the 512 tensor-memory columns): the Gram pairs of
+// both forms and the FP64 form's rotation. The digit base is a
 // parameter (kBase bits); kScale = kBits - kBase (kDigits - 1), so that
 // x = 2^(e - kScale) sum_s d_s 2^(-kBase s).
 struct Tc23 {
@@ -87,16 +90,18 @@ struct Tc47 {
                          kN = 64, kStages = 4, kBase = 8;
 };
 // A stage holds A's blobs (all 128 columns of each digit) and the kN columns of B's blobs
-// this CTA multiplies: per digit and 8-row K group, kN / 8 core matrices of 128 B (copied
-// as one contiguous piece of each blob's K group), so B's K-adjacent cores sit kN * 16 B
-// apart in shared memory.
+// this CTA multiplies. B is stored digit-concatenated: per 8-row K group, the kN / 8 core
+// matrices of digit 0, then those of digit 1, ... (kDigits kN columns, each piece copied
+// from one contiguous run of a blob's K group), so that one MMA with N = nb kN multiplies
+// an A digit by nb consecutive B digits at once and writes the nb class accumulators that
+// sit side by side in tensor memory. B's K-adjacent cores are kDigits kN 16 B apart.
 template <class C> struct TcDims {
     static constexpr int kStepsPerChunk = C::kChunk / C::kStep;
     static constexpr int kBlobElems = kTile * C::kStep;                    // BF16 per blob
     static constexpr unsigned kOperandBytes = C::kDigits * kBlobElems * 2;
-    static constexpr unsigned kBLbo = C::kN * 16;                          // B K-group stride
-    static constexpr unsigned kBDigitBytes = C::kN * C::kStep * 2;
-    static constexpr unsigned kBOperandBytes = C::kDigits * kBDigitBytes;
+    static constexpr unsigned kBPiece = C::kN * 16;            // one digit's cores of a K group
+    static constexpr unsigned kBLbo = C::kDigits * kBPiece;     // B K-group stride
+    static constexpr unsigned kBOperandBytes = C::kDigits * C::kN * C::kStep * 2;
     static constexpr unsigned kStageBytes = kOperandBytes + kBOperandBytes;
     static constexpr int kHalves = kTile / C::kN;                          // CTAs per tile
     static constexpr int kEpiCols = C::kN / 2;                             // per epilogue warp
@@ -358,7 +363,7 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
     using Dm = TcDims<C>;
     constexpr int kStages = C::kStages, kStepsPerChunk = Dm::kStepsPerChunk;
     constexpr unsigned kStageBytes = Dm::kStageBytes, kOperandBytes = Dm::kOperandBytes;
-    constexpr unsigned kBLbo = Dm::kBLbo, kBDigitBytes = Dm::kBDigitBytes;
+    constexpr unsigned kBLbo = Dm::kBLbo, kBPiece = Dm::kBPiece;
     constexpr int kGroups = C::kStep / 8;  // 8-row K groups of a step
     constexpr int kEpiCols = Dm::kEpiCols;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -377,7 +382,6 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
         int hf, tile, split;
         int2 tb;
         long c0, c1;
-        bool one;  // a diagonal tile of A^T A reads one operand: B's descriptors use A's blobs
     };
     auto unit = [&](int u) {
         Unit w;
@@ -387,7 +391,6 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
         w.tb = ROT ? make_int2(w.tile / mblk, w.tile % mblk) : tiles[w.tile];
         w.c0 = ROT ? 0 : (long)w.split * nchunk / nsplit;
         w.c1 = ROT ? nchunk : (long)(w.split + 1) * nchunk / nsplit;
-        w.one = !ROT && DA == DB && w.tb.x == w.tb.y;
         return w;
     };
 
@@ -428,26 +431,18 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                         break;
                     }
                     unsigned char *dst = smem + (size_t)s * kStageBytes;
-                    mbar_arrive_expect_tx(&full[s], w.one ? kOperandBytes : kStageBytes);
+                    mbar_arrive_expect_tx(&full[s], kStageBytes);
                     bulk_load(dst, DA + blob_offset<C>(w.tb.x, st, 0, nstep), kOperandBytes,
                               &full[s]);
-                    if (!w.one) {
-                        if (Dm::kHalves == 1) {
-                            bulk_load(dst + kOperandBytes,
-                                      DB + blob_offset<C>(w.tb.y, st, 0, nstep), kOperandBytes,
-                                      &full[s]);
-                        } else {
-                            // this unit's kN columns of every digit and K group of B
+                    // this unit's kN columns of every digit and K group of B, digit-concatenated
 #pragma unroll
-                            for (int d = 0; d < C::kDigits; ++d)
+                    for (int d = 0; d < C::kDigits; ++d)
 #pragma unroll
-                                for (int g = 0; g < kGroups; ++g)
-                                    bulk_load(dst + kOperandBytes + d * kBDigitBytes + g * kBLbo,
-                                              DB + blob_offset<C>(w.tb.y, st, d, nstep) +
-                                                  g * (kTile * 8) + w.hf * (C::kN * 8),
-                                              kBLbo, &full[s]);
-                        }
-                    }
+                        for (int g = 0; g < kGroups; ++g)
+                            bulk_load(dst + kOperandBytes + g * kBLbo + d * kBPiece,
+                                      DB + blob_offset<C>(w.tb.y, st, d, nstep) + g * (kTile * 8) +
+                                          w.hf * (C::kN * 8),
+                                      kBPiece, &full[s]);
                     issued = j + 1;
                 }
             }
@@ -464,12 +459,9 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
     } else if (warp == 1) {
         // ---- MMA issuer ----
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16_f32(kTile, C::kN);
             long j = 0, cc = 0;  // steps and chunks over all units
             for (int u = blockIdx.x; u < nunits && !abort_flag; u += ustride) {
                 const Unit w = unit(u);
-                // this unit's kN B columns start kN / 8 core matrices into the blob
-                const unsigned boff = (unsigned)(w.hf * (C::kN / 8) * kSbo);
                 const long st0 = w.c0 * kStepsPerChunk;
                 for (long st = st0; st < w.c1 * kStepsPerChunk && !abort_flag; ++st, ++j) {
                     const int s = (int)(j % kStages);
@@ -492,23 +484,22 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                     for (int ks = 0; ks < C::kStep / 16; ++ks) {
 #pragma unroll
                         for (int sa = 0; sa < C::kDigits; ++sa) {
+                            // A digit sa times B digits 0 .. nb-1 (classes sa .. sa+nb-1, the
+                            // kept ones), as MMAs of N <= 256 over the digit-concatenated B
+                            const int nb = C::kClasses - sa < C::kDigits ? C::kClasses - sa
+                                                                         : C::kDigits;
+                            const uint64_t ad =
+                                smem_desc(a + sa * Dm::kBlobElems * 2 + ks * 2 * kLbo, kLbo, kSbo);
 #pragma unroll
-                            for (int sb = 0; sb < C::kDigits; ++sb) {
-                                const int cl = sa + sb;
-                                if (cl >= C::kClasses) continue;
-                                // in this loop order the first product of every class is the
-                                // one with sa = 0; at a chunk start it overwrites the class
-                                const bool first = kin == 0 && ks == 0 && sa == 0;
-                                const uint64_t ad = smem_desc(
-                                    a + sa * Dm::kBlobElems * 2 + ks * 2 * kLbo, kLbo, kSbo);
-                                // B: its own compact kN columns, or (a diagonal tile of
-                                // A^T A) the unit's columns inside A's blobs
+                            for (int n0 = 0; n0 < nb * C::kN; n0 += 256) {
+                                const int nl = nb * C::kN - n0 < 256 ? nb * C::kN - n0 : 256;
                                 const uint64_t bd =
-                                    w.one ? smem_desc(a + sb * Dm::kBlobElems * 2 + ks * 2 * kLbo +
-                                                          boff, kLbo, kSbo)
-                                          : smem_desc(b + sb * kBDigitBytes + ks * 2 * kBLbo,
-                                                      kBLbo, kSbo);
-                                tc_mma_bf16(tmem + (uint32_t)(cl * C::kN), ad, bd, idesc, !first);
+                                    smem_desc(b + ks * 2 * kBLbo + (n0 / 8) * kSbo, kBLbo, kSbo);
+                                // the sa = 0 MMAs cover every class: at a chunk start they
+                                // overwrite the accumulators, all later ones accumulate
+                                const bool first = kin == 0 && ks == 0 && sa == 0;
+                                tc_mma_bf16(tmem + (uint32_t)(sa * C::kN + n0), ad, bd,
+                                            idesc_bf16_f32(kTile, nl), !first);
                             }
                         }
                     }
@@ -837,7 +828,7 @@ template cudaError_t gram_tc47_pair<float>(const float *, long, const double *, 
 // of a column. The FP64 form uses the 47-bit digits (FP64 blocks, FP64 output); the mixed
 // form the 23-bit digits (FP32 block or the FP64 H Y of its residuals, FP32 output): each
 // entry of Y and C is rounded to 2^-24 of its chunk's largest, the rounding an FP32 result
-// carries anyway, for 6 digit MMAs per 16 K instead of 21.
+// carries anyway, for 6 digit products per 16 K instead of 21.
 namespace {
 struct RotPlan {
     int ns_pad, mblk;
