@@ -524,15 +524,33 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                     (size_t)(warp - 2) * kEpiCols * 32 + lane;  // Lw[u * 32]: column u
         long cc = 0;  // chunks over all units
         bool ok = true;
+        // the chunk exponents are loaded one chunk ahead (they do not depend on the MMAs):
+        // this thread's A column, and kEpiCols / 32 of the warp's B columns per lane, whose
+        // factors reach the other lanes by shuffle
+        constexpr int kEB = kEpiCols / 32;
+        const long eb_stride = ROT ? eb_ld : ns_pad;
         for (int u = blockIdx.x; u < nunits && ok; u += ustride) {
             const Unit w = unit(u);
             const long colA = (long)w.tb.x * kTile + r;
+            const int *ebw = EB + (long)w.tb.y * kTile + w.hf * C::kN + hw * kEpiCols + lane;
 #pragma unroll
             for (int x = 0; x < kEpiCols; ++x) {
                 H[x] = 0.0f;
                 Lw[x * 32] = 0.0f;
             }
+            int ea_n = EA[w.c0 * ea_stride + colA], eb_n[kEB];
+#pragma unroll
+            for (int k = 0; k < kEB; ++k) eb_n[k] = ebw[w.c0 * eb_stride + 32 * k];
             for (long c = w.c0; c < w.c1; ++c, ++cc) {
+                const float fA = pow2_factor<C>(ea_n);
+                float fb[kEB];
+#pragma unroll
+                for (int k = 0; k < kEB; ++k) fb[k] = pow2_factor<C>(eb_n[k]);
+                if (c + 1 < w.c1) {
+                    ea_n = EA[(c + 1) * ea_stride + colA];
+#pragma unroll
+                    for (int k = 0; k < kEB; ++k) eb_n[k] = ebw[(c + 1) * eb_stride + 32 * k];
+                }
                 ok = mbar_wait(&acc_full, (unsigned)(cc & 1), kWaitLimit) && !abort_flag;
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) {
@@ -540,9 +558,6 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                     break;
                 }
                 tc_fence_after();
-                const float fA = pow2_factor<C>(EA[c * ea_stride + colA]);
-                const int *eb = EB + c * (ROT ? eb_ld : ns_pad) + (long)w.tb.y * kTile +
-                                w.hf * C::kN + hw * kEpiCols;
 #pragma unroll
                 for (int g = 0; g < kEpiCols / 8; ++g) {
                     const uint32_t ta =
@@ -565,7 +580,8 @@ k_gram_tc(const __nv_bfloat16 *__restrict__ DA, const int *__restrict__ EA,
                             h = t;
                             l += e2;
                         }
-                        const float f = fA * pow2_factor<C>(eb[g * 8 + x]);
+                        const float f =
+                            fA * __shfl_sync(0xffffffffu, fb[(g * 8 + x) / 32], (g * 8 + x) % 32);
                         const float ph = h * f, pl = l * f;
                         float sh, se;
                         two_sum_f(H[g * 8 + x], ph, sh, se);

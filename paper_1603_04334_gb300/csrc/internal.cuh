@@ -82,8 +82,8 @@ cudaError_t stencil_f64(const DevHam &H, const double *Y, const double *Yprev, d
                         const unsigned *bY, unsigned *bOut, cudaStream_t st);
 cudaError_t scaled_v(const double *V, double alpha, double shift, double *u, long n,
                      cudaStream_t st);
-// out += V_nl part from Cs = alpha chi^T Y (pairs), for FP64 blocks (stencil_df.cu); bOut
-// as for stencil_f64 (raised to the bound of the updated values)
+// out += V_nl part from Cs = alpha chi^T Y (pairs), for FP64 outputs (nonlocal.cu); bOut
+// as for stencil_f64 (raised to the bound of the updated values), or null
 cudaError_t scatter_f64_df(const DevHam &H, const float2 *Cs, double *out, int ncols, long ld,
                            unsigned *bOut, cudaStream_t st);
 // b[c] = max(b[c], largest high word of |Y| over column c) for FP64 or FP32 blocks (an FP32
@@ -176,11 +176,9 @@ cudaError_t project_f64_df(const DevHam &H, const double *Y, int ncols, long ld,
                            float2 *C, cudaStream_t st);
 cudaError_t project_f32(const DevHam &H, const float *Y, int ncols, long ld, double alpha,
                         float *C, cudaStream_t st);
-cudaError_t project_f32in_f64(const DevHam &H, const float *Y, int ncols, long ld, double *C,
+// the FP64 projection of an FP32 block (pairs, alpha = 1), for the pair scatter
+cudaError_t project_f32in_f64(const DevHam &H, const float *Y, int ncols, long ld, float2 *C,
                               cudaStream_t st);
-// out[node + c*ld] += alpha * sum_{entries e at node} sum_lm gchi(e,lm) C[(atom(e)*4+lm)*ncols + c]
-cudaError_t scatter_f64(const DevHam &H, const double *C, double *out, int ncols, long ld,
-                        double alpha, cudaStream_t st);
 // node-ordered entry tables of the scatter kernels
 cudaError_t build_nl_node_tables(long nuniq, const int *uniq_ptr, const int *ent_list,
                                  const int *ent_atom, const double *gchi, int *nl_atom,

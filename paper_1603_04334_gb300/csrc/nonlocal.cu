@@ -157,20 +157,16 @@ cudaError_t project_f32(const DevHam &H, const float *Y, int ncols, long ld, dou
 {
     return project<float, float, true>(H, Y, ncols, ld, H.chi_f, C, (float)alpha, st);
 }
-cudaError_t project_f32in_f64(const DevHam &H, const float *Y, int ncols, long ld, double *C,
-                              cudaStream_t st)
-{
-    return project<float, double, false>(H, Y, ncols, ld, H.chi, C, 1.0, st);
-}
-
-// ---- FP64 blocks in FP32-pair arithmetic (see df.cuh) ----------------------------------
+// ---- FP64 arithmetic in FP32 pairs (see df.cuh) -----------------------------------------
 // Projection with compensated products; each thread's partial sums over its share of the
 // support are combined across the CTA with pair additions (TwoSum). The result is written
-// as FP32 pairs, scaled by `alpha` (the filter step's factor), for the pair scatter.
+// as FP32 pairs, scaled by `alpha` (the filter step's factor), for the pair scatter. T: the
+// block's type (FP64 blocks, or the FP32 block to which the mixed-precision Rayleigh-Ritz
+// step applies H in FP64; an FP32 value is the pair (y, 0)).
 // Grid as k_project: x = atom, y = column block.
-template <int CB, int NT>
+template <typename T, int CB, int NT>
 __global__ void __launch_bounds__(NT, 4)
-k_project_df(const double *__restrict__ Y, long ld, int ncols, const int *__restrict__ atom_ptr,
+k_project_df(const T *__restrict__ Y, long ld, int ncols, const int *__restrict__ atom_ptr,
              const int *__restrict__ idx, const float2 *__restrict__ chi, float2 *__restrict__ C,
              float alh, float all)
 {
@@ -236,90 +232,65 @@ k_project_df(const double *__restrict__ Y, long ld, int ncols, const int *__rest
     }
 }
 
-cudaError_t project_f64_df(const DevHam &H, const double *Y, int ncols, long ld, double alpha,
-                           float2 *C, cudaStream_t st)
+template <typename T>
+static cudaError_t project_df(const DevHam &H, const T *Y, int ncols, long ld, double alpha,
+                              float2 *C, cudaStream_t st)
 {
     if (H.natoms == 0 || ncols <= 0) return cudaSuccess;
     constexpr int CB = 2, NT = 256;
     dim3 grid(H.natoms, (ncols + CB - 1) / CB);
     if (grid.y > 65535) return cudaErrorInvalidValue;
     const float alh = (float)alpha, all = (float)(alpha - (double)alh);
-    k_project_df<CB, NT><<<grid, NT, 0, st>>>(Y, ld, ncols, H.atom_ptr, H.idx, H.chi_df, C, alh,
-                                              all);
+    k_project_df<T, CB, NT><<<grid, NT, 0, st>>>(Y, ld, ncols, H.atom_ptr, H.idx, H.chi_df, C,
+                                                 alh, all);
     note_launch();
     return cudaGetLastError();
 }
 
-// Native FP64 scatter, used where H is applied in FP64 to an FP32 block (the H Y_f of the
-// mixed-precision Rayleigh-Ritz step). Same grid as the FP32 scatter below: one covered
-// node per thread, kScatCols columns per CTA, column groups along the grid's x dimension.
-constexpr int kScatNodes = 256;
-constexpr int kScatCols = 16;
-constexpr int kScatF32Cols = 8;  // columns per thread of the FP32 scatter
-
-__global__ void __launch_bounds__(kScatNodes)
-k_scatter_f64(double *out, long ld, int ncols, long nuniq, const int *__restrict__ uniq_node,
-              const int *__restrict__ uniq_ptr, const int *__restrict__ ent_list,
-              const int *__restrict__ ent_atom, const double *__restrict__ gchi,
-              const double *__restrict__ C, double alpha)
+cudaError_t project_f64_df(const DevHam &H, const double *Y, int ncols, long ld, double alpha,
+                           float2 *C, cudaStream_t st)
 {
-    const int c0 = blockIdx.x * kScatCols, c1 = min(ncols, c0 + kScatCols);
-    for (long ub = blockIdx.y; ub * kScatNodes < nuniq; ub += gridDim.y) {
-        const long u = ub * kScatNodes + threadIdx.x;
-        if (u >= nuniq) continue;
-        const long node = uniq_node[u];
-        const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
-#pragma unroll 2
-        for (int c = c0; c < c1; ++c) {
-            double v = 0.0;
-            for (int q = q0; q < q1; ++q) {
-                const int e = ent_list[q];
-                const int J = ent_atom[e];
-#pragma unroll
-                for (int l = 0; l < 4; ++l)
-                    v += gchi[4 * (long)e + l] * C[(long)(J * 4 + l) * ncols + c];
-            }
-            double *o = out + node + (long)c * ld;
-            *o = *o + alpha * v;
-        }
-    }
+    return project_df<double>(H, Y, ncols, ld, alpha, C, st);
 }
 
-// FP32 blocks: Cs holds alpha chi^T Y as one float4 per (atom, column), Cs4[J * ncols + c],
-// and g4[q] the four h^3 gamma chi values of entry q. A thread owns one covered node and a
-// group of columns; the grid's x dimension (dispatched first) runs over the column groups,
-// so the CTAs resident at one time share their covered nodes and read the node's entry
-// tables from L1/L2 (with the nodes outermost, every column group read the tables again
-// from DRAM: about as many bytes as the output itself at 1024 columns). The thread first
-// issues its kScatCols output reads (independent DRAM loads in flight), then walks its
-// node's entries (the atoms whose support holds it, ascending): per entry one load of the
-// four coefficients and, per column, one 16-byte load of Cs (L1/L2-resident). The entry
-// loop runs to the largest entry count of the warp with the shorter lanes predicated off,
-// so a warp whose nodes are covered by different numbers of atoms stays on one path.
-// Per column the entries are summed in ascending order.
-template <int NC>
-__device__ __forceinline__ void scatter_f32_node(float *out, long ld, int ncols, long node, int q0,
-                                                 int q1, int c0, int nc, bool live,
-                                                 const int *__restrict__ nl_atom,
-                                                 const float4 *__restrict__ g4,
-                                                 const float4 *__restrict__ Cs4)
+cudaError_t project_f32in_f64(const DevHam &H, const float *Y, int ncols, long ld, float2 *C,
+                              cudaStream_t st)
 {
-    float *oc = out + node + (long)c0 * ld;
-    float x[NC], v[NC];
+    return project_df<float>(H, Y, ncols, ld, 1.0, C, st);
+}
+
+constexpr int kScatNodes = 256;     // covered nodes (threads) per CTA of the FP32 scatter
+constexpr int kScatF32Cols = 8;     // columns per group
+constexpr int kScatF32Groups = 4;   // column groups per thread
+
+// FP32 blocks: Cs holds alpha chi^T Y as one float4 per (atom, column), Cs4[J * ncols + c],
+// and g4[q] the four h^3 gamma chi values of entry q. A thread owns one covered node and
+// kScatF32Groups groups of kScatF32Cols columns; the grid's x dimension (dispatched first)
+// runs over the column ranges, so the CTAs resident at one time share their covered nodes
+// and read the node's entry tables from L1/L2 (with the nodes outermost, every column group
+// read the tables again from DRAM: about as many bytes as the output itself at 1024
+// columns). Per group the thread walks its node's entries (the atoms whose support holds
+// it, ascending): per entry one load of the four coefficients and, per column, one 16-byte
+// load of Cs (L1/L2-resident). The entry loop runs to the largest entry count of the warp
+// with the shorter lanes predicated off, so a warp whose nodes are covered by different
+// numbers of atoms stays on one path. Per column the entries are summed in ascending order.
+template <int NC>
+__device__ __forceinline__ void scatter_f32_group(float *ob, long ld, int ncols, int cg, int q0,
+                                                  int n, int nmax, bool live, const float (&x)[NC],
+                                                  const int *__restrict__ nl_atom,
+                                                  const float4 *__restrict__ g4,
+                                                  const float4 *__restrict__ Cs4)
+{
+    float v[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        x[c] = (live && c < nc) ? oc[(long)c * ld] : 0.0f;
-        v[c] = 0.0f;
-    }
-    const int n = live ? q1 - q0 : 0;
-    const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
+    for (int c = 0; c < NC; ++c) v[c] = 0.0f;
     for (int t = 0; t < nmax; ++t) {
         if (t < n) {
             const float4 g = g4[q0 + t];
-            const float4 *cq = Cs4 + (long)nl_atom[q0 + t] * ncols + c0;
+            const float4 *cq = Cs4 + (long)nl_atom[q0 + t] * ncols + cg;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                if (c < nc) {
+                if (cg + c < ncols) {
                     const float4 cc = cq[c];
                     v[c] += g.x * cc.x;
                     v[c] += g.y * cc.y;
@@ -332,24 +303,58 @@ __device__ __forceinline__ void scatter_f32_node(float *out, long ld, int ncols,
     if (live) {
 #pragma unroll
         for (int c = 0; c < NC; ++c)
-            if (c < nc) oc[(long)c * ld] = x[c] + v[c];
+            if (cg + c < ncols) ob[(long)(cg + c) * ld] = x[c] + v[c];
     }
 }
 
-// One covered node per thread, NC columns; every lane of a warp reaches the entry loop's
-// warp-wide maximum (lanes past nuniq take part with no entries).
-template <int NC>
+// Covered node `node` (entries q0 .. q1-1), columns c0 .. c0 + NG NC - 1 (those below ncols)
+// in NG groups of NC: the output reads of group g+1 are issued before the sums of group g
+// are formed and stored, so a thread keeps NC DRAM reads in flight throughout. All lanes
+// of a warp call it together (lanes without a node pass live = false).
+template <int NC, int NG>
+__device__ __forceinline__ void scatter_f32_node(float *out, long ld, int ncols, long node, int q0,
+                                                 int q1, int c0, bool live,
+                                                 const int *__restrict__ nl_atom,
+                                                 const float4 *__restrict__ g4,
+                                                 const float4 *__restrict__ Cs4)
+{
+    float *ob = out + node;
+    const int n = live ? q1 - q0 : 0;
+    const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
+    float x[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) x[c] = (live && c0 + c < ncols) ? ob[(long)(c0 + c) * ld] : 0.0f;
+#pragma unroll 1
+    for (int gi = 0; gi < NG; ++gi) {
+        const int cg = c0 + gi * NC;
+        if (cg >= ncols) break;
+        const int cn = cg + NC;
+        const bool more = gi + 1 < NG && cn < ncols;
+        float xn[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            xn[c] = (more && live && cn + c < ncols) ? ob[(long)(cn + c) * ld] : 0.0f;
+        scatter_f32_group<NC>(ob, ld, ncols, cg, q0, n, nmax, live, x, nl_atom, g4, Cs4);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) x[c] = xn[c];
+    }
+}
+
+// One covered node per thread, NG groups of NC columns; every lane of a warp reaches the
+// entry loop's warp-wide maximum (lanes past nuniq take part with no entries).
+template <int NC, int NG>
 __global__ void __launch_bounds__(kScatNodes)
 k_scatter_f32(float *out, long ld, int ncols, long nuniq, const int *__restrict__ uniq_node,
               const int *__restrict__ uniq_ptr, const int *__restrict__ nl_atom,
               const float4 *__restrict__ g4, const float4 *__restrict__ Cs4)
 {
-    const int c0 = blockIdx.x * NC, nc = min(ncols - c0, NC);
+    const int c0 = blockIdx.x * NC * NG;
     for (long ub = blockIdx.y; ub * kScatNodes < nuniq; ub += gridDim.y) {
         const long u = ub * kScatNodes + threadIdx.x;
         const bool live = u < nuniq;
-        scatter_f32_node<NC>(out, ld, ncols, live ? uniq_node[u] : 0, live ? uniq_ptr[u] : 0,
-                             live ? uniq_ptr[u + 1] : 0, c0, nc, live, nl_atom, g4, Cs4);
+        scatter_f32_node<NC, NG>(out, ld, ncols, live ? uniq_node[u] : 0,
+                                 live ? uniq_ptr[u] : 0, live ? uniq_ptr[u + 1] : 0, c0, live,
+                                 nl_atom, g4, Cs4);
     }
 }
 
@@ -362,11 +367,11 @@ k_batch_scatter(const BatchItem *__restrict__ items, int nitems, const BatchNonl
         const BatchNonlocal &P = cs[w.cluster];
         const long u = (long)w.a * kBatchNodes + threadIdx.x;
         const bool live = u < P.nuniq;
-        const int nc = min(P.ncols - w.col, kBatchCols);
-        scatter_f32_node<kBatchCols>(P.out, P.ld, P.ncols, live ? P.uniq_node[u] : 0,
-                         live ? P.uniq_ptr[u] : 0, live ? P.uniq_ptr[u + 1] : 0, w.col, nc, live,
-                         P.nl_atom, reinterpret_cast<const float4 *>(P.nl_gf),
-                         reinterpret_cast<const float4 *>(P.C));
+        scatter_f32_node<kBatchCols, 1>(P.out, P.ld, P.ncols, live ? P.uniq_node[u] : 0,
+                                        live ? P.uniq_ptr[u] : 0, live ? P.uniq_ptr[u + 1] : 0,
+                                        w.col, live, P.nl_atom,
+                                        reinterpret_cast<const float4 *>(P.nl_gf),
+                                        reinterpret_cast<const float4 *>(P.C));
     }
 }
 
@@ -383,41 +388,28 @@ cudaError_t scatter_f32(const DevHam &H, const float *Cs, float *out, int ncols,
                         cudaStream_t st)
 {
     if (H.natoms == 0 || H.nuniq == 0 || ncols <= 0) return cudaSuccess;
-    constexpr int NC = kScatF32Cols;
+    constexpr int NC = kScatF32Cols, NG = kScatF32Groups;
     const long nb = (H.nuniq + kScatNodes - 1) / kScatNodes;
-    dim3 grid((unsigned)((ncols + NC - 1) / NC), (unsigned)(nb < 65535 ? nb : 65535));
-    k_scatter_f32<NC><<<grid, kScatNodes, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node, H.uniq_ptr,
+    dim3 grid((unsigned)((ncols + NC * NG - 1) / (NC * NG)), (unsigned)(nb < 65535 ? nb : 65535));
+    k_scatter_f32<NC, NG><<<grid, kScatNodes, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node, H.uniq_ptr,
                                                H.nl_atom, reinterpret_cast<const float4 *>(H.nl_gf),
                                                reinterpret_cast<const float4 *>(Cs));
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t scatter_f64(const DevHam &H, const double *C, double *out, int ncols, long ld,
-                        double alpha, cudaStream_t st)
-{
-    if (H.natoms == 0 || H.nuniq == 0 || ncols <= 0) return cudaSuccess;
-    const long nb = (H.nuniq + kScatNodes - 1) / kScatNodes;
-    dim3 grid((unsigned)((ncols + kScatCols - 1) / kScatCols),
-              (unsigned)(nb < 65535 ? nb : 65535));
-    k_scatter_f64<<<grid, kScatNodes, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node,
-                                               H.uniq_ptr, H.ent_list, H.ent_atom, H.gchi, C,
-                                               alpha);
-    note_launch();
-    return cudaGetLastError();
-}
-
 // Nonlocal scatter for FP64 blocks in pair arithmetic: out(p, c) += sum_{q at p} sum_l
 // g(q, l) Cs(atom(q), l, c), Cs = alpha chi^T Y as pairs (k_project_df). A thread owns one
-// covered node and a group of kScatDfCols columns; the grid's x dimension (dispatched first)
-// runs over the column groups, so the CTAs resident at one time share their covered nodes
-// (the node's entry tables are read from L1/L2, not once per column group from DRAM), and
-// y over blocks of covered nodes (strided when there are more than the grid holds). The pair
-// sum is added to the FP64 output with one FP64 add. With bOut, the column bounds of the
-// output are raised to cover the updated values.
+// covered node and kScatDfGroups groups of kScatDfCols columns; the grid's x dimension
+// (dispatched first) runs over the column ranges, so the CTAs resident at one time share
+// their covered nodes (the node's entry tables are read from L1/L2, not once per column
+// group from DRAM), and y over blocks of covered nodes (strided when there are more than the
+// grid holds). The pair sum is added to the FP64 output with one FP64 add. With bOut, the
+// column bounds of the output are raised to cover the updated values.
 namespace {
 constexpr int kScatDfNodes = 256;
-constexpr int kScatDfCols = 4;
+constexpr int kScatDfCols = 4;    // columns per group
+constexpr int kScatDfGroups = 4;  // column groups per thread
 }  // namespace
 
 __global__ void __launch_bounds__(kScatDfNodes, 4)
@@ -425,50 +417,63 @@ k_scatter_df(double *out, long ld, int ncols, long nuniq, const int *__restrict_
              const int *__restrict__ uniq_ptr, const int *__restrict__ nl_atom,
              const float2 *__restrict__ g, const float2 *__restrict__ Cs, unsigned *bOut)
 {
-    const int c0 = blockIdx.x * kScatDfCols, c1 = min(ncols, c0 + kScatDfCols);
-    unsigned om[kScatDfCols];
-#pragma unroll
-    for (int k = 0; k < kScatDfCols; ++k) om[k] = 0u;
-    // the block loop is uniform over the CTA: every lane reaches the bound reduction below
+    constexpr int K = kScatDfCols;
+    const int c0 = blockIdx.x * K * kScatDfGroups;
+    // both loops are uniform over the CTA: every lane reaches the bound reductions
     for (long ub = blockIdx.y; ub * kScatDfNodes < nuniq; ub += gridDim.y) {
         const long u = ub * kScatDfNodes + threadIdx.x;
-        if (u >= nuniq) continue;
-        const long node = uniq_node[u];
-        const int q0 = uniq_ptr[u], q1 = uniq_ptr[u + 1];
-        // the output reads go first (kScatDfCols DRAM reads in flight while the sums are
-        // formed); each entry's atom and coefficients are loaded once for all columns, and
-        // per column the entries are summed in ascending order
-        double *op = out + node + (long)c0 * ld;
-        double o[kScatDfCols];
+        const bool live = u < nuniq;
+        const long node = live ? uniq_node[u] : 0;
+        const int q0 = live ? uniq_ptr[u] : 0, q1 = live ? uniq_ptr[u + 1] : 0;
+        double *ob = out + node;
+        // the output reads of group g+1 are issued before the sums of group g are formed,
+        // so K DRAM reads stay in flight; each entry's atom and coefficients are loaded once
+        // per group, and per column the entries are summed in ascending order
+        double o[K];
 #pragma unroll
-        for (int k = 0; k < kScatDfCols; ++k) o[k] = c0 + k < c1 ? op[(long)k * ld] : 0.0;
-        float vh[kScatDfCols], vl[kScatDfCols];
+        for (int k = 0; k < K; ++k) o[k] = (live && c0 + k < ncols) ? ob[(long)(c0 + k) * ld] : 0.0;
+#pragma unroll 1
+        for (int gi = 0; gi < kScatDfGroups; ++gi) {
+            const int cg = c0 + gi * K;
+            if (cg >= ncols) break;
+            const int cn = cg + K;
+            const bool more = gi + 1 < kScatDfGroups && cn < ncols;
+            double on[K];
 #pragma unroll
-        for (int k = 0; k < kScatDfCols; ++k) vh[k] = vl[k] = 0.0f;
-        for (int q = q0; q < q1; ++q) {
-            const float2 *cs = Cs + (long)nl_atom[q] * 4 * ncols + c0;
+            for (int k = 0; k < K; ++k)
+                on[k] = (more && live && cn + k < ncols) ? ob[(long)(cn + k) * ld] : 0.0;
+            float vh[K], vl[K];
 #pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const float2 gl = g[4L * q + l];
+            for (int k = 0; k < K; ++k) vh[k] = vl[k] = 0.0f;
+            for (int q = q0; q < q1; ++q) {
+                const float2 *cs = Cs + (long)nl_atom[q] * 4 * ncols + cg;
 #pragma unroll
-                for (int k = 0; k < kScatDfCols; ++k)
-                    if (c0 + k < c1) mac(gl, cs[(long)l * ncols + k], vh[k], vl[k]);
+                for (int l = 0; l < 4; ++l) {
+                    const float2 gl = g[4L * q + l];
+#pragma unroll
+                    for (int k = 0; k < K; ++k)
+                        if (cg + k < ncols) mac(gl, cs[(long)l * ncols + k], vh[k], vl[k]);
+                }
             }
-        }
+            unsigned om[K];
 #pragma unroll
-        for (int k = 0; k < kScatDfCols; ++k) {
-            o[k] += pair_to_double(vh[k], vl[k]);
-            if (c0 + k < c1) {
-                op[(long)k * ld] = o[k];
-                om[k] = max(om[k], abs_hi_word(o[k]));
+            for (int k = 0; k < K; ++k) {
+                o[k] += pair_to_double(vh[k], vl[k]);
+                om[k] = 0u;
+                if (live && cg + k < ncols) {
+                    ob[(long)(cg + k) * ld] = o[k];
+                    om[k] = abs_hi_word(o[k]);
+                }
             }
-        }
-    }
-    if (bOut) {
+            if (bOut) {
 #pragma unroll
-        for (int k = 0; k < kScatDfCols; ++k) {
-            const unsigned m = __reduce_max_sync(0xffffffffu, om[k]);
-            if ((threadIdx.x & 31) == 0 && m && c0 + k < c1) raise_bound(bOut + c0 + k, m);
+                for (int k = 0; k < K; ++k) {
+                    const unsigned m = __reduce_max_sync(0xffffffffu, om[k]);
+                    if ((threadIdx.x & 31) == 0 && m && cg + k < ncols) raise_bound(bOut + cg + k, m);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) o[k] = on[k];
         }
     }
 }
@@ -478,8 +483,8 @@ cudaError_t scatter_f64_df(const DevHam &H, const float2 *Cs, double *out, int n
 {
     if (H.natoms == 0 || H.nuniq == 0 || ncols <= 0) return cudaSuccess;
     const long nb = (H.nuniq + kScatDfNodes - 1) / kScatDfNodes;
-    dim3 grid((unsigned)((ncols + kScatDfCols - 1) / kScatDfCols),
-              (unsigned)(nb < 65535 ? nb : 65535));
+    constexpr int cpb = kScatDfCols * kScatDfGroups;
+    dim3 grid((unsigned)((ncols + cpb - 1) / cpb), (unsigned)(nb < 65535 ? nb : 65535));
     k_scatter_df<<<grid, kScatDfNodes, 0, st>>>(out, ld, ncols, H.nuniq, H.uniq_node, H.uniq_ptr,
                                               H.nl_atom, H.nl_gdf, Cs, bOut);
     note_launch();

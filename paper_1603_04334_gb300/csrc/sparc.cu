@@ -302,12 +302,12 @@ sparc_status apply_f32in_f64(sparc_ctx *ctx, const float *Y, double *out, int nc
     const DevHam &H = ctx->H;
     if (H.natoms > 0) {
         TRY(ensure_C(ctx, ncols));
-        { PHASE(SPARC_PHASE_PROJECT); CK(project_f32in_f64(H, Y, ncols, ld, (double *)ctx->C, ctx->st)); }
+        { PHASE(SPARC_PHASE_PROJECT); CK(project_f32in_f64(H, Y, ncols, ld, (float2 *)ctx->C, ctx->st)); }
     }
     unsigned *bY = nullptr;
     TRY(scratch_bounds(ctx, Y, ncols, ld, &bY));
     { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f32in_f64(H, Y, out, ncols, ld, bY, ctx->st)); }
-    if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f64(H, (const double *)ctx->C, out, ncols, ld, 1.0, ctx->st)); }
+    if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f64_df(H, (const float2 *)ctx->C, out, ncols, ld, nullptr, ctx->st)); }
     return SPARC_OK;
 }
 
