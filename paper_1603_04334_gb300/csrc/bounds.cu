@@ -1,7 +1,6 @@
 // bounds.cu -- helpers of the FP64 path that run once per block or per context:
 // per-column magnitude bounds (the FP64 stencil's fixed-point grid), V_eff - shift as FP32
 // pairs, and FP64 arrays as FP32 pairs.
-#include "df.cuh"
 #include "fx.cuh"
 #include "internal.cuh"
 
@@ -63,20 +62,6 @@ cudaError_t colmax_f32(const float *Y, int ncols, long ld, long nd, unsigned *b,
                        cudaStream_t st)
 {
     return colmax_launch<float>(Y, ncols, ld, nd, b, st);
-}
-
-__global__ void k_to_float_pair(const double *in, float2 *out, long n)
-{
-    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (long)gridDim.x * blockDim.x)
-        out[q] = split_double(in[q]);
-}
-
-cudaError_t to_float_pair(const double *in, float2 *out, long n, cudaStream_t st)
-{
-    k_to_float_pair<<<152 * 8, 256, 0, st>>>(in, out, n);
-    note_launch();
-    return cudaGetLastError();
 }
 
 }  // namespace sparc

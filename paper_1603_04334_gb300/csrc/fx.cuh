@@ -1,7 +1,7 @@
 // fx.cuh -- per-column magnitude bounds of FP64 blocks and the fixed-point grid they
-// define, shared by the FP64 stencil (stencil_df.cu), the pair scatter (nonlocal.cu) and
-// the bound pass (bounds.cu). A bound is the largest high word (bits 32..62) of |y| over a
-// column; it only grows.
+// define, shared by the FP64 stencil (stencil_df.cu), the nonlocal projection and pair
+// scatter (nonlocal.cu) and the bound pass (bounds.cu). A bound is the largest high word
+// (bits 32..62) of |y| over a column; it only grows.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -32,46 +32,36 @@ __device__ __forceinline__ unsigned abs_hi_word(float x)
 // Column bound (largest high word of |y|) -> E with |y| < 2^E for every y of the column.
 __device__ __forceinline__ int bound_exponent(unsigned b) { return (int)((b >> 20) & 0x7ffu) - 1022; }
 
-// A value on the column's grid: .x = d, .y = the bits of r (y 2^(28-E) = d + r).
-// From the significand M (53 bits) of y = M 2^(e-1075): d = M >> s and r = the next 23
-// bits of M below d, with s = 1047 + E - e >= 25 (|y| < 2^E); zero and subnormal y give 0.
-__device__ __forceinline__ int2 to_fx(double y, int E)
+// A value on its column's 49-bit grid as two integers: y 2^(49-E) = d 2^23 + r truncated
+// toward zero, |d| < 2^26 and |r| < 2^23, both with the sign of y (|y| < 2^E). From
+// y = M 2^(e-1075) (M the 53-bit significand): N = M >> s, s = 1026 + E - e >= 4, holds d
+// (N >> 23) and r (the low 23 bits); zero and subnormal y give 0.
+__device__ __forceinline__ int2 fx_split(double y, int E)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(y);
-    const unsigned hw = (unsigned)(b >> 32), ml = (unsigned)b;
+    const unsigned hw = (unsigned)(b >> 32);
     const int e = (int)((hw >> 20) & 0x7ffu);
-    const unsigned mh = (hw & 0xfffffu) | 0x100000u;
-    const int s = 1047 + E - e, s2 = s - 23;
-    const unsigned d = s < 32 ? __funnelshift_r(ml, mh, s) : (mh >> min(s - 32, 31));
-    const unsigned r23 =
-        (s2 < 32 ? __funnelshift_r(ml, mh, s2) : (mh >> min(s2 - 32, 31))) & 0x7fffffu;
-    float r = __uint_as_float(0x3F800000u | r23) - 1.0f;  // r23 2^-23, exact
-    int di = (int)d;
-    if (hw >> 31) {
-        di = -di;
-        r = -r;
-    }
-    return e == 0 ? make_int2(0, 0) : make_int2(di, __float_as_int(r));
+    const unsigned long long M =
+        e ? ((b & 0x000fffffffffffffull) | 0x0010000000000000ull) : 0ull;
+    const unsigned long long N = M >> min(1026 + E - e, 63);
+    const int sm = (int)hw >> 31;  // 0 or -1
+    const int d = ((int)(unsigned)(N >> 23) ^ sm) - sm;
+    const int r = ((int)((unsigned)N & 0x7fffffu) ^ sm) - sm;
+    return make_int2(d, r);
 }
 
-// FP32 input: y = m 2^(e-150) (24-bit m); with M = m 2^27 (< 2^51),
-// y 2^(28-E) = M 2^-s, s = 149 + E - e >= 23 (|y| < 2^E), so d = M >> s < 2^28.
-__device__ __forceinline__ int2 to_fx(float y, int E)
+// FP32: y = m 2^(e-150) (24-bit m) = (m 2^29) 2^(e-179), so s = 130 + E - e.
+__device__ __forceinline__ int2 fx_split(float y, int E)
 {
     const unsigned u = __float_as_uint(y);
     const int e = (int)((u >> 23) & 0xffu);
-    const unsigned long long M = (unsigned long long)((u & 0x7fffffu) | 0x800000u) << 27;
-    const int s = 149 + E - e;
-    const unsigned d = s < 64 ? (unsigned)(M >> s) : 0u;
-    const int s2 = s - 23;
-    const unsigned r23 = (s2 < 64 ? (unsigned)(M >> s2) : 0u) & 0x7fffffu;
-    float r = __uint_as_float(0x3F800000u | r23) - 1.0f;
-    int di = (int)d;
-    if (u >> 31) {
-        di = -di;
-        r = -r;
-    }
-    return e == 0 ? make_int2(0, 0) : make_int2(di, __float_as_int(r));
+    const unsigned long long M =
+        e ? ((unsigned long long)((u & 0x7fffffu) | 0x800000u) << 29) : 0ull;
+    const unsigned long long N = M >> min(130 + E - e, 63);
+    const int sm = (int)u >> 31;
+    const int d = ((int)(unsigned)(N >> 23) ^ sm) - sm;
+    const int r = ((int)((unsigned)N & 0x7fffffu) ^ sm) - sm;
+    return make_int2(d, r);
 }
 
 }  // namespace sparc

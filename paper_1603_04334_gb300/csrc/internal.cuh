@@ -38,7 +38,10 @@ struct DevHam {
     const int *idx = nullptr;        // node index of each entry
     const double *chi = nullptr;     // 4 per entry: chi_s, chi_px, chi_py, chi_pz
     const float *chi_f = nullptr;
-    const float2 *chi_df = nullptr;  // chi as FP32 pairs (pair-arithmetic projection)
+    // chi on a 46-bit grid per (atom, l) for the integer projection: per entry (a_0..a_3),
+    // (b_0..b_3) with chi_l = 2^(F-46) (a_l 2^23 + b_l); chi_F: F per (atom, l)
+    const int4 *chi_q = nullptr;
+    const int *chi_F = nullptr;
     const double *gchi = nullptr;    // 4 per entry: h^3 gamma_Jlm chi_Jlm
     const float *gchi_f = nullptr;
     const int *ent_atom = nullptr;   // atom of each entry
@@ -171,14 +174,18 @@ cudaError_t stencil_f32in_f64(const DevHam &H, const float *Y, double *out, int 
 
 // ---- nonlocal.cu ------------------------------------------------------------------
 // C[(J*4+lm)*ncols + c] = alpha * sum_{s in supp(J)} chi_Jlm(s) Y[idx(s) + c*ld]
-// (FP64 blocks: FP32-pair arithmetic, output as pairs; FP32 blocks: FP32)
-cudaError_t project_f64_df(const DevHam &H, const double *Y, int ncols, long ld, double alpha,
-                           float2 *C, cudaStream_t st);
+// (FP64 blocks: exact integer sums on the columns' grids (bY: the column bounds of Y),
+// output as FP32 pairs; FP32 blocks: FP32)
+cudaError_t project_f64_fx(const DevHam &H, const double *Y, int ncols, long ld, double alpha,
+                           const unsigned *bY, float2 *C, cudaStream_t st);
 cudaError_t project_f32(const DevHam &H, const float *Y, int ncols, long ld, double alpha,
                         float *C, cudaStream_t st);
 // the FP64 projection of an FP32 block (pairs, alpha = 1), for the pair scatter
-cudaError_t project_f32in_f64(const DevHam &H, const float *Y, int ncols, long ld, float2 *C,
-                              cudaStream_t st);
+cudaError_t project_f32in_f64(const DevHam &H, const float *Y, int ncols, long ld,
+                              const unsigned *bY, float2 *C, cudaStream_t st);
+// the integer grid of chi (DevHam::chi_q, chi_F) from chi
+cudaError_t chi_fixed(int natoms, const int *atom_ptr, const double *chi, int4 *chi_q,
+                      int *chi_F, cudaStream_t st);
 // node-ordered entry tables of the scatter kernels
 cudaError_t build_nl_node_tables(long nuniq, const int *uniq_ptr, const int *ent_list,
                                  const int *ent_atom, const double *gchi, int *nl_atom,
@@ -203,8 +210,6 @@ cudaError_t build_inverse_map(long nd, long nsup, const int *idx, int *node_cnt,
                               cudaStream_t st);
 cudaError_t exclusive_scan_int(const int *in, int *out, long n, int *tmp, cudaStream_t st);
 cudaError_t to_float(const double *in, float *out, long n, cudaStream_t st);
-// out[i] = (hi, lo) FP32 pair of in[i] (stencil_df.cu)
-cudaError_t to_float_pair(const double *in, float2 *out, long n, cudaStream_t st);
 
 // ---- gram.cu --------------------------------------------------------------------
 // G (ns x ns, column-major, FP64) = A^T B over nd rows; A, B column-major with lda/ldb.

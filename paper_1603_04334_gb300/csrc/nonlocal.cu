@@ -157,106 +157,190 @@ cudaError_t project_f32(const DevHam &H, const float *Y, int ncols, long ld, dou
 {
     return project<float, float, true>(H, Y, ncols, ld, H.chi_f, C, (float)alpha, st);
 }
-// ---- FP64 arithmetic in FP32 pairs (see df.cuh) -----------------------------------------
-// Projection with compensated products; each thread's partial sums over its share of the
-// support are combined across the CTA with pair additions (TwoSum). The result is written
-// as FP32 pairs, scaled by `alpha` (the filter step's factor), for the pair scatter. T: the
-// block's type (FP64 blocks, or the FP32 block to which the mixed-precision Rayleigh-Ritz
-// step applies H in FP64; an FP32 value is the pair (y, 0)).
+// ---- FP64 projection in exact integer arithmetic ---------------------------------------
+// Each column of Y is put on its 49-bit grid (fx_split: y = 2^(E-49) (d 2^23 + r), E from
+// the column bound) and each projector l of atom J on a 46-bit grid of its own (chi =
+// 2^(F-46) (a 2^23 + b), F from max |chi_Jl| over the support, a and b integers below 2^23
+// in magnitude). Then
+//   chi y = 2^(E+F-95) (a d 2^46 + (a r + b d) 2^23 + b r),
+// and the kernel sums a d and a r + b d exactly in two int64 accumulators per (l, column);
+// only b r is dropped (below 2^-49 of the largest product), so C is the projection of the
+// two grids to about 2^-48 of sum |chi y|, with no rounding along the support (compensated
+// FP32-pair sums lose about 2^-44 of it to cancellation). Integer sums do not depend on
+// their order; the per-warp sums are combined across the CTA in FP64 in a fixed order. The
+// result is alpha C as an FP32 pair, for the pair scatter.
+// chi_q: per entry two int4, (a_0..a_3) then (b_0..b_3); chi_F: per (atom, l) the exponent F.
+
+// chi_q and chi_F from chi. CTA: one atom; F from the largest high word of |chi| per l.
+__global__ void __launch_bounds__(256)
+k_chi_fixed(const int *__restrict__ atom_ptr, const double *__restrict__ chi, int4 *chi_q,
+            int *chi_F)
+{
+    __shared__ unsigned mx[4];
+    const int J = blockIdx.x;
+    const int b = atom_ptr[J], e = atom_ptr[J + 1];
+    if (threadIdx.x < 4) mx[threadIdx.x] = 0u;
+    __syncthreads();
+    unsigned m[4] = {0u, 0u, 0u, 0u};
+    for (int s = b + threadIdx.x; s < e; s += blockDim.x)
+#pragma unroll
+        for (int l = 0; l < 4; ++l) m[l] = max(m[l], abs_hi_word(chi[4L * s + l]));
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        const unsigned w = __reduce_max_sync(0xffffffffu, m[l]);
+        if ((threadIdx.x & 31) == 0) atomicMax(&mx[l], w);
+    }
+    __syncthreads();
+    int F[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) F[l] = mx[l] ? bound_exponent(mx[l]) : 0;
+    if (threadIdx.x < 4) chi_F[4 * J + threadIdx.x] = F[threadIdx.x];
+    for (int s = b + threadIdx.x; s < e; s += blockDim.x) {
+        int qa[4], qb[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            // |chi| 2^(46 - F) < 2^46, rounded to an integer (a power-of-two scaling is exact)
+            const double c = chi[4L * s + l];
+            const long long A = llrint(fabs(ldexp(c, 46 - F[l])));
+            const int sg = c < 0.0 ? -1 : 1;
+            qa[l] = sg * (int)(A >> 23);
+            qb[l] = sg * (int)(A & 0x7fffff);
+        }
+        chi_q[2L * s] = make_int4(qa[0], qa[1], qa[2], qa[3]);
+        chi_q[2L * s + 1] = make_int4(qb[0], qb[1], qb[2], qb[3]);
+    }
+}
+
+cudaError_t chi_fixed(int natoms, const int *atom_ptr, const double *chi, int4 *chi_q,
+                      int *chi_F, cudaStream_t st)
+{
+    if (natoms <= 0) return cudaSuccess;
+    k_chi_fixed<<<natoms, 256, 0, st>>>(atom_ptr, chi, chi_q, chi_F);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// One CTA per (atom, CB columns); T: the block's type (FP64, or the FP32 block to which the
+// mixed-precision Rayleigh-Ritz step applies H in FP64). bY: the columns' bounds.
 // Grid as k_project: x = atom, y = column block.
 template <typename T, int CB, int NT>
-__global__ void __launch_bounds__(NT, 4)
-k_project_df(const T *__restrict__ Y, long ld, int ncols, const int *__restrict__ atom_ptr,
-             const int *__restrict__ idx, const float2 *__restrict__ chi, float2 *__restrict__ C,
-             float alh, float all)
+__global__ void __launch_bounds__(NT, 3)
+k_project_fx(const T *__restrict__ Y, long ld, int ncols, const int *__restrict__ atom_ptr,
+             const int *__restrict__ idx, const int4 *__restrict__ chi_q,
+             const int *__restrict__ chi_F, const unsigned *__restrict__ bY, double alpha,
+             float2 *__restrict__ C)
 {
-    __shared__ float2 red[NT / 32][4 * CB];
+    __shared__ double red[NT / 32][8 * CB];
     const int J = blockIdx.x;
     const int c0 = blockIdx.y * CB;
     const int b = atom_ptr[J], e = atom_ptr[J + 1];
-    float sh[4][CB], sl[4][CB];
+    int E[CB];
+#pragma unroll
+    for (int cb = 0; cb < CB; ++cb) E[cb] = c0 + cb < ncols ? bound_exponent(bY[c0 + cb]) : 0;
+    long long hi[4][CB], lo[4][CB];
 #pragma unroll
     for (int l = 0; l < 4; ++l)
 #pragma unroll
-        for (int cb = 0; cb < CB; ++cb) sh[l][cb] = sl[l][cb] = 0.0f;
-#pragma unroll 4
-    for (int s = b + threadIdx.x; s < e; s += NT) {
-        const long p = idx[s];
-        float2 x[4];
-#pragma unroll
-        for (int l = 0; l < 4; ++l) x[l] = chi[4 * (long)s + l];
+        for (int cb = 0; cb < CB; ++cb) hi[l][cb] = lo[l][cb] = 0;
+    // two entries per trip, their node indices loaded one trip ahead: 2 CB independent loads
+    // of Y in flight per thread instead of an index -> value chain
+    auto acc = [&](const T (&y)[CB], int4 qa, int4 qb) {
+        const int a[4] = {qa.x, qa.y, qa.z, qa.w}, bb[4] = {qb.x, qb.y, qb.z, qb.w};
 #pragma unroll
         for (int cb = 0; cb < CB; ++cb) {
-            if (c0 + cb < ncols) {
-                const float2 y = split_double(Y[p + (long)(c0 + cb) * ld]);
+            const int2 q = fx_split(y[cb], E[cb]);
 #pragma unroll
-                for (int l = 0; l < 4; ++l) mac(x[l], y, sh[l][cb], sl[l][cb]);
+            for (int l = 0; l < 4; ++l) {
+                hi[l][cb] += (long long)a[l] * q.x;
+                lo[l][cb] += (long long)a[l] * q.y + (long long)bb[l] * q.x;
             }
         }
+    };
+    int s = b + threadIdx.x;
+    long pa = s < e ? idx[s] : 0, pb = s + NT < e ? idx[s + NT] : 0;
+    for (; s < e; s += 2 * NT) {
+        const bool vb = s + NT < e;
+        T ya[CB], yb[CB];
+#pragma unroll
+        for (int cb = 0; cb < CB; ++cb) {
+            const bool vc = c0 + cb < ncols;
+            ya[cb] = vc ? Y[pa + (long)(c0 + cb) * ld] : (T)0;
+            yb[cb] = (vc && vb) ? Y[pb + (long)(c0 + cb) * ld] : (T)0;
+        }
+        const int4 qa = chi_q[2L * s], qb = chi_q[2L * s + 1];
+        const int4 z = make_int4(0, 0, 0, 0);
+        const int4 ra = vb ? chi_q[2L * (s + NT)] : z, rb = vb ? chi_q[2L * (s + NT) + 1] : z;
+        const int sn = s + 2 * NT;
+        pa = sn < e ? idx[sn] : 0;
+        pb = sn + NT < e ? idx[sn + NT] : 0;
+        acc(ya, qa, qb);
+        acc(yb, ra, rb);
     }
+    // |a d| and |a r + b d| are below 2^50: a thread's sums stay below 2^(50 + log2 t) for t
+    // entries; before the 32-way warp sum they are shifted right by max(0, log2 t - 7) so that
+    // it stays below 2^62 (for supports up to 32768 entries per atom no shift is needed)
+    const int t = (e - b + NT - 1) / NT;
+    const int sh = t > 128 ? (32 - __clz(t - 1)) - 7 : 0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int l = 0; l < 4; ++l)
 #pragma unroll
         for (int cb = 0; cb < CB; ++cb) {
-            float h = sh[l][cb], lo = sl[l][cb];
+            long long h = hi[l][cb] >> sh, g = lo[l][cb] >> sh;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
-                const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-                float t, err;
-                two_sum(h, h2, t, err);
-                h = t;
-                lo = (lo + l2) + err;
+                h += __shfl_xor_sync(0xffffffffu, h, o);
+                g += __shfl_xor_sync(0xffffffffu, g, o);
             }
-            if (lane == 0) red[wid][l * CB + cb] = make_float2(h, lo);
+            if (lane == 0) {
+                red[wid][(l * CB + cb) * 2] = (double)h;
+                red[wid][(l * CB + cb) * 2 + 1] = (double)g;
+            }
         }
     __syncthreads();
     if (threadIdx.x < 4 * CB) {
         const int l = threadIdx.x / CB, cb = threadIdx.x % CB;
-        float h = 0.0f, lo = 0.0f;
+        double h = 0.0, g = 0.0;
 #pragma unroll
         for (int w = 0; w < NT / 32; ++w) {
-            const float2 v = red[w][threadIdx.x];
-            float t, err;
-            two_sum(h, v.x, t, err);
-            h = t;
-            lo = (lo + v.y) + err;
+            h += red[w][threadIdx.x * 2];
+            g += red[w][threadIdx.x * 2 + 1];
         }
-        // alpha * (h + lo), renormalised
-        float ph = 0.0f, pl = 0.0f;
-        mac(make_float2(h, lo), make_float2(alh, all), ph, pl);
-        float t, err;
-        two_sum(ph, pl, t, err);
-        if (c0 + cb < ncols) C[(long)(J * 4 + l) * ncols + c0 + cb] = make_float2(t, err);
+        if (c0 + cb < ncols) {
+            // alpha 2^(E+F-49+sh) (h + 2^-23 g); a column whose bound is not finite gives NaN
+            const unsigned u = bY[c0 + cb];
+            double v = alpha * ldexp(fma(g, 0x1p-23, h), E[cb] + chi_F[4 * J + l] - 49 + sh);
+            if (((u >> 20) & 0x7ffu) == 0x7ffu) v = __longlong_as_double(0x7ff8000000000000ll);
+            const float vh = (float)v;
+            C[(long)(J * 4 + l) * ncols + c0 + cb] = make_float2(vh, (float)(v - (double)vh));
+        }
     }
 }
 
 template <typename T>
-static cudaError_t project_df(const DevHam &H, const T *Y, int ncols, long ld, double alpha,
-                              float2 *C, cudaStream_t st)
+static cudaError_t project_fx(const DevHam &H, const T *Y, int ncols, long ld, double alpha,
+                              const unsigned *bY, float2 *C, cudaStream_t st)
 {
     if (H.natoms == 0 || ncols <= 0) return cudaSuccess;
     constexpr int CB = 2, NT = 256;
     dim3 grid(H.natoms, (ncols + CB - 1) / CB);
-    if (grid.y > 65535) return cudaErrorInvalidValue;
-    const float alh = (float)alpha, all = (float)(alpha - (double)alh);
-    k_project_df<T, CB, NT><<<grid, NT, 0, st>>>(Y, ld, ncols, H.atom_ptr, H.idx, H.chi_df, C,
-                                                 alh, all);
+    if (grid.y > 65535 || !bY) return cudaErrorInvalidValue;
+    k_project_fx<T, CB, NT><<<grid, NT, 0, st>>>(Y, ld, ncols, H.atom_ptr, H.idx, H.chi_q,
+                                                 H.chi_F, bY, alpha, C);
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t project_f64_df(const DevHam &H, const double *Y, int ncols, long ld, double alpha,
-                           float2 *C, cudaStream_t st)
+cudaError_t project_f64_fx(const DevHam &H, const double *Y, int ncols, long ld, double alpha,
+                           const unsigned *bY, float2 *C, cudaStream_t st)
 {
-    return project_df<double>(H, Y, ncols, ld, alpha, C, st);
+    return project_fx<double>(H, Y, ncols, ld, alpha, bY, C, st);
 }
 
-cudaError_t project_f32in_f64(const DevHam &H, const float *Y, int ncols, long ld, float2 *C,
-                              cudaStream_t st)
+cudaError_t project_f32in_f64(const DevHam &H, const float *Y, int ncols, long ld,
+                              const unsigned *bY, float2 *C, cudaStream_t st)
 {
-    return project_df<float>(H, Y, ncols, ld, 1.0, C, st);
+    return project_fx<float>(H, Y, ncols, ld, 1.0, bY, C, st);
 }
 
 constexpr int kScatNodes = 256;     // covered nodes (threads) per CTA of the FP32 scatter

@@ -61,7 +61,9 @@ struct sparc_ctx {
     double *chi = nullptr, *gchi = nullptr;
     float *chi_f = nullptr, *gchi_f = nullptr;
     int *uniq_node = nullptr, *uniq_ptr = nullptr, *ent_list = nullptr;
-    float2 *chi_df = nullptr, *nl_gdf = nullptr;
+    float2 *nl_gdf = nullptr;
+    int4 *chi_q = nullptr;
+    int *chi_F = nullptr;
     int *nl_atom = nullptr;
     float *nl_gf = nullptr;
 
@@ -276,7 +278,7 @@ sparc_status step_f64(sparc_ctx *ctx, const double *Y, const double *Yprev, doub
     { PHASE(SPARC_PHASE_OTHER); TRY(scaled_potential(ctx, alpha, shift, &u)); }
     if (H.natoms > 0) {
         TRY(ensure_C(ctx, ncols));
-        { PHASE(SPARC_PHASE_PROJECT); CK(project_f64_df(H, Y, ncols, ld, alpha, (float2 *)ctx->C, ctx->st)); }
+        { PHASE(SPARC_PHASE_PROJECT); CK(project_f64_fx(H, Y, ncols, ld, alpha, bY, (float2 *)ctx->C, ctx->st)); }
     }
     { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f64(H, Y, Yprev, out, ncols, ld, alpha, u, beta, bY, bOut, ctx->st)); }
     if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f64_df(H, (const float2 *)ctx->C, out, ncols, ld, bOut, ctx->st)); }
@@ -300,12 +302,12 @@ sparc_status step_f32(sparc_ctx *ctx, const float *Y, const float *Yprev, float 
 sparc_status apply_f32in_f64(sparc_ctx *ctx, const float *Y, double *out, int ncols, long ld)
 {
     const DevHam &H = ctx->H;
-    if (H.natoms > 0) {
-        TRY(ensure_C(ctx, ncols));
-        { PHASE(SPARC_PHASE_PROJECT); CK(project_f32in_f64(H, Y, ncols, ld, (float2 *)ctx->C, ctx->st)); }
-    }
     unsigned *bY = nullptr;
     TRY(scratch_bounds(ctx, Y, ncols, ld, &bY));
+    if (H.natoms > 0) {
+        TRY(ensure_C(ctx, ncols));
+        { PHASE(SPARC_PHASE_PROJECT); CK(project_f32in_f64(H, Y, ncols, ld, bY, (float2 *)ctx->C, ctx->st)); }
+    }
     { PHASE(SPARC_PHASE_STENCIL); CK(stencil_f32in_f64(H, Y, out, ncols, ld, bY, ctx->st)); }
     if (H.natoms > 0) { PHASE(SPARC_PHASE_SCATTER); CK(scatter_f64_df(H, (const float2 *)ctx->C, out, ncols, ld, nullptr, ctx->st)); }
     return SPARC_OK;
@@ -588,7 +590,7 @@ void free_ctx(sparc_ctx *c)
 {
     if (!c) return;
     void *ps[] = {c->V, c->Vf, c->atom_ptr, c->idx, c->ent_atom, c->chi, c->gchi, c->chi_f,
-                  c->gchi_f, c->chi_df, c->uniq_node, c->uniq_ptr, c->ent_list, c->nl_atom, c->nl_gf, c->nl_gdf, c->C, c->hx, c->rotx, c->roth, c->part,
+                  c->gchi_f, c->chi_q, c->chi_F, c->uniq_node, c->uniq_ptr, c->ent_list, c->nl_atom, c->nl_gf, c->nl_gdf, c->C, c->hx, c->rotx, c->roth, c->part,
                   c->tcws, c->dm, c->lz, c->bnd, c->bsc, c->vc, c->flags, c->obs, c->pois};
     for (void *p : ps) dfree(p);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -661,16 +663,18 @@ sparc_status build_tables(sparc_ctx *ctx, const sparc_atoms *at)
     for (void *p : {(void *)R, (void *)G, (void *)counts, (void *)node_cnt, (void *)node_start,
                     (void *)cursor, (void *)flags, (void *)rank, (void *)scan_tmp})
         CK(cudaFree(p));
-    // pair copy of chi (pair-arithmetic projection) and the node-ordered entry tables of
-    // the scatter kernels
-    TRY(dmalloc(ctx, ctx->chi_df, 4 * tot));
-    CK(to_float_pair(ctx->chi, ctx->chi_df, 4 * tot, ctx->st));
+    // chi on its integer grid (FP64 projection) and the node-ordered entry tables of the
+    // scatter kernels
+    TRY(dmalloc(ctx, ctx->chi_q, 2 * tot));
+    TRY(dmalloc(ctx, ctx->chi_F, 4 * (long)H.natoms));
+    CK(chi_fixed(H.natoms, ctx->atom_ptr, ctx->chi, ctx->chi_q, ctx->chi_F, ctx->st));
     TRY(dmalloc(ctx, ctx->nl_atom, tot));
     TRY(dmalloc(ctx, ctx->nl_gf, 4 * tot));
     TRY(dmalloc(ctx, ctx->nl_gdf, 4 * tot));
     CK(build_nl_node_tables(nuniq, ctx->uniq_ptr, ctx->ent_list, ctx->ent_atom, ctx->gchi,
                             ctx->nl_atom, ctx->nl_gf, ctx->nl_gdf, ctx->st));
-    H.chi_df = ctx->chi_df;
+    H.chi_q = ctx->chi_q;
+    H.chi_F = ctx->chi_F;
     H.nl_atom = ctx->nl_atom;
     H.nl_gf = ctx->nl_gf;
     H.nl_gdf = ctx->nl_gdf;

@@ -121,6 +121,40 @@ def test_apply_H_f64_ragged_grids(n3, natoms):
     ctx.close()
 
 
+@pytest.mark.parametrize("h,ncols", [(0.45, 5), (0.15, 3)])
+def test_nonlocal_part_f64_alone(h, ncols):
+    # H with the kinetic part off and V = 0 is V_nl alone, so its FP64 projection and
+    # scatter are compared with the oracle directly (random columns: their projections
+    # cancel strongly, so the sums must be exact), on two overlapping supports and on one
+    # support of about 33 500 entries (radius 20 grid spacings at h = 0.15: more than 128
+    # per thread of the projection's 256-thread CTA, the pre-shifted warp sum).
+    n3 = (48, 48, 48) if h < 0.2 else (23, 19, 21)
+    nd = n3[0] * n3[1] * n3[2]
+    rng = np.random.default_rng(int(h * 100))
+    c = np.array([(n3[0] - 1) * h / 2, (n3[1] - 1) * h / 2, (n3[2] - 1) * h / 2])
+    R = np.vstack([c, c + [0.7, -0.4, 0.3]]) if h > 0.2 else c.reshape(1, 3)
+    gamma = rng.uniform(-2, 2, (R.shape[0], 4))
+    V = np.zeros(nd)
+    H = oracle.Hamiltonian(n3, h, V, R, gamma, kscale=0.0)
+    ctx = sparc.Context(n3, h, R, None, gamma, veff=V)
+    ctx.set_kinetic_scale(0.0)
+    if h < 0.2:
+        assert ctx.info()["nsupport"] > 32768
+    X = rng.uniform(-0.5, 0.5, (ncols, nd))
+    # a column far below the others' scale (its coefficients stay within the FP32 range of
+    # the pair scatter's coefficients)
+    X[-1] *= 1e-20
+    ref = H.apply(X)
+    Xd = to_dev(X)
+    HXd = torch.empty_like(Xd)
+    ctx.apply_H(Xd, HXd)
+    got = HXd.cpu().numpy()
+    assert np.abs(ref).max() > 0.0
+    for j in range(ncols):
+        assert nrm_err(got[j:j + 1], ref[j:j + 1]) <= 1e-12
+    ctx.close()
+
+
 def test_apply_H_f32(c24):
     w, cl, H, ctx = c24
     X = synth.initial_block(5, w.nd, 4)
