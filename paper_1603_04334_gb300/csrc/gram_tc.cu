@@ -303,39 +303,45 @@ k_tc_digits_t(const T *__restrict__ Y, long ld, long nd, int ns, long nstep,
     const int e = mx == 0 ? 0 : (bxm == 0 ? 2 - B::kBias : bxm - B::kBias + 1);
     if (g == 0 && row < nd_pad) E[chunk * nd_pad + row] = bad ? kNonFinite : e;
     if (row >= nd_pad) return;
-    int d[C::kDigits][8];
+    // each value's magnitude on the grid and its sign; the digits are then peeled off from
+    // the bottom and each digit's 8 values stored at once (16 bytes: the 8 K-adjacent
+    // elements of a core-matrix row; the 32 rows of a warp fill 512 contiguous bytes)
+    long N[8];
+    unsigned neg = 0u;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         const U mag = B::mag(x[t]);
-        long N = 0;
+        N[t] = 0;
         if (!bad && mag != 0) {
             const int bx = (int)(mag >> B::kMant);
             const U m = (mag & (((U)1 << B::kMant) - 1)) | (bx ? ((U)1 << B::kMant) : 0);
             const int ebx = bx ? bx : 1;
             const int sh = e + B::kBias + B::kMant - C::kBits - ebx;
             if (sh <= 0)
-                N = (long)m << (-sh);
+                N[t] = (long)m << (-sh);
             else if (sh < 8 * (int)sizeof(U))
-                N = (long)((m + ((U)1 << (sh - 1))) >> sh);
+                N[t] = (long)((m + ((U)1 << (sh - 1))) >> sh);
         }
-        const int sg = B::neg(x[t]) ? -1 : 1;
-        constexpr long kHalf = 1L << (C::kBase - 1), kMask = (1L << C::kBase) - 1;
-#pragma unroll
-        for (int s2 = C::kDigits - 1; s2 > 0; --s2) {
-            const int v = (int)(((N + kHalf) & kMask) - kHalf);
-            d[s2][t] = sg * v;
-            N = (N - v) >> C::kBase;
-        }
-        d[0][t] = sg * (int)N;
+        neg |= (B::neg(x[t]) ? 1u : 0u) << t;
     }
     // the 8 columns kb .. kb+7 lie in one K-step (kStep is a multiple of 8) and one core
     const int cb = (int)(row >> 7), c = (int)(row & 127);
     const long base = blob_offset<C>(cb, kb / C::kStep, 0, nstep) + in_blob(kb % C::kStep, c);
+    constexpr long kHalf = 1L << (C::kBase - 1), kMask = (1L << C::kBase) - 1;
 #pragma unroll
-    for (int s2 = 0; s2 < C::kDigits; ++s2) {
+    for (int s2 = C::kDigits - 1; s2 >= 0; --s2) {
         __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) v[t] = __float2bfloat16_rn((float)d[s2][t]);
+        for (int t = 0; t < 8; ++t) {
+            int dv;
+            if (s2 > 0) {
+                dv = (int)(((N[t] + kHalf) & kMask) - kHalf);
+                N[t] = (N[t] - dv) >> C::kBase;
+            } else {
+                dv = (int)N[t];
+            }
+            v[t] = __float2bfloat16_rn((float)(((neg >> t) & 1u) ? -dv : dv));
+        }
         *reinterpret_cast<uint4 *>(D + base + (long)s2 * TcDims<C>::kBlobElems) =
             *reinterpret_cast<const uint4 *>(v);
     }
