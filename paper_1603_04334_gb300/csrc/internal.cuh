@@ -307,8 +307,8 @@ cudaError_t dense_syev(double *A, int ns, const int *ns_dev, double *ev, double 
 // ---- jacobi.cu --------------------------------------------------------------------
 // Grid-wide barrier state (zeroed before each cooperative launch).
 struct GridBarrier {
-    unsigned count;
-    unsigned gen;
+    unsigned count;  // arrivals since the barrier was zeroed (grid.cuh)
+    unsigned gen;    // unused
     int err;
     int pad;
 };

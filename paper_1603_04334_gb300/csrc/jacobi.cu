@@ -54,7 +54,7 @@ __device__ __forceinline__ void pair_of(int r, int k, int m, int &p, int &q)
 // T = double: the eigensolve; T = float: the FP32 pre-solve of the mixed-precision
 // eigensolve (dense.cu), with eps the unit roundoff of T.
 template <typename T>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 1)
 k_jacobi_grid(T *A0, T *A1, T *V, T *diag, int n, GridBarrier *bar, int *status,
               int *sweeps_out, double eps, int max_sweeps)
 {
@@ -112,9 +112,13 @@ k_jacobi_grid(T *A0, T *A1, T *V, T *diag, int n, GridBarrier *bar, int *status,
             // a round without rotations leaves A and V as they are; every CTA computed the
             // same angles from the same copy, so all of them skip it (and its barrier)
             if (!round_rot) continue;
-            // 2 x 2 blocks: next = J_1^T cur J_2 (every entry of next is written)
+            // 2 x 2 blocks: next = J_1^T cur J_2. A is symmetric, so block (k2, k1) of next is
+            // the transpose of block (k1, k2): only k1 <= k2 is computed and written to both
+            // places (every entry of next is written; half the FP64 work of computing all
+            // blocks, and next stays exactly symmetric)
             for (long b = gtid; b < (long)half * half; b += gstride) {
                 const int k1 = (int)(b % half), k2 = (int)(b / half);
+                if (k1 > k2) continue;
                 const int p1 = sp[k1], q1 = sq[k1], p2 = sp[k2], q2 = sq[k2];
                 const bool v1 = q1 < n, v2 = q2 < n;
                 const T c1 = sc[k1], s1 = ss[k1], c2 = sc[k2], s2 = ss[k2];
@@ -124,10 +128,18 @@ k_jacobi_grid(T *A0, T *A1, T *V, T *diag, int n, GridBarrier *bar, int *status,
                 const T aqq = (v1 && v2) ? __ldcg(cur + q1 + (long)q2 * n) : (T)0;
                 const T bpp = c1 * app - s1 * aqp, bpq = c1 * apq - s1 * aqq;
                 const T bqp = s1 * app + c1 * aqp, bqq = s1 * apq + c1 * aqq;
-                nxt[p1 + (long)p2 * n] = c2 * bpp - s2 * bpq;
-                if (v2) nxt[p1 + (long)q2 * n] = s2 * bpp + c2 * bpq;
-                if (v1) nxt[q1 + (long)p2 * n] = c2 * bqp - s2 * bqq;
-                if (v1 && v2) nxt[q1 + (long)q2 * n] = s2 * bqp + c2 * bqq;
+                const T npp = c2 * bpp - s2 * bpq, npq = s2 * bpp + c2 * bpq;
+                const T nqp = c2 * bqp - s2 * bqq, nqq = s2 * bqp + c2 * bqq;
+                nxt[p1 + (long)p2 * n] = npp;
+                if (v2) nxt[p1 + (long)q2 * n] = npq;
+                if (v1) nxt[q1 + (long)p2 * n] = nqp;
+                if (v1 && v2) nxt[q1 + (long)q2 * n] = nqq;
+                if (k1 != k2) {
+                    nxt[p2 + (long)p1 * n] = npp;
+                    if (v2) nxt[q2 + (long)p1 * n] = npq;
+                    if (v1) nxt[p2 + (long)q1 * n] = nqp;
+                    if (v1 && v2) nxt[q2 + (long)q1 * n] = nqq;
+                }
             }
             // V <- V J, columns p, q of each rotated pair
             for (long t = gtid; t < (long)half * n; t += gstride) {
