@@ -24,6 +24,7 @@
 #include "internal.cuh"
 
 #include <atomic>
+#include <type_traits>
 
 namespace sparc {
 
@@ -31,6 +32,12 @@ namespace {
 constexpr int NT = 256;
 constexpr int kMaxSweeps = 60;
 constexpr double kEps = 2.220446049250313e-16;
+// CTAs of a grid Jacobi, at most. A round streams all of A and V through L2; the FP32
+// pre-solve's rounds go faster with two CTAs per SM (more loads in flight: 197 against
+// 213 ms per Ns = 1024 dense step; one per SM: 274 ms with 76 CTAs), the FP64 ones, bound
+// by the FP64 pipe, gain nothing from a second CTA per SM.
+constexpr int kJacobiCtasF32 = 304;
+constexpr int kJacobiCtasF64 = 152;
 
 __device__ __forceinline__ void pair_of(int r, int k, int m, int &p, int &q)
 {
@@ -196,7 +203,8 @@ static cudaError_t jacobi_grid_t(T *A0, T *A1, T *V, T *diag, int n, GridBarrier
     if (want < 1) want = 1;
     const int cb = coop_blocks.load(std::memory_order_acquire);
     int G = (int)(want < cb ? want : cb);
-    if (G > 152) G = 152;
+    const int cap = std::is_same<T, float>::value ? kJacobiCtasF32 : kJacobiCtasF64;
+    if (G > cap) G = cap;
     cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st);
     if (e != cudaSuccess) return e;
     void *args[] = {&A0, &A1, &V, &diag, &n, &bar, &status, &sweeps_out, &eps, &max_sweeps};
