@@ -42,6 +42,7 @@ struct DevHam {
     // (b_0..b_3) with chi_l = 2^(F-46) (a_l 2^23 + b_l); chi_F: F per (atom, l)
     const int4 *chi_q = nullptr;
     const int *chi_F = nullptr;
+    const int *proj_order = nullptr; // natoms: the projections' atom order (spatial)
     const double *gchi = nullptr;    // 4 per entry: h^3 gamma_Jlm chi_Jlm
     const float *gchi_f = nullptr;
     const int *ent_atom = nullptr;   // atom of each entry

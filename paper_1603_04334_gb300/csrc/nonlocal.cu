@@ -103,13 +103,16 @@ __device__ __forceinline__ void project_block(const T *__restrict__ Y, long ld, 
 
 // Grid: x = atom (dispatched first: the CTAs resident at one time read the supports of
 // many atoms for the same columns, so the nodes that several supports share are read from
-// DRAM about once), y = column block.
+// DRAM about once), y = column block. order (optional): the atoms in a spatial order, so
+// that CTAs dispatched together gather overlapping supports (and the DRAM granules that the
+// short x-runs of one support fetch only in part serve its neighbours).
 template <typename T, typename TC, int CB, int NT, bool ILV>
 __global__ void __launch_bounds__(NT)
 k_project(const T *__restrict__ Y, long ld, int ncols, const int *__restrict__ atom_ptr,
-          const int *__restrict__ idx, const TC *__restrict__ chi, TC *__restrict__ C, TC alpha)
+          const int *__restrict__ idx, const TC *__restrict__ chi, TC *__restrict__ C, TC alpha,
+          const int *__restrict__ order)
 {
-    const int J = blockIdx.x;
+    const int J = order ? order[blockIdx.x] : (int)blockIdx.x;
     project_block<T, TC, CB, NT, ILV>(Y, ld, ncols, J, atom_ptr[J], atom_ptr[J + 1],
                                       blockIdx.y * CB, idx, chi, C, alpha);
 }
@@ -147,7 +150,7 @@ static cudaError_t project(const DevHam &H, const T *Y, int ncols, long ld, cons
     dim3 grid(H.natoms, (ncols + CB - 1) / CB);
     if (grid.y > 65535) return cudaErrorInvalidValue;
     k_project<T, TC, CB, NT, ILV>
-        <<<grid, NT, 0, st>>>(Y, ld, ncols, H.atom_ptr, H.idx, chi, C, alpha);
+        <<<grid, NT, 0, st>>>(Y, ld, ncols, H.atom_ptr, H.idx, chi, C, alpha, H.proj_order);
     note_launch();
     return cudaGetLastError();
 }
@@ -222,16 +225,16 @@ cudaError_t chi_fixed(int natoms, const int *atom_ptr, const double *chi, int4 *
 
 // One CTA per (atom, CB columns); T: the block's type (FP64, or the FP32 block to which the
 // mixed-precision Rayleigh-Ritz step applies H in FP64). bY: the columns' bounds.
-// Grid as k_project: x = atom, y = column block.
+// Grid as k_project: x = atom (in the spatial order), y = column block.
 template <typename T, int CB, int NT>
 __global__ void __launch_bounds__(NT, 3)
 k_project_fx(const T *__restrict__ Y, long ld, int ncols, const int *__restrict__ atom_ptr,
              const int *__restrict__ idx, const int4 *__restrict__ chi_q,
              const int *__restrict__ chi_F, const unsigned *__restrict__ bY, double alpha,
-             float2 *__restrict__ C)
+             float2 *__restrict__ C, const int *__restrict__ order)
 {
     __shared__ double red[NT / 32][8 * CB];
-    const int J = blockIdx.x;
+    const int J = order ? order[blockIdx.x] : (int)blockIdx.x;
     const int c0 = blockIdx.y * CB;
     const int b = atom_ptr[J], e = atom_ptr[J + 1];
     int E[CB];
@@ -326,7 +329,7 @@ static cudaError_t project_fx(const DevHam &H, const T *Y, int ncols, long ld, d
     dim3 grid(H.natoms, (ncols + CB - 1) / CB);
     if (grid.y > 65535 || !bY) return cudaErrorInvalidValue;
     k_project_fx<T, CB, NT><<<grid, NT, 0, st>>>(Y, ld, ncols, H.atom_ptr, H.idx, H.chi_q,
-                                                 H.chi_F, bY, alpha, C);
+                                                 H.chi_F, bY, alpha, C, H.proj_order);
     note_launch();
     return cudaGetLastError();
 }

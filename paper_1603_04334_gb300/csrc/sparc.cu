@@ -8,6 +8,7 @@
 #include "sparc.h"
 #include "internal.cuh"
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <cmath>
@@ -64,6 +65,7 @@ struct sparc_ctx {
     float2 *nl_gdf = nullptr;
     int4 *chi_q = nullptr;
     int *chi_F = nullptr;
+    int *proj_order = nullptr;   // atoms in Morton order of their cells (projections)
     int *nl_atom = nullptr;
     float *nl_gf = nullptr;
 
@@ -590,7 +592,7 @@ void free_ctx(sparc_ctx *c)
 {
     if (!c) return;
     void *ps[] = {c->V, c->Vf, c->atom_ptr, c->idx, c->ent_atom, c->chi, c->gchi, c->chi_f,
-                  c->gchi_f, c->chi_q, c->chi_F, c->uniq_node, c->uniq_ptr, c->ent_list, c->nl_atom, c->nl_gf, c->nl_gdf, c->C, c->hx, c->rotx, c->roth, c->part,
+                  c->gchi_f, c->chi_q, c->chi_F, c->proj_order, c->uniq_node, c->uniq_ptr, c->ent_list, c->nl_atom, c->nl_gf, c->nl_gdf, c->C, c->hx, c->rotx, c->roth, c->part,
                   c->tcws, c->dm, c->lz, c->bnd, c->bsc, c->vc, c->flags, c->obs, c->pois};
     for (void *p : ps) dfree(p);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -629,6 +631,30 @@ sparc_status build_tables(sparc_ctx *ctx, const sparc_atoms *at)
         ptr[J + 1] = (int)tot;
     }
     H.nsup = tot;
+    {   // the projections' CTA order: atoms sorted by the Morton code of their cell (cells
+        // of 2 rcut), so that atoms whose supports overlap are gathered at about the same time
+        std::vector<std::pair<unsigned long long, int>> key(na);
+        const double cell = 2.0 * at->rcut;
+        for (int J = 0; J < na; ++J) {
+            unsigned long long code = 0;
+            unsigned c3[3];
+            for (int d = 0; d < 3; ++d) {
+                const double v = at->R[3 * J + d] / cell;
+                c3[d] = v <= 0.0 ? 0u : (v >= 1048575.0 ? 1048575u : (unsigned)v);
+            }
+            for (int b = 19; b >= 0; --b)
+                for (int d = 2; d >= 0; --d) code = (code << 1) | ((c3[d] >> b) & 1u);
+            key[J] = {code, J};
+        }
+        std::sort(key.begin(), key.end());
+        std::vector<int> order(na);
+        for (int J = 0; J < na; ++J) order[J] = key[J].second;
+        TRY(dmalloc(ctx, ctx->proj_order, na));
+        CK(cudaMemcpyAsync(ctx->proj_order, order.data(), sizeof(int) * na,
+                           cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        H.proj_order = ctx->proj_order;
+    }
     TRY(dmalloc(ctx, ctx->atom_ptr, na + 1));
     CK(cudaMemcpyAsync(ctx->atom_ptr, ptr.data(), sizeof(int) * (na + 1), cudaMemcpyHostToDevice,
                        ctx->st));
