@@ -297,7 +297,7 @@ sparc_status sparc_sync(sparc_ctx *ctx);
  * which = 0: an mbarrier that expects two arrivals and receives one (the wait of the TMA
  * stencil pipeline); which = 1: a cooperative two-CTA grid barrier that expects three CTAs
  * (the barrier of the multi-SM Jacobi solver). Neither wait can complete; each gives up
- * after about 0.1 s. Returns SPARC_ERR_TIMEOUT when the kernel detected the expired wait
+ * after its poll limit (2^20 polls, well under a second). Returns SPARC_ERR_TIMEOUT when the kernel detected the expired wait
  * and reported it through the host (the expected result), SPARC_OK if the wait completed
  * (a defect), SPARC_ERR_ARG for another `which`. The context stays usable afterwards.
  * The paper has no counterpart. */
