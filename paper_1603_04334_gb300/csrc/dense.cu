@@ -307,7 +307,7 @@ k_dense_sort(int n, const double *diag, const double *V, double *ritz, double *Q
 }
 
 // ---- mixed-precision eigensolve of A = U^T H_s U (Ns > kMixedFrom) ----------------------
-// Cyclic Jacobi in FP32 first (64x the FP64 rate on GB300), its eigenvectors P made
+// Block Jacobi in FP32 first (jacobi.cu; 64x the FP64 rate on GB300), its eigenvectors P made
 // orthogonal to FP64 accuracy by two Newton-Schulz steps P <- P (3 I - P^T P) / 2, then the
 // FP64 Jacobi on A' = P^T A P, which is already diagonal to the FP32 level and converges in
 // a few sweeps (quadratically); the eigenvectors of A are P V'. The result is the FP64
@@ -356,7 +356,7 @@ cudaError_t dense_rr(double *M, double *Hs, int ns, double *ritz, double *Cf, do
     double *G = work + 6 * nn;    // P^T P / Newton-Schulz coefficients / A P / P V'
     double *P2 = work + 7 * nn;   // Newton-Schulz ping-pong
     float *A32 = (float *)(work + 8 * nn), *V32 = A32 + nn;
-    float *A32b = (float *)(work + 9 * nn), *D32 = A32b + nn;
+    float *A32b = (float *)(work + 9 * nn);
     double *diag = work + 10 * nn, *dinv = diag + ns, *odiag = dinv + ns;
     GridBarrier *bar = (GridBarrier *)(status + 8);
     int *status32 = status + 13;  // FP32 phase: running out of sweeps only shortens its help
@@ -406,8 +406,9 @@ cudaError_t dense_rr(double *M, double *Hs, int ns, double *ritz, double *Cf, do
         k_f64_to_f32<<<cg, 256, 0, st>>>(A, A32, nn);
         note_launch();
         if ((e = cudaMemsetAsync(status32, 0, sizeof(int), st)) != cudaSuccess) return e;
-        if ((e = jacobi_grid_f32(A32, A32b, V32, D32, ns, bar, status32, status + 14 + 1,
-                                 kMaxSweeps32, st)) != cudaSuccess)
+        // the block form (its scratch in the second FP32 buffer, which it does not need)
+        if ((e = block_jacobi_f32(A32, V32, ns, A32b, status + 14 + 1, kMaxSweeps32, st)) !=
+            cudaSuccess)
             return e;
         k_f32_to_f64<<<cg, 256, 0, st>>>(V32, P, nn);
         note_launch();

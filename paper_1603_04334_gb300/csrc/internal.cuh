@@ -318,10 +318,13 @@ struct GridBarrier {
 // sets *status = 3 if the sweeps do not converge; bar->err != 0 after a barrier timeout.
 cudaError_t jacobi_grid(double *A0, double *A1, double *V, double *diag, int n, GridBarrier *bar,
                         int *status, int *sweeps_out, cudaStream_t st);
-// The same in FP32 (the pre-solve of the mixed-precision eigensolve), at most max_sweeps
-// sweeps; *status gets 3 when they do not suffice.
-cudaError_t jacobi_grid_f32(float *A0, float *A1, float *V, float *diag, int n, GridBarrier *bar,
-                            int *status, int *sweeps_out, int max_sweeps, cudaStream_t st);
+// Block Jacobi in FP32 (jacobi.cu): V = eigenvectors of the symmetric A (n x n, column-
+// major, overwritten by the nearly diagonal result); scratch of block_jacobi_f32_scratch(n)
+// bytes (device, 8-byte aligned); *sweeps_out (device) = sweeps used or -1. Synchronises
+// the stream once per sweep from the third on.
+size_t block_jacobi_f32_scratch(int n);
+cudaError_t block_jacobi_f32(float *A, float *V, int n, void *scratch, int *sweeps_out,
+                             int max_sweeps, cudaStream_t st);
 // Self-tests of the bounded waits (failure detection without a fault): a grid barrier
 // that can never complete (status <- 4 after its spin limit) and an mbarrier that never
 // completes (err <- 1 after its probe limit).
