@@ -459,6 +459,7 @@ def mixed_vs_fp64(seed: int, resid_cut: float = 1e-4) -> dict:
     start()
     X32.copy_(X64)
     (rm, resm, _), t_m, ph_m, ck_m = timed(mixed)
+    f32 = f32_filter_roofline(ctx, w, X32, W32, b0)
     start()
     (r64, res64, _), t_64, ph_64, ck_64 = timed(fp64)
     ctx.close()
@@ -479,9 +480,36 @@ def mixed_vs_fp64(seed: int, resid_cut: float = 1e-4) -> dict:
                                           if conv.any() else None),
             "ritz_lowest": [float(x) for x in r64[:3]],
             "mixed_phases_ms": ph_m, "fp64_phases_ms": ph_64,
+            "f32_filter": f32,
             "clocks": {"mixed": ck_m, "fp64": ck_64},
             "timing": "one timed solve of each form (CUDA events), after one warm-up iteration "
                       "of each; start block drawn on the device before the timing"}
+
+
+def f32_filter_roofline(ctx, w, X32, W32, bounds, reps: int = 3) -> dict:
+    """The FP32 filter step alone: `reps` degree-m filters of the FP32 block (the mixed
+    solve's result, any valid interval), the CUDA-event time of their stencil launches
+    (k_stencil_f32_tma) from the library's phase counters, and the HBM fraction of the
+    steps' algorithmic bytes: 12 B per point-orbital (Y_j, Y_{j-1} read, Y_{j+1} written;
+    8 B for the first step) + 4 B of potential per node, against the measured copy."""
+    import torch
+    a, b, a0 = bounds
+    torch.cuda.synchronize()
+    ctx.profile_reset()
+    ctx.profile_enable(True)
+    for _ in range(reps):
+        ctx.cheb_filter(X32, W32, w.degree, a, b, a0)
+    torch.cuda.synchronize()
+    ctx.profile_enable(False)
+    n_launch, ms = ctx.profile_read()["stencil"]
+    m = w.degree
+    per_filter = w.nd * w.ns * (2 * 4 + (m - 1) * 3 * 4) + w.nd * m * 4
+    gbs = reps * per_filter / (ms / 1e3) / 1e9
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
+    return {"launches": n_launch, "ms_per_step": ms / max(n_launch, 1),
+            "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak,
+            "kernel": "k_stencil_f32_tma", "bytes_per_filter": per_filter,
+            "sample": f"{reps} degree-{m} FP32 filters of the {w.ns}-column block"}
 
 
 def serving_study(seed: int, requests: int, rates=(400.0, 20.0), below=(0.5,),
