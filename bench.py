@@ -16,12 +16,14 @@ Under torchrun (N > 1) each rank solves its own replica on its own GPU (replicas
 the path has no data exchange), times are max-reduced over ranks and `value` sums the
 ranks' work.
 
-Two more objects follow on one GPU (N = 1): `mixed160`, the large cluster (160^3, 400 atoms,
-Ns = 1024, degree 24) solved in the mixed-precision form and in the FP64 form on the same
-GPU from the same start (times, speed-up, Ritz-value differences of the converged states),
-and `serving`, the request loop under Poisson arrivals (p50/p99 latency and throughput at
-the configured and at sub-saturation rates, beside serial FP64 solves). Together they take
-about 15-20 minutes; --no-mixed160 and --serving-requests 0 skip them.
+Three more objects follow on one GPU (N = 1), after the timed region: `mixed160`, the large
+cluster (160^3, 400 atoms, Ns = 1024, degree 24) solved in the mixed-precision form and in
+the FP64 form on the same GPU from the same start (times, speed-up, Ritz-value differences
+of the converged states, the FP32 filter step's HBM fraction), `batching` (the batched
+filter of 64 uneven clusters against per-cluster launches) and `serving`, the request loop
+under Poisson arrivals (p50/p99 latency and throughput at the configured and at
+sub-saturation rates, beside serial FP64 solves). Together they take about 25 minutes;
+--no-mixed160, --no-batching and --serving-requests 0 skip them.
 
 --impl reference times the FP64 CPU oracle instead (on the host cores, rank 0 only),
 each step one CheFSI iteration of the same workload on a column slice, set up once.
