@@ -124,7 +124,10 @@ k_stencil_df(const TI *__restrict__ Y, const double *Yprev, double *out,
     const unsigned uy = bY[col];
     const bool nonfinite = ((uy >> 20) & 0x7ffu) == 0x7ffu;
     const int EY = bound_exponent(uy);
-    const double gs = ldexp(cf.ag, EY - 26);  // alpha g 2^(EY-26)
+    // alpha g 2^(EY-26); NaN for a column whose bound is not finite, which makes every output
+    // of the column NaN without a test per point
+    const double gs =
+        nonfinite ? __longlong_as_double(0x7ff8000000000000ll) : ldexp(cf.ag, EY - 26);
     // halo duties: nodes tid and tid + NT of the strips (left, right: R x BY each; top,
     // bottom: BX x R each); hs = shared-memory index (-1: none), hg = offset in the plane
     // (kNoNode: the node lies outside the grid and stays zero)
@@ -213,8 +216,8 @@ k_stencil_df(const TI *__restrict__ Y, const double *Yprev, double *out,
                 Rs = fmaf(cf.Wf[r], sr, Rs);
             }
             const double T = int51_to_double(A + (long long)__float2int_rn(Rs));
-            double o = fma(gs, T, fma(ucur, yc, hasP ? cf.mbeta * pcur : 0.0));
-            if (nonfinite) o = __longlong_as_double(0x7ff8000000000000ll);
+            // pcur is 0 without Y_{j-1} (its loads are guarded), so the term needs no test
+            const double o = fma(gs, T, fma(ucur, yc, cf.mbeta * pcur));
             omax = max(omax, abs_hi_word(o));
             out[cb + pij + pk] = o;
         }
